@@ -1,0 +1,261 @@
+/*
+ * FP64 CPU oracle for all-sky seedless clustering (Thrane & Coughlin,
+ * "Seedless clustering in all-sky searches for gravitational-wave transients").
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the slow, plain statement of what the
+ * GPU scorer must compute.  It shares no code, header, table or constant
+ * generator with the CUDA library; only tests, the package's smoke check and the
+ * benchmark's CPU-baseline leg may load it.
+ *
+ * What it computes (paper sections cited per function):
+ *   template generation  Sec. III (six random numbers per Bezier template, plus
+ *                        a uniform random delay, Sec. III after Eq. 6)
+ *   rasterisation        Sec. III, the quadratic Bezier curve (t(xi), f(xi))
+ *   statistic            Eq. 7 (Eq. 5 with the delay phase), sigma^-2 weighted
+ *                        form allowed by the footnote to Eq. 5
+ *   selection            Sec. III (most significant cluster), Sec. V (runs with
+ *                        different seeds combined by a maximum)
+ *
+ * Readings of the paper used here (the paper is silent on each):
+ *   - Bezier control times are pinned to the first, middle and last column, so
+ *     t(xi) = M xi with M = n_t - 1 and column j sits at xi = j / M; the curve
+ *     gives exactly one pixel per column, the nearest frequency bin with halves
+ *     rounded up.
+ *   - Random numbers: Philox4x64-10 (Salmon et al., SC'11) with counter
+ *     (g, 0, 0, 0) and key (seed, 0) for template index g.  Words u0, u1, u2
+ *     give the control frequency bins floor(u * n_f / 2^64); u3 gives the delay
+ *     tau = tau_max * ((2 (u3 >> 12) + 1) / 2^52 - 1), open and symmetric.
+ *   - Phase factor exp(+2 pi i f tau) with f = f_min + bin * df (Eq. 7).
+ *   - Weighted statistic: SNR = sum_j Re[e^{i theta_j} y_j sigma_j^-2] /
+ *     sqrt(sum_j sigma_j^-2); paper mode: SNR = (1/N) sum_j Re[e^{i theta_j}
+ *     y_j / sigma_j] (Eq. 7 with the complex SNR p = y / sigma).
+ *   - Loudest = signed maximum; ties go to the smaller template index.
+ *
+ * Precision: every step is IEEE binary64 with libm cos/sin; integers are exact
+ * 64-bit (128-bit for the Philox products and the bin draw).
+ */
+#include <math.h>
+#include <pthread.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ------------------------------------------------------------------ Philox */
+/* Philox4x64-10 as defined by Salmon, Moraes, Dror and Shaw (SC'11): each
+ * round multiplies words 0 and 2 by two fixed odd constants, the new state is
+ * (hi(M1*x2) ^ x1 ^ k0, lo(M1*x2), hi(M0*x0) ^ x3 ^ k1, lo(M0*x0)), and the
+ * key is bumped by two Weyl constants between rounds. */
+static const uint64_t PHILOX_M0 = 0xD2E7470EE14C6C93ULL;
+static const uint64_t PHILOX_M1 = 0xCA5A826395121157ULL;
+static const uint64_t PHILOX_W0 = 0x9E3779B97F4A7C15ULL; /* golden ratio */
+static const uint64_t PHILOX_W1 = 0xBB67AE8584CAA73BULL; /* sqrt(3) - 1 */
+
+void orc_philox4x64_10(const uint64_t ctr[4], const uint64_t key[2], uint64_t out[4])
+{
+    uint64_t x0 = ctr[0], x1 = ctr[1], x2 = ctr[2], x3 = ctr[3];
+    uint64_t k0 = key[0], k1 = key[1];
+    for (int r = 0; r < 10; ++r) {
+        unsigned __int128 p0 = (unsigned __int128)PHILOX_M0 * x0;
+        unsigned __int128 p1 = (unsigned __int128)PHILOX_M1 * x2;
+        uint64_t hi0 = (uint64_t)(p0 >> 64), lo0 = (uint64_t)p0;
+        uint64_t hi1 = (uint64_t)(p1 >> 64), lo1 = (uint64_t)p1;
+        uint64_t n0 = hi1 ^ x1 ^ k0;
+        uint64_t n1 = lo1;
+        uint64_t n2 = hi0 ^ x3 ^ k1;
+        uint64_t n3 = lo0;
+        x0 = n0; x1 = n1; x2 = n2; x3 = n3;
+        k0 += PHILOX_W0;
+        k1 += PHILOX_W1;
+    }
+    out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
+}
+
+/* ------------------------------------------------------ template parameters */
+/* Sec. III: a template is drawn from random numbers; here three control
+ * frequencies (integer bins, uniform on [0, n_f)) and one delay uniform on
+ * (-tau_max, +tau_max) (the isotropic-sky delay prior of Sec. III). */
+void orc_track_params(uint64_t seed, uint64_t g, int n_f, double tau_max,
+                      uint32_t f[3], double *tau)
+{
+    uint64_t ctr[4] = {g, 0, 0, 0};
+    uint64_t key[2] = {seed, 0};
+    uint64_t u[4];
+    orc_philox4x64_10(ctr, key, u);
+    for (int k = 0; k < 3; ++k)
+        f[k] = (uint32_t)(((unsigned __int128)u[k] * (uint64_t)n_f) >> 64);
+    uint64_t v = u[3] >> 12;                         /* 52 random bits */
+    double unit = (double)(2 * v + 1) / 4503599627370496.0 - 1.0; /* 2^52 */
+    *tau = tau_max * unit;
+}
+
+/* ------------------------------------------------------------ rasterisation */
+/* Sec. III, quadratic Bezier: f(xi) = (1-xi)^2 f0 + 2 (1-xi) xi f1 + xi^2 f2.
+ * With xi = j / M the value is num_j / M^2 where
+ * num_j = (M-j)^2 f0 + 2 (M-j) j f1 + j^2 f2, an exact integer; the pixel is
+ * the nearest bin, halves rounded up: floor((2 num_j + M^2) / (2 M^2)). */
+void orc_track_bins(const uint32_t f[3], int n_t, int32_t *bins)
+{
+    int64_t M = (int64_t)n_t - 1;
+    int64_t M2 = M * M;
+    for (int64_t j = 0; j <= M; ++j) {
+        int64_t a = M - j;
+        int64_t num = a * a * (int64_t)f[0] + 2 * a * j * (int64_t)f[1] + j * j * (int64_t)f[2];
+        bins[j] = (int32_t)((2 * num + M2) / (2 * M2));
+    }
+}
+
+/* ---------------------------------------------------------------------- map */
+/* The map the statistic reads: z = y sigma^-2 and w = sigma^-2 (weighted), or
+ * z = y / sigma and w = 1 (paper mode), all in binary64, [n_t][n_f]. */
+typedef struct {
+    int n_t, n_f;
+    double f_min, df;
+    int paper_mode;
+    double *z;   /* interleaved re, im: 2 * n_t * n_f */
+    double *w;   /* n_t * n_f */
+} orc_map;
+
+orc_map *orc_map_create(const float *y_c64, const float *sigma, int sigma_per_freq,
+                        int n_t, int n_f, double f_min, double df, int paper_mode)
+{
+    orc_map *m = (orc_map *)calloc(1, sizeof(orc_map));
+    if (!m) return NULL;
+    size_t np = (size_t)n_t * (size_t)n_f;
+    m->n_t = n_t; m->n_f = n_f; m->f_min = f_min; m->df = df; m->paper_mode = paper_mode;
+    m->z = (double *)malloc(2 * np * sizeof(double));
+    m->w = (double *)malloc(np * sizeof(double));
+    if (!m->z || !m->w) { free(m->z); free(m->w); free(m); return NULL; }
+    for (int t = 0; t < n_t; ++t) {
+        for (int k = 0; k < n_f; ++k) {
+            size_t p = (size_t)t * n_f + k;
+            double s = sigma_per_freq ? (double)sigma[k] : (double)sigma[p];
+            double yr = (double)y_c64[2 * p], yi = (double)y_c64[2 * p + 1];
+            if (paper_mode) {
+                m->z[2 * p] = yr / s; m->z[2 * p + 1] = yi / s; m->w[p] = 1.0;
+            } else {
+                double w = 1.0 / (s * s);
+                m->z[2 * p] = yr * w; m->z[2 * p + 1] = yi * w; m->w[p] = w;
+            }
+        }
+    }
+    return m;
+}
+
+void orc_map_free(orc_map *m)
+{
+    if (!m) return;
+    free(m->z); free(m->w); free(m);
+}
+
+/* ---------------------------------------------------------------- statistic */
+/* Eq. 7: sum over the template's pixels of Re[exp(2 pi i f tau) p(t; f)].
+ * Returns the SNR; also the raw sums S, W, and two magnitude sums used to
+ * bound rounding in comparisons: sum_j |Re term_j| and sum_j |z_j|. */
+double orc_score_track(const orc_map *m, const uint32_t f[3], double tau,
+                       double *S_out, double *W_out, double *absterm_out, double *absz_out)
+{
+    int n_t = m->n_t;
+    int32_t *bins = (int32_t *)malloc(sizeof(int32_t) * (size_t)n_t);
+    orc_track_bins(f, n_t, bins);
+    double S = 0.0, W = 0.0, A = 0.0, Z = 0.0;
+    for (int j = 0; j < n_t; ++j) {
+        size_t p = (size_t)j * m->n_f + (size_t)bins[j];
+        double fr = m->f_min + (double)bins[j] * m->df;
+        double th = 2.0 * M_PI * fr * tau;
+        double zr = m->z[2 * p], zi = m->z[2 * p + 1];
+        double term = cos(th) * zr - sin(th) * zi;   /* Re[(cos + i sin)(zr + i zi)] */
+        S += term;
+        W += m->w[p];
+        A += fabs(term);
+        Z += sqrt(zr * zr + zi * zi);
+    }
+    free(bins);
+    double snr = m->paper_mode ? S / (double)n_t : S / sqrt(W);
+    if (S_out) *S_out = S;
+    if (W_out) *W_out = W;
+    if (absterm_out) *absterm_out = A;
+    if (absz_out) *absz_out = Z;
+    return snr;
+}
+
+void orc_score_explicit(const orc_map *m, const uint32_t *f3, const double *tau, uint64_t n,
+                        double *snr, double *S, double *W, double *absterm, double *absz)
+{
+    for (uint64_t i = 0; i < n; ++i)
+        snr[i] = orc_score_track(m, f3 + 3 * i, tau[i], S ? S + i : NULL, W ? W + i : NULL,
+                                 absterm ? absterm + i : NULL, absz ? absz + i : NULL);
+}
+
+/* Score templates g = offset .. offset + T - 1 drawn with `seed`; threads take
+ * contiguous slices of the range.  snr_out[i] is the SNR of template offset+i. */
+typedef struct {
+    const orc_map *m;
+    uint64_t seed, g0, n;
+    double tau_max;
+    double *out;
+} orc_job;
+
+static void *orc_range_worker(void *arg)
+{
+    orc_job *jb = (orc_job *)arg;
+    for (uint64_t i = 0; i < jb->n; ++i) {
+        uint32_t f[3];
+        double tau;
+        orc_track_params(jb->seed, jb->g0 + i, jb->m->n_f, jb->tau_max, f, &tau);
+        jb->out[i] = orc_score_track(jb->m, f, tau, NULL, NULL, NULL, NULL);
+    }
+    return NULL;
+}
+
+int orc_score_range(const orc_map *m, uint64_t seed, uint64_t offset, uint64_t T,
+                    double tau_max, int nthreads, double *snr_out)
+{
+    if (nthreads < 1) nthreads = 1;
+    if ((uint64_t)nthreads > T) nthreads = T ? (int)T : 1;
+    pthread_t *th = (pthread_t *)malloc(sizeof(pthread_t) * (size_t)nthreads);
+    orc_job *jobs = (orc_job *)malloc(sizeof(orc_job) * (size_t)nthreads);
+    if (!th || !jobs) { free(th); free(jobs); return -1; }
+    uint64_t base = T / (uint64_t)nthreads, rem = T % (uint64_t)nthreads, start = 0;
+    for (int t = 0; t < nthreads; ++t) {
+        uint64_t n = base + ((uint64_t)t < rem ? 1 : 0);
+        jobs[t].m = m; jobs[t].seed = seed; jobs[t].g0 = offset + start; jobs[t].n = n;
+        jobs[t].tau_max = tau_max; jobs[t].out = snr_out + start;
+        start += n;
+    }
+    int rc = 0, started = 0;
+    for (int t = 0; t < nthreads; ++t) {
+        if (pthread_create(&th[t], NULL, orc_range_worker, &jobs[t]) != 0) { rc = -2; break; }
+        ++started;
+    }
+    for (int t = 0; t < started; ++t) pthread_join(th[t], NULL);
+    free(th); free(jobs);
+    return rc;
+}
+
+/* ---------------------------------------------------------------- selection */
+/* Most significant cluster (Sec. III) generalised to the K largest: order by
+ * SNR descending, then template index ascending. */
+typedef struct { double snr; uint64_t g; } orc_rec;
+
+static int orc_rec_cmp(const void *a, const void *b)
+{
+    const orc_rec *x = (const orc_rec *)a, *y = (const orc_rec *)b;
+    if (x->snr > y->snr) return -1;
+    if (x->snr < y->snr) return 1;
+    if (x->g < y->g) return -1;
+    if (x->g > y->g) return 1;
+    return 0;
+}
+
+int orc_topk(const double *snr, uint64_t T, uint64_t offset, int K,
+             double *snr_k, uint64_t *g_k)
+{
+    if (K < 0 || (uint64_t)K > T) return -1;
+    orc_rec *r = (orc_rec *)malloc(sizeof(orc_rec) * (size_t)(T ? T : 1));
+    if (!r) return -2;
+    for (uint64_t i = 0; i < T; ++i) { r[i].snr = snr[i]; r[i].g = offset + i; }
+    qsort(r, (size_t)T, sizeof(orc_rec), orc_rec_cmp);
+    for (int i = 0; i < K; ++i) { snr_k[i] = r[i].snr; g_k[i] = r[i].g; }
+    free(r);
+    return 0;
+}
