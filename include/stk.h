@@ -1,0 +1,186 @@
+/*
+ * stk.h - C ABI of the B300 scorer for all-sky seedless clustering
+ * (Thrane & Coughlin, "Seedless clustering in all-sky searches for
+ * gravitational-wave transients").
+ *
+ * The library scores many pseudo-random quadratic Bezier templates, each with a
+ * random inter-detector delay tau, against a complex cross-power SNR map and
+ * returns the loudest templates.  All arithmetic runs in CUDA kernels on one
+ * GPU; the host side only validates arguments, sizes buffers and launches.
+ *
+ * Conventions
+ *   - Every int-returning call returns STK_OK (0) or a negative STK_E* code;
+ *     stk_last_error() then holds a one-line message.
+ *   - Calls are asynchronous on the context's CUDA stream unless they return
+ *     host data (stk_score with STK_OUT_HOST, stk_track_params, stk_load_map,
+ *     stk_sync).  The stream is borrowed: the caller keeps ownership.
+ *   - Device pointers passed in stay owned by the caller; buffers the library
+ *     allocates (packed maps, scratch) are owned by the map or context and are
+ *     freed by stk_free_map / stk_destroy.
+ *   - A context is not thread-safe; use one context per host thread.
+ *   - Template index g runs over counter_offset .. counter_offset + n_tracks-1;
+ *     template g is the same on every call, any split of the index range, and
+ *     any GPU, so runs over disjoint ranges combine exactly by taking the
+ *     largest SNR (Sec. V, "intermediate data files").
+ */
+#ifndef STK_H
+#define STK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define STK_API __attribute__((visibility("default")))
+#else
+#define STK_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------- */
+#define STK_OK        0
+#define STK_EINVAL   -1  /* bad argument: sizes, pointers, flags, non-finite or non-positive inputs */
+#define STK_ENOMEM   -2  /* device or host allocation failed */
+#define STK_ECUDA    -3  /* a CUDA runtime call failed (message names it) */
+#define STK_ETIMEOUT -4  /* a bounded in-kernel wait gave up; results of that call are invalid */
+#define STK_ESTATE   -5  /* call out of order, e.g. scoring before stk_set_tracks */
+
+/* ---- stk_load_map flags ---------------------------------------------- */
+#define STK_HOST_PTR       0x1u /* y and sigma are host pointers (pageable or pinned) */
+#define STK_SIGMA_PER_FREQ 0x2u /* sigma holds n_f values, one per frequency bin, constant in time */
+#define STK_NORM_PAPER     0x4u /* Eq. 7 as printed: SNR = (1/N) sum Re[e^{2 pi i f tau} y/sigma] */
+
+/* ---- stk_score flags ------------------------------------------------- */
+#define STK_OUT_HOST 0x1u /* out_topk is host memory; the call waits for the result */
+
+/* Largest k accepted by stk_score. */
+#define STK_MAX_K 4096
+
+typedef struct stk_ctx stk_ctx; /* opaque; owns scratch and the borrowed stream */
+typedef struct stk_map stk_map; /* opaque; the packed map on the device */
+
+/* One selected template.  40 bytes, no padding surprises. */
+typedef struct {
+    double   snr;      /* detection statistic of the template (see stk_load_map) */
+    uint64_t index;    /* template index g */
+    uint32_t f[3];     /* control frequency bins f0 (first column), f1 (middle control), f2 (last column) */
+    uint32_t reserved; /* zero */
+    double   tau;      /* delay in seconds, |tau| < tau_max */
+} stk_hit;
+
+/* Library version, 10000*major + 100*minor + patch. */
+STK_API int stk_version(void);
+
+/* Create a context on CUDA device `device`, issuing work on `cuda_stream`
+ * (a cudaStream_t; NULL = the legacy default stream).  *out receives the
+ * context.  Errors: STK_EINVAL (out NULL, device out of range), STK_ECUDA. */
+STK_API int stk_create(stk_ctx **out, int device, void *cuda_stream);
+
+/* Free the context and its scratch after the stream has finished with them.
+ * NULL is a no-op.  Maps created through it must be freed first. */
+STK_API void stk_destroy(stk_ctx *ctx);
+
+/* Change the stream later calls are issued on (borrowed, not owned). */
+STK_API int stk_set_stream(stk_ctx *ctx, void *cuda_stream);
+
+/* Copy and pack an ft-map (Eq. 6: the complex SNR map p(t; f), here given as
+ * a cross-power y with per-pixel standard deviation sigma, Appendix A).
+ *   y_c64   complex64 [n_t][n_f], time-major (frequency fastest), interleaved re, im
+ *   sigma   float32 [n_t][n_f], or [n_f] with STK_SIGMA_PER_FREQ; every value finite, > 0
+ *   n_t     time columns, >= 2 (a template has one pixel per column)
+ *   n_f     frequency bins, >= 1; bin k has frequency f_min_hz + k * df_hz
+ *   flags   STK_HOST_PTR | STK_SIGMA_PER_FREQ | STK_NORM_PAPER
+ * Statistic selected (Eq. 7 and the footnote to Eq. 5 allowing other weights):
+ *   default         SNR = sum_j Re[e^{2 pi i f_j tau} y_j sigma_j^-2] / sqrt(sum_j sigma_j^-2)
+ *   STK_NORM_PAPER  SNR = (1/n_t) sum_j Re[e^{2 pi i f_j tau} y_j / sigma_j]
+ * The library keeps its own packed copy; the caller may free y and sigma when
+ * the call returns (it synchronises the stream).  Errors: STK_EINVAL (sizes,
+ * NULL pointers, a non-finite y, sigma <= 0 or non-finite, f_min/df
+ * non-finite or df <= 0), STK_ENOMEM, STK_ECUDA. */
+STK_API int stk_load_map(stk_ctx *ctx, const void *y_c64, const float *sigma, int n_t, int n_f,
+                 double f_min_hz, double df_hz, unsigned flags, stk_map **out);
+
+/* Free a packed map (waits for the context's stream).  NULL is a no-op. */
+STK_API void stk_free_map(stk_map *map);
+
+/* Report a map's shape and flags (any pointer may be NULL). */
+STK_API int stk_map_info(const stk_map *map, int *n_t, int *n_f, unsigned *flags);
+
+/* Set the template range scored by later calls (Sec. III: T templates drawn at
+ * random, each with a delay uniform on (-tau_max, +tau_max)).
+ *   n_tracks        T, >= 1
+ *   seed            Philox key word; runs meant to be combined use different seeds (Sec. V)
+ *   counter_offset  first template index g
+ *   tau_max_s       >= 0, finite (the inter-site light travel time, ~10 ms for the LIGO pair)
+ * Errors: STK_EINVAL. */
+STK_API int stk_set_tracks(stk_ctx *ctx, uint64_t n_tracks, uint64_t seed, uint64_t counter_offset,
+                   double tau_max_s);
+
+/* Score every template of the current range against `map` and return the k
+ * loudest (Sec. III: the most significant cluster; k > 1 keeps runners-up),
+ * ordered by SNR descending, then index ascending.  `out_topk` holds k
+ * entries: device memory, or host memory with STK_OUT_HOST (then the call
+ * waits for the result).  k in 1 .. min(STK_MAX_K, n_tracks).
+ * Errors: STK_EINVAL, STK_ESTATE (no range set), STK_ENOMEM, STK_ECUDA,
+ * STK_ETIMEOUT (reported by a later stk_sync when the output is on the device). */
+STK_API int stk_score(stk_ctx *ctx, const stk_map *map, int k, stk_hit *out_topk, unsigned flags);
+
+/* Score every template of the current range and write its SNR (Eq. 7) to
+ * out_snr_dev[i] for template counter_offset + i; caller-owned device buffer
+ * of n_tracks doubles.  Errors: STK_EINVAL, STK_ESTATE, STK_ECUDA. */
+STK_API int stk_score_all(stk_ctx *ctx, const stk_map *map, double *out_snr_dev);
+
+/* Parameters of template g as the scoring kernels draw them (Sec. III):
+ * f[3] control bins, *tau delay, and, if bins_host is not NULL, the pixel
+ * (frequency bin) of each of the map's n_t columns.  Uses the seed and
+ * tau_max of the current range; g need not lie inside it.  Synchronous.
+ * Errors: STK_EINVAL, STK_ESTATE, STK_ECUDA. */
+STK_API int stk_track_params(stk_ctx *ctx, const stk_map *map, uint64_t g, uint32_t f[3], double *tau,
+                     int32_t *bins_host);
+
+/* Score n explicit templates (Eq. 7): f3_dev [n][3] control bins (each < n_f),
+ * tau_dev [n] delays in seconds; SNRs to out_snr_dev [n].  All device
+ * pointers, caller-owned.  Bins outside [0, n_f) are clamped to the map edge
+ * after the out-of-range template is flagged: the call then returns
+ * STK_EINVAL at the next stk_sync.  Errors: STK_EINVAL, STK_ECUDA. */
+STK_API int stk_score_explicit(stk_ctx *ctx, const stk_map *map, const uint32_t *f3_dev, const double *tau_dev,
+                       uint64_t n, double *out_snr_dev);
+
+/* Wait for the context's stream and report the first deferred error raised
+ * by a kernel since the last stk_sync (bounded-wait timeout, bad explicit
+ * template).  Clears it. */
+STK_API int stk_sync(stk_ctx *ctx);
+
+/* Turn per-kernel timing on (1) or off (0).  When on, every scoring and
+ * selection kernel is bracketed with CUDA events on the context's stream. */
+STK_API int stk_set_profiling(stk_ctx *ctx, int enable);
+
+/* Per-kernel device time of the last stk_score / stk_score_all call, in ms:
+ * out[0] scoring kernel, out[1] selection (all top-k kernels), out[2] launch
+ * count of that call.  Requires profiling on; synchronises the stream. */
+STK_API int stk_last_timings(stk_ctx *ctx, double out[3]);
+
+/* ---- tuning (kernel choice and launch shape; results do not depend on them) */
+#define STK_OPT_KERNEL   1 /* 0 automatic, 1 one-thread-per-template kernel, 2 shared-memory slab kernel */
+#define STK_OPT_THREADS  2 /* slab kernel block size, 0 = automatic, else 32 .. 1024 */
+#define STK_OPT_MAX_R    3 /* slab kernel: most templates held per thread, 1 .. 4 (default 4) */
+#define STK_OPT_STAGES   4 /* slab kernel: shared-memory slab buffers, 2 .. 4 (default 2) */
+#define STK_OPT_SMEM_KB  5 /* slab kernel: shared-memory budget in KiB, 0 = the device maximum */
+
+/* Set a tuning option for later scoring calls.  Errors: STK_EINVAL. */
+STK_API int stk_set_option(stk_ctx *ctx, int option, int64_t value);
+
+/* Launch shape of the last scoring call: out[0] kernel (1 simple, 2 slab),
+ * [1] templates per thread, [2] threads per block, [3] grid, [4] time columns
+ * per slab, [5] slab buffers, [6] template batches, [7] dynamic shared bytes. */
+STK_API int stk_last_plan(const stk_ctx *ctx, int64_t out[8]);
+
+/* Message for the last error on ctx (never NULL; "" when none). */
+STK_API const char *stk_last_error(const stk_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* STK_H */

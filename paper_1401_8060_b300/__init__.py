@@ -1,0 +1,219 @@
+"""B300 scorer for all-sky seedless clustering (Thrane & Coughlin).
+
+A thin Python binding over libstk.so.  Every step of scoring (template draws,
+rasterisation, phase rotation, sums, normalisation, top-k) runs in the
+library's CUDA kernels; this module only marshals arguments.  PyTorch supplies
+device memory and the CUDA stream.
+
+    ctx = Context()                                 # device 0, torch's current stream
+    m = ctx.load_map(y, sigma, f_min=40.0, df=0.5)   # y complex64 [n_t][n_f]; sigma [n_f] or [n_t][n_f]
+    ctx.set_tracks(5_000_000, seed=2, offset=0, tau_max=0.010)
+    hits = ctx.score(m, k=16)                       # numpy structured array, loudest first
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from . import _lib as L
+from ._lib import HIT_DTYPE, STK_MAX_K  # noqa: F401
+
+__all__ = ["Context", "Map", "StkError", "HIT_DTYPE", "STK_MAX_K", "lib"]
+
+lib = L.lib
+
+
+class StkError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"stk error {code}: {msg}")
+        self.code = code
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _is_tensor(x):
+    try:
+        import torch
+    except ImportError:  # pragma: no cover
+        return False
+    return isinstance(x, torch.Tensor)
+
+
+class Map:
+    """A packed ft-map owned by the library (freed on close / garbage collection)."""
+
+    def __init__(self, ctx, handle, n_t, n_f, flags):
+        self._ctx, self._h, self.n_t, self.n_f, self.flags = ctx, handle, n_t, n_f, flags
+
+    @property
+    def handle(self):
+        if not self._h:
+            raise ValueError("map has been freed")
+        return self._h
+
+    def close(self):
+        if self._h:
+            lib().stk_free_map(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Context:
+    """A scoring context on one CUDA device (calls stk_create)."""
+
+    def __init__(self, device: int = 0, stream=None):
+        torch = _torch()
+        self.device = int(device)
+        h = C.c_void_p()
+        self._stream = stream
+        rc = lib().stk_create(C.byref(h), self.device, C.c_void_p(self._stream_ptr()))
+        if rc != 0:
+            raise StkError(rc, lib().stk_last_error(None).decode())
+        self._h = h
+        self._torch = torch
+
+    # ---- plumbing
+    def _stream_ptr(self):
+        torch = _torch()
+        s = self._stream if self._stream is not None else torch.cuda.current_stream(self.device)
+        return int(s.cuda_stream)
+
+    def _check(self, rc):
+        if rc != 0:
+            raise StkError(rc, lib().stk_last_error(self._h).decode())
+
+    def _bind_stream(self):
+        self._check(lib().stk_set_stream(self._h, C.c_void_p(self._stream_ptr())))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().stk_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- calls
+    def load_map(self, y, sigma, f_min: float, df: float, paper_mode: bool = False) -> Map:
+        """stk_load_map.  y: complex64 [n_t][n_f] (CUDA tensor, or host numpy/tensor);
+        sigma: float32 [n_f] (per frequency) or [n_t][n_f]."""
+        self._bind_stream()
+        host = not (_is_tensor(y) and y.is_cuda)
+        if host:
+            ya = y.numpy() if _is_tensor(y) else y
+            sa = sigma.numpy() if _is_tensor(sigma) else sigma
+            ya = np.ascontiguousarray(ya, dtype=np.complex64)
+            sa = np.ascontiguousarray(sa, dtype=np.float32)
+            yp, sp = ya.ctypes.data, sa.ctypes.data
+            keep = (ya, sa)
+        else:
+            torch = self._torch
+            if y.dtype != torch.complex64 or sigma.dtype != torch.float32:
+                raise TypeError("y must be complex64 and sigma float32")
+            if not sigma.is_cuda:
+                raise TypeError("y and sigma must both be CUDA tensors or both host arrays")
+            y = y.contiguous()
+            sigma = sigma.contiguous()
+            yp, sp = y.data_ptr(), sigma.data_ptr()
+            keep = (y, sigma)
+        n_t, n_f = keep[0].shape
+        per_freq = tuple(keep[1].shape) == (n_f,)
+        if not per_freq and tuple(keep[1].shape) != (n_t, n_f):
+            raise ValueError(f"sigma shape {tuple(keep[1].shape)} is neither ({n_f},) nor ({n_t}, {n_f})")
+        flags = (L.STK_HOST_PTR if host else 0) | (L.STK_SIGMA_PER_FREQ if per_freq else 0) | \
+            (L.STK_NORM_PAPER if paper_mode else 0)
+        h = C.c_void_p()
+        self._check(lib().stk_load_map(self._h, C.c_void_p(yp), C.c_void_p(sp), int(n_t), int(n_f),
+                                       float(f_min), float(df), flags, C.byref(h)))
+        del keep
+        return Map(self, h, int(n_t), int(n_f), flags)
+
+    def set_tracks(self, n_tracks: int, seed: int, offset: int = 0, tau_max: float = 0.010):
+        """stk_set_tracks: templates offset .. offset+n_tracks-1 drawn with `seed`."""
+        self._check(lib().stk_set_tracks(self._h, int(n_tracks), int(seed), int(offset), float(tau_max)))
+        self.n_tracks = int(n_tracks)
+
+    def score(self, m: Map, k: int, out=None):
+        """stk_score.  Returns a numpy HIT_DTYPE array (host, waits) or, when `out`
+        is a CUDA uint8 tensor of k*40 bytes, fills it asynchronously and returns it."""
+        self._bind_stream()
+        if out is None:
+            res = np.zeros(k, dtype=HIT_DTYPE)
+            self._check(lib().stk_score(self._h, m.handle, int(k), C.c_void_p(res.ctypes.data), L.STK_OUT_HOST))
+            return res
+        if out.numel() * out.element_size() < 40 * k or not out.is_cuda:
+            raise ValueError("out must be a CUDA tensor of at least 40*k bytes")
+        self._check(lib().stk_score(self._h, m.handle, int(k), C.c_void_p(out.data_ptr()), 0))
+        return out
+
+    def score_all(self, m: Map, out=None):
+        """stk_score_all: SNR of every template (float64 CUDA tensor)."""
+        torch = self._torch
+        self._bind_stream()
+        if out is None:
+            out = torch.empty(self.n_tracks, dtype=torch.float64, device=f"cuda:{self.device}")
+        if out.dtype != torch.float64 or not out.is_cuda or out.numel() < self.n_tracks:
+            raise ValueError("out must be a CUDA float64 tensor of n_tracks elements")
+        self._check(lib().stk_score_all(self._h, m.handle, C.c_void_p(out.data_ptr())))
+        return out
+
+    def track_params(self, m: Map, g: int, bins: bool = True):
+        """stk_track_params: ((f0, f1, f2), tau, bins[n_t] or None) of template g."""
+        self._bind_stream()
+        f = np.zeros(3, dtype=np.uint32)
+        tau = C.c_double()
+        b = np.zeros(m.n_t, dtype=np.int32) if bins else None
+        self._check(lib().stk_track_params(self._h, m.handle, int(g), C.c_void_p(f.ctypes.data), C.byref(tau),
+                                           C.c_void_p(b.ctypes.data) if bins else None))
+        return tuple(int(v) for v in f), float(tau.value), b
+
+    def score_explicit(self, m: Map, f3, tau, out=None):
+        """stk_score_explicit on CUDA tensors f3 [n][3] (int32/uint32 bins) and tau [n] (float64)."""
+        torch = self._torch
+        self._bind_stream()
+        dev = f"cuda:{self.device}"
+        f3 = torch.as_tensor(f3).to(device=dev).contiguous()
+        if f3.dtype not in (torch.int32, torch.uint32):
+            f3 = f3.to(torch.int32)
+        tau = torch.as_tensor(tau, dtype=torch.float64).to(device=dev).contiguous()
+        n = tau.numel()
+        if f3.numel() != 3 * n:
+            raise ValueError("f3 must have shape [n][3]")
+        if out is None:
+            out = torch.empty(n, dtype=torch.float64, device=dev)
+        self._check(lib().stk_score_explicit(self._h, m.handle, C.c_void_p(f3.data_ptr()),
+                                             C.c_void_p(tau.data_ptr()), n, C.c_void_p(out.data_ptr())))
+        return out
+
+    def sync(self):
+        """stk_sync: wait and raise the first deferred kernel error."""
+        self._check(lib().stk_sync(self._h))
+
+    def set_option(self, option: int, value: int):
+        self._check(lib().stk_set_option(self._h, int(option), int(value)))
+
+    def last_plan(self) -> dict:
+        a = (C.c_int64 * 8)()
+        self._check(lib().stk_last_plan(self._h, a))
+        keys = ["kernel", "R", "threads", "grid", "S", "nstage", "nbatches", "smem"]
+        return dict(zip(keys, [int(v) for v in a]))
+
+    def set_profiling(self, on: bool):
+        self._check(lib().stk_set_profiling(self._h, 1 if on else 0))
+
+    def last_timings(self) -> dict:
+        a = (C.c_double * 3)()
+        self._check(lib().stk_last_timings(self._h, a))
+        return dict(score_ms=a[0], select_ms=a[1], launches=int(a[2]))

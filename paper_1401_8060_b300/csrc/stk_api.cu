@@ -1,0 +1,534 @@
+// C ABI of the scorer: contexts, map packing, argument checks and launches.
+// The statistic and template definitions are those of Eq. 7 and Sec. III of
+// the paper; see stk.h for the contract of each call.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "stk_internal.cuh"
+
+using namespace stk;
+
+struct stk_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int num_sms = 0;
+    size_t smem_optin = 0;
+    bool have_tracks = false;
+    TrackSet ts{};
+    int *d_err = nullptr;          // device error/flag word
+    double *snr_buf = nullptr;     // scratch: one SNR per template
+    size_t snr_cap = 0;
+    void *sel_buf = nullptr;       // scratch: selection state
+    size_t sel_cap = 0;
+    stk_hit *hits_dev = nullptr;   // STK_MAX_K records
+    uint32_t *small_dev = nullptr; // track_params: f[3] + pad, tau, bins
+    size_t small_cap = 0;
+    Tuning tune{};
+    ScorePlan plan{};
+    bool profiling = false;
+    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+    bool timed = false;
+    int last_launches = 0;
+    std::string err;
+};
+
+struct stk_map {
+    stk_ctx *ctx = nullptr;
+    MapDev dev{};
+    void *rec_buf = nullptr;
+    void *w_buf = nullptr;
+    unsigned flags = 0;
+};
+
+static thread_local std::string g_create_err;
+
+static int set_err(stk_ctx *c, int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (c) c->err = buf;
+    else g_create_err = buf;
+    return code;
+}
+
+#define CUDA_TRY(ctx, call)                                                                                         \
+    do {                                                                                                           \
+        cudaError_t e_ = (call);                                                                                   \
+        if (e_ != cudaSuccess)                                                                                     \
+            return set_err((ctx), e_ == cudaErrorMemoryAllocation ? STK_ENOMEM : STK_ECUDA, "%s: %s (%s:%d)", #call, \
+                           cudaGetErrorString(e_), __FILE__, __LINE__);                                            \
+    } while (0)
+
+namespace {
+
+// Pack y, sigma into polar records z = |z| e^{2 pi i arg} with
+// z = y sigma^-2 (weighted) or y / sigma (paper form), and the weights.
+__global__ void pack_kernel(const float2 *__restrict__ y, const float *__restrict__ sigma, int per_freq, int n_t,
+                            int n_f, int ldr, int ldw, int paper, uint2 *__restrict__ rec, float *__restrict__ wout,
+                            int *err)
+{
+    const float s0 = sigma[0];
+    int flags = 0;
+    const uint64_t total = (uint64_t)n_t * ldr;
+    for (uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; p < total;
+         p += (uint64_t)gridDim.x * blockDim.x) {
+        const int t = (int)(p / ldr), k = (int)(p % ldr);
+        if (k >= n_f) {
+            rec[p] = make_uint2(0u, 0u);
+            continue;
+        }
+        const size_t q = (size_t)t * n_f + k;
+        const float2 v = y[q];
+        const float s = per_freq ? sigma[k] : sigma[q];
+        if (!isfinite(v.x) || !isfinite(v.y) || !(s > 0.f) || !isfinite(s)) flags |= ERR_BADINPUT;
+        if (s != s0) flags |= FLAG_SIGMA_VARIES;
+        const double sd = (double)s;
+        double zr, zi, w;
+        if (paper) {
+            zr = (double)v.x / sd;
+            zi = (double)v.y / sd;
+            w = 1.0;
+        } else {
+            w = 1.0 / (sd * sd);
+            zr = (double)v.x * w;
+            zi = (double)v.y * w;
+        }
+        const double mag = hypot(zr, zi);
+        const double turns = atan2(zi, zr) / 6.283185307179586476925;  // (-1/2, 1/2]
+        const long long fix = llrint(turns * 4294967296.0);
+        rec[p] = make_uint2(__float_as_uint((float)mag), (uint32_t)fix);
+        if (wout) {
+            if (!per_freq) wout[(size_t)t * ldw + k] = (float)w;
+            else if (t == 0) wout[k] = (float)w;
+        }
+    }
+    if (flags) atomicOr(err, flags);
+}
+
+// floor(N / d) == umulhi(N, magic) >> shift for every N <= n_max:
+// magic = ceil(2^(32+s) / d) < 2^32 and (magic d - 2^(32+s)) n_max < 2^(32+s).
+bool find_magic(uint64_t d, uint64_t n_max, uint32_t &magic, int &shift)
+{
+    if (n_max >= (1ull << 32) || d == 0) return false;
+    for (int s = 0; s < 32; ++s) {
+        const unsigned __int128 p2 = (unsigned __int128)1 << (32 + s);
+        const unsigned __int128 m = (p2 + d - 1) / d;
+        if (m >= ((unsigned __int128)1 << 32)) continue;
+        const unsigned __int128 e = m * d - p2;
+        if (e * n_max < p2) {
+            magic = (uint32_t)m;
+            shift = s;
+            return true;
+        }
+    }
+    return false;
+}
+
+int ensure(stk_ctx *c, void **buf, size_t *cap, size_t need)
+{
+    if (*cap >= need && *buf) return STK_OK;
+    if (*buf) {
+        cudaStreamSynchronize(c->stream);
+        cudaFree(*buf);
+        *buf = nullptr;
+        *cap = 0;
+    }
+    cudaError_t e = cudaMalloc(buf, need);
+    if (e != cudaSuccess) {
+        *buf = nullptr;
+        return set_err(c, STK_ENOMEM, "cudaMalloc(%zu bytes): %s", need, cudaGetErrorString(e));
+    }
+    *cap = need;
+    return STK_OK;
+}
+
+int read_err_flags(stk_ctx *c, int *flags)
+{
+    int h = 0;
+    CUDA_TRY(c, cudaMemcpyAsync(&h, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    CUDA_TRY(c, cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
+    *flags = h;
+    return STK_OK;
+}
+
+int flags_to_status(stk_ctx *c, int f)
+{
+    if (f & ERR_TIMEOUT) return set_err(c, STK_ETIMEOUT, "a bounded in-kernel wait for a map slab gave up");
+    if (f & ERR_BADTRACK) return set_err(c, STK_EINVAL, "explicit template with a control bin outside [0, n_f)");
+    return STK_OK;
+}
+
+int check_ready(stk_ctx *c, const stk_map *m)
+{
+    if (!m || m->ctx != c) return set_err(c, STK_EINVAL, "map is NULL or belongs to another context");
+    if (!c->have_tracks) return set_err(c, STK_ESTATE, "stk_set_tracks has not been called");
+    return STK_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int stk_version(void) { return 100; }
+
+const char *stk_last_error(const stk_ctx *ctx) { return ctx ? ctx->err.c_str() : g_create_err.c_str(); }
+
+int stk_create(stk_ctx **out, int device, void *cuda_stream)
+{
+    if (!out) return set_err(nullptr, STK_EINVAL, "out is NULL");
+    *out = nullptr;
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess) return set_err(nullptr, STK_ECUDA, "cudaGetDeviceCount: %s", cudaGetErrorString(e));
+    if (device < 0 || device >= ndev) return set_err(nullptr, STK_EINVAL, "device %d not in [0, %d)", device, ndev);
+    e = cudaSetDevice(device);
+    if (e != cudaSuccess) return set_err(nullptr, STK_ECUDA, "cudaSetDevice: %s", cudaGetErrorString(e));
+    stk_ctx *c = new stk_ctx();
+    c->device = device;
+    c->stream = (cudaStream_t)cuda_stream;
+    int v = 0;
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, device);
+    c->num_sms = v;
+    cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+    c->smem_optin = (size_t)v;
+    if (cudaMalloc(&c->d_err, sizeof(int)) != cudaSuccess ||
+        cudaMalloc(&c->hits_dev, sizeof(stk_hit) * STK_MAX_K) != cudaSuccess) {
+        cudaFree(c->d_err);
+        delete c;
+        return set_err(nullptr, STK_ENOMEM, "context allocation failed");
+    }
+    cudaMemset(c->d_err, 0, sizeof(int));
+    for (auto &ev : c->ev) cudaEventCreate(&ev);
+    cudaDeviceSynchronize();
+    *out = c;
+    return STK_OK;
+}
+
+void stk_destroy(stk_ctx *c)
+{
+    if (!c) return;
+    cudaSetDevice(c->device);
+    cudaStreamSynchronize(c->stream);
+    cudaFree(c->d_err);
+    cudaFree(c->snr_buf);
+    cudaFree(c->sel_buf);
+    cudaFree(c->hits_dev);
+    cudaFree(c->small_dev);
+    for (auto &ev : c->ev)
+        if (ev) cudaEventDestroy(ev);
+    delete c;
+}
+
+int stk_set_stream(stk_ctx *c, void *s)
+{
+    if (!c) return STK_EINVAL;
+    c->stream = (cudaStream_t)s;
+    return STK_OK;
+}
+
+int stk_set_option(stk_ctx *c, int option, int64_t value)
+{
+    if (!c) return STK_EINVAL;
+    switch (option) {
+    case STK_OPT_KERNEL:
+        if (value < 0 || value > 2) return set_err(c, STK_EINVAL, "kernel option must be 0, 1 or 2");
+        c->tune.kernel = (int)value;
+        return STK_OK;
+    case STK_OPT_THREADS:
+        if (value < 0 || value > 1024) return set_err(c, STK_EINVAL, "threads must be in [0, 1024]");
+        c->tune.threads = (int)value;
+        return STK_OK;
+    case STK_OPT_MAX_R:
+        if (value < 1 || value > 4) return set_err(c, STK_EINVAL, "templates per thread must be in [1, 4]");
+        c->tune.max_R = (int)value;
+        return STK_OK;
+    case STK_OPT_STAGES:
+        if (value < 2 || value > 4) return set_err(c, STK_EINVAL, "stages must be in [2, 4]");
+        c->tune.nstage = (int)value;
+        return STK_OK;
+    case STK_OPT_SMEM_KB:
+        if (value < 0 || value > 1024) return set_err(c, STK_EINVAL, "shared-memory budget out of range");
+        c->tune.smem_kb = (int)value;
+        return STK_OK;
+    default: return set_err(c, STK_EINVAL, "unknown option %d", option);
+    }
+}
+
+int stk_last_plan(const stk_ctx *c, int64_t out[8])
+{
+    if (!c || !out) return STK_EINVAL;
+    const ScorePlan &p = c->plan;
+    out[0] = p.kernel; out[1] = p.R; out[2] = p.threads; out[3] = p.grid;
+    out[4] = p.S; out[5] = p.nstage; out[6] = (int64_t)p.nbatches; out[7] = (int64_t)p.smem;
+    return STK_OK;
+}
+
+int stk_load_map(stk_ctx *c, const void *y_c64, const float *sigma, int n_t, int n_f, double f_min_hz,
+                 double df_hz, unsigned flags, stk_map **out)
+{
+    if (!c) return STK_EINVAL;
+    if (!out) return set_err(c, STK_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!y_c64 || !sigma) return set_err(c, STK_EINVAL, "y or sigma is NULL");
+    if (n_t < 2) return set_err(c, STK_EINVAL, "n_t = %d: a template needs at least 2 columns", n_t);
+    if (n_f < 1) return set_err(c, STK_EINVAL, "n_f = %d must be >= 1", n_f);
+    if ((uint64_t)n_t * (uint64_t)n_f > (1ull << 34)) return set_err(c, STK_EINVAL, "map too large");
+    {
+        const unsigned __int128 M = (unsigned __int128)(n_t - 1);
+        if (M * M * (2 * (unsigned __int128)n_f) >= ((unsigned __int128)1 << 62))
+            return set_err(c, STK_EINVAL, "map shape %d x %d too large for exact 64-bit rasterisation", n_t, n_f);
+    }
+    if (!std::isfinite(f_min_hz) || !std::isfinite(df_hz) || !(df_hz > 0))
+        return set_err(c, STK_EINVAL, "f_min must be finite and df finite and > 0");
+    if (flags & ~(STK_HOST_PTR | STK_SIGMA_PER_FREQ | STK_NORM_PAPER))
+        return set_err(c, STK_EINVAL, "unknown flags 0x%x", flags);
+    CUDA_TRY(c, cudaSetDevice(c->device));
+    const bool host = flags & STK_HOST_PTR, per_freq = flags & STK_SIGMA_PER_FREQ, paper = flags & STK_NORM_PAPER;
+    const size_t npx = (size_t)n_t * n_f;
+    const size_t ybytes = npx * 8, sbytes = (per_freq ? (size_t)n_f : npx) * 4;
+
+    stk_map *m = new stk_map();
+    m->ctx = c;
+    m->flags = flags;
+    MapDev &d = m->dev;
+    d.n_t = n_t;
+    d.n_f = n_f;
+    d.ldr = (n_f + 1) / 2 * 2;
+    d.ldw = (n_f + 3) / 4 * 4;
+    d.paper = paper ? 1 : 0;
+    d.f_min = f_min_hz;
+    d.df = df_hz;
+    d.M = (uint32_t)(n_t - 1);
+    d.d = 2ull * d.M * d.M;
+    const uint64_t n_max = (uint64_t)d.M * d.M * (2ull * (uint64_t)n_f - 1);
+    d.fast32 = find_magic(d.d, n_max, d.magic, d.shift) ? 1 : 0;
+
+    void *ytmp = nullptr, *stmp = nullptr;
+    auto fail = [&](int code) {
+        cudaStreamSynchronize(c->stream);
+        cudaFree(ytmp);
+        cudaFree(stmp);
+        cudaFree(m->rec_buf);
+        cudaFree(m->w_buf);
+        delete m;
+        return code;
+    };
+    cudaError_t e;
+    const float2 *ysrc = (const float2 *)y_c64;
+    const float *ssrc = sigma;
+    if (host) {
+        if ((e = cudaMalloc(&ytmp, ybytes)) != cudaSuccess || (e = cudaMalloc(&stmp, sbytes)) != cudaSuccess)
+            return fail(set_err(c, STK_ENOMEM, "staging allocation: %s", cudaGetErrorString(e)));
+        if ((e = cudaMemcpyAsync(ytmp, y_c64, ybytes, cudaMemcpyHostToDevice, c->stream)) != cudaSuccess ||
+            (e = cudaMemcpyAsync(stmp, sigma, sbytes, cudaMemcpyHostToDevice, c->stream)) != cudaSuccess)
+            return fail(set_err(c, STK_ECUDA, "host-to-device copy: %s", cudaGetErrorString(e)));
+        ysrc = (const float2 *)ytmp;
+        ssrc = (const float *)stmp;
+    }
+    const size_t recbytes = (size_t)n_t * d.ldr * 8;
+    if ((e = cudaMalloc(&m->rec_buf, recbytes)) != cudaSuccess)
+        return fail(set_err(c, STK_ENOMEM, "map allocation (%zu bytes): %s", recbytes, cudaGetErrorString(e)));
+    const size_t wbytes = per_freq ? (size_t)d.ldw * 4 : (size_t)n_t * d.ldw * 4;
+    if ((e = cudaMalloc(&m->w_buf, wbytes)) != cudaSuccess)
+        return fail(set_err(c, STK_ENOMEM, "weight allocation: %s", cudaGetErrorString(e)));
+    if ((e = cudaMemsetAsync(m->w_buf, 0, wbytes, c->stream)) != cudaSuccess ||
+        (e = cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream)) != cudaSuccess)
+        return fail(set_err(c, STK_ECUDA, "memset: %s", cudaGetErrorString(e)));
+    const uint64_t total = (uint64_t)n_t * d.ldr;
+    const int blocks = (int)std::min<uint64_t>((total + 255) / 256, (uint64_t)c->num_sms * 8);
+    pack_kernel<<<blocks, 256, 0, c->stream>>>(ysrc, ssrc, per_freq ? 1 : 0, n_t, n_f, d.ldr, d.ldw, d.paper,
+                                                (uint2 *)m->rec_buf, (float *)m->w_buf, c->d_err);
+    if ((e = cudaGetLastError()) != cudaSuccess)
+        return fail(set_err(c, STK_ECUDA, "pack kernel launch: %s", cudaGetErrorString(e)));
+    int fl = 0;
+    if (read_err_flags(c, &fl) != STK_OK) return fail(STK_ECUDA);
+    if (fl & ERR_BADINPUT) return fail(set_err(c, STK_EINVAL, "y has a non-finite value or sigma is <= 0 or non-finite"));
+    cudaFree(ytmp);
+    cudaFree(stmp);
+    ytmp = stmp = nullptr;
+    if (paper) {
+        d.wmode = WMODE_CONST;
+        d.w_const = 1.0f;
+    } else if (!(fl & FLAG_SIGMA_VARIES)) {
+        d.wmode = WMODE_CONST;
+        float w0 = 0.f;
+        if ((e = cudaMemcpy(&w0, m->w_buf, sizeof(float), cudaMemcpyDeviceToHost)) != cudaSuccess)
+            return fail(set_err(c, STK_ECUDA, "weight read-back: %s", cudaGetErrorString(e)));
+        d.w_const = w0;
+    } else {
+        d.wmode = per_freq ? WMODE_FREQ : WMODE_PIXEL;
+    }
+    d.rec = (const uint2 *)m->rec_buf;
+    d.w = d.wmode == WMODE_CONST ? nullptr : (const float *)m->w_buf;
+    *out = m;
+    return STK_OK;
+}
+
+void stk_free_map(stk_map *m)
+{
+    if (!m) return;
+    if (m->ctx) {
+        cudaSetDevice(m->ctx->device);
+        cudaStreamSynchronize(m->ctx->stream);
+    }
+    cudaFree(m->rec_buf);
+    cudaFree(m->w_buf);
+    delete m;
+}
+
+int stk_map_info(const stk_map *m, int *n_t, int *n_f, unsigned *flags)
+{
+    if (!m) return STK_EINVAL;
+    if (n_t) *n_t = m->dev.n_t;
+    if (n_f) *n_f = m->dev.n_f;
+    if (flags) *flags = m->flags;
+    return STK_OK;
+}
+
+int stk_set_tracks(stk_ctx *c, uint64_t n_tracks, uint64_t seed, uint64_t counter_offset, double tau_max_s)
+{
+    if (!c) return STK_EINVAL;
+    if (n_tracks < 1) return set_err(c, STK_EINVAL, "n_tracks must be >= 1");
+    if (n_tracks > 0xffffffffull) return set_err(c, STK_EINVAL, "n_tracks must be < 2^32 per call; split the range");
+    if (!std::isfinite(tau_max_s) || tau_max_s < 0) return set_err(c, STK_EINVAL, "tau_max must be finite and >= 0");
+    c->ts.n = n_tracks;
+    c->ts.seed = seed;
+    c->ts.offset = counter_offset;
+    c->ts.tau_max = tau_max_s;
+    c->have_tracks = true;
+    return STK_OK;
+}
+
+static int score_into(stk_ctx *c, const stk_map *m, double *out)
+{
+    CUDA_TRY(c, cudaSetDevice(c->device));
+    if (c->profiling) CUDA_TRY(c, cudaEventRecord(c->ev[0], c->stream));
+    cudaError_t e = launch_score_generated(m->dev, c->ts, out, c->d_err, c->tune, c->num_sms, c->smem_optin,
+                                           c->stream, &c->plan);
+    if (e != cudaSuccess) return set_err(c, STK_ECUDA, "scoring kernel launch: %s", cudaGetErrorString(e));
+    if (c->profiling) CUDA_TRY(c, cudaEventRecord(c->ev[1], c->stream));
+    return STK_OK;
+}
+
+int stk_score_all(stk_ctx *c, const stk_map *m, double *out_snr_dev)
+{
+    if (!c) return STK_EINVAL;
+    int rc = check_ready(c, m);
+    if (rc) return rc;
+    if (!out_snr_dev) return set_err(c, STK_EINVAL, "out_snr_dev is NULL");
+    rc = score_into(c, m, out_snr_dev);
+    if (rc) return rc;
+    c->timed = c->profiling;
+    c->last_launches = 1;
+    if (c->profiling) CUDA_TRY(c, cudaEventRecord(c->ev[2], c->stream));
+    return STK_OK;
+}
+
+int stk_score(stk_ctx *c, const stk_map *m, int k, stk_hit *out, unsigned flags)
+{
+    if (!c) return STK_EINVAL;
+    int rc = check_ready(c, m);
+    if (rc) return rc;
+    if (!out) return set_err(c, STK_EINVAL, "out_topk is NULL");
+    if (flags & ~STK_OUT_HOST) return set_err(c, STK_EINVAL, "unknown flags 0x%x", flags);
+    if (k < 1 || k > STK_MAX_K || (uint64_t)k > c->ts.n)
+        return set_err(c, STK_EINVAL, "k = %d must be in [1, min(%d, n_tracks))", k, STK_MAX_K);
+    rc = ensure(c, (void **)&c->snr_buf, &c->snr_cap, c->ts.n * sizeof(double));
+    if (rc) return rc;
+    rc = ensure(c, &c->sel_buf, &c->sel_cap, select_scratch_bytes(c->ts.n, k));
+    if (rc) return rc;
+    rc = score_into(c, m, c->snr_buf);
+    if (rc) return rc;
+    stk_hit *dst = (flags & STK_OUT_HOST) ? c->hits_dev : out;
+    int nl = 0;
+    cudaError_t e = launch_select_topk(c->snr_buf, c->ts.n, k, c->ts, m->dev, c->sel_buf, dst, c->stream, &nl);
+    if (e != cudaSuccess) return set_err(c, STK_ECUDA, "selection launch: %s", cudaGetErrorString(e));
+    c->last_launches = 1 + nl;
+    c->timed = c->profiling;
+    if (c->profiling) CUDA_TRY(c, cudaEventRecord(c->ev[2], c->stream));
+    if (flags & STK_OUT_HOST) {
+        CUDA_TRY(c, cudaMemcpyAsync(out, c->hits_dev, sizeof(stk_hit) * (size_t)k, cudaMemcpyDeviceToHost, c->stream));
+        int fl = 0;
+        rc = read_err_flags(c, &fl);
+        if (rc) return rc;
+        return flags_to_status(c, fl);
+    }
+    return STK_OK;
+}
+
+int stk_track_params(stk_ctx *c, const stk_map *m, uint64_t g, uint32_t f[3], double *tau, int32_t *bins_host)
+{
+    if (!c) return STK_EINVAL;
+    int rc = check_ready(c, m);
+    if (rc) return rc;
+    if (!f || !tau) return set_err(c, STK_EINVAL, "f or tau is NULL");
+    CUDA_TRY(c, cudaSetDevice(c->device));
+    const size_t need = 32 + (size_t)m->dev.n_t * 4;
+    rc = ensure(c, (void **)&c->small_dev, &c->small_cap, need);
+    if (rc) return rc;
+    uint32_t *fd = c->small_dev;
+    double *td = (double *)((char *)c->small_dev + 16);
+    int32_t *bd = (int32_t *)((char *)c->small_dev + 32);
+    cudaError_t e = launch_track_params(m->dev, c->ts, g, fd, td, bins_host ? bd : nullptr, c->stream);
+    if (e != cudaSuccess) return set_err(c, STK_ECUDA, "params launch: %s", cudaGetErrorString(e));
+    CUDA_TRY(c, cudaMemcpyAsync(f, fd, 12, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(tau, td, 8, cudaMemcpyDeviceToHost, c->stream));
+    if (bins_host)
+        CUDA_TRY(c, cudaMemcpyAsync(bins_host, bd, (size_t)m->dev.n_t * 4, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    return STK_OK;
+}
+
+int stk_score_explicit(stk_ctx *c, const stk_map *m, const uint32_t *f3, const double *tau, uint64_t n,
+                       double *out)
+{
+    if (!c) return STK_EINVAL;
+    if (!m || m->ctx != c) return set_err(c, STK_EINVAL, "map is NULL or belongs to another context");
+    if (n == 0) return STK_OK;
+    if (!f3 || !tau || !out) return set_err(c, STK_EINVAL, "NULL pointer");
+    CUDA_TRY(c, cudaSetDevice(c->device));
+    cudaError_t e = launch_score_explicit(m->dev, f3, tau, n, out, c->d_err, c->stream);
+    if (e != cudaSuccess) return set_err(c, STK_ECUDA, "explicit scoring launch: %s", cudaGetErrorString(e));
+    return STK_OK;
+}
+
+int stk_sync(stk_ctx *c)
+{
+    if (!c) return STK_EINVAL;
+    CUDA_TRY(c, cudaSetDevice(c->device));
+    int fl = 0;
+    int rc = read_err_flags(c, &fl);
+    if (rc) return rc;
+    return flags_to_status(c, fl);
+}
+
+int stk_set_profiling(stk_ctx *c, int enable)
+{
+    if (!c) return STK_EINVAL;
+    c->profiling = enable != 0;
+    c->timed = false;
+    return STK_OK;
+}
+
+int stk_last_timings(stk_ctx *c, double out[3])
+{
+    if (!c || !out) return STK_EINVAL;
+    if (!c->timed) return set_err(c, STK_ESTATE, "no profiled call yet (stk_set_profiling)");
+    CUDA_TRY(c, cudaEventSynchronize(c->ev[2]));
+    float a = 0.f, b = 0.f;
+    CUDA_TRY(c, cudaEventElapsedTime(&a, c->ev[0], c->ev[1]));
+    CUDA_TRY(c, cudaEventElapsedTime(&b, c->ev[1], c->ev[2]));
+    out[0] = a;
+    out[1] = b;
+    out[2] = c->last_launches;
+    return STK_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,278 @@
+// Internal declarations shared by the library's translation units.
+//
+// Notation follows the paper (Thrane & Coughlin, all-sky seedless clustering):
+// a template is a quadratic Bezier curve through control frequencies f0, f1,
+// f2 (Sec. III) with a random delay tau (Sec. III, after Eq. 6); its statistic
+// is Eq. 7, the sum over its pixels of Re[exp(2 pi i f tau) p(t; f)].
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/stk.h"
+
+namespace stk {
+
+// ---------------------------------------------------------------- packed map
+// Each pixel is stored once, in polar form, as an 8-byte record:
+//   .x = bits of |z| (float), .y = arg(z) in turns as unsigned Q0.32,
+// where z = y sigma^-2 (weighted statistic) or z = y / sigma (STK_NORM_PAPER).
+// Then Re[e^{i theta} z] = |z| cos(theta + 2 pi arg z): one cosine per pixel.
+// Weights w = sigma^-2 enter only the weighted normaliser sqrt(sum w).
+enum WMode : int {
+    WMODE_CONST = 0,  // every pixel has the same weight (w_const), or paper mode
+    WMODE_FREQ = 1,   // weight depends on frequency only: table w[n_f]
+    WMODE_PIXEL = 2,  // weight per pixel: plane w[n_t][ldw]
+};
+
+struct MapDev {
+    int n_t, n_f;
+    int ldr;          // records per row: n_f rounded up to a multiple of 2 (16-byte rows)
+    int ldw;          // floats per weight row (WMODE_PIXEL): n_f rounded up to a multiple of 4
+    int wmode;
+    int paper;        // 1: SNR = S / n_t
+    float w_const;    // WMODE_CONST weight (sigma^-2), 1 in paper mode
+    double f_min, df; // Hz
+    const uint2 *rec; // [n_t][ldr]
+    const float *w;   // [n_f] (WMODE_FREQ) or [n_t][ldw] (WMODE_PIXEL), else null
+    // Rasteriser: column j of template (f0, f1, f2) sits at bin floor(N_j / d) with
+    // N_j = 2 num_j + M^2, num_j = (M-j)^2 f0 + 2 (M-j) j f1 + j^2 f2, d = 2 M^2.
+    uint32_t M;       // n_t - 1
+    uint64_t d;       // 2 M^2
+    uint32_t magic;   // floor(N / d) = umulhi(N, magic) >> shift for all N <= N_max (when fast32)
+    int shift;
+    int fast32;       // N_max = M^2 (2 n_f - 1) < 2^32 and the magic pair is exact up to N_max
+};
+
+struct TrackSet {
+    uint64_t n, seed, offset;
+    double tau_max;
+};
+
+// ---------------------------------------------------------------- error bits (device flag)
+enum : int {
+    ERR_TIMEOUT = 1,   // a bounded mbarrier wait gave up
+    ERR_BADTRACK = 2,  // explicit template with a control bin >= n_f
+    ERR_BADINPUT = 4,  // map packing saw a non-finite y or a bad sigma
+    FLAG_SIGMA_VARIES = 8,  // map packing saw more than one sigma value
+};
+
+// ---------------------------------------------------------------- Philox4x64-10
+// Counter-based generator of Salmon, Moraes, Dror and Shaw (SC'11): ten
+// rounds of two 64x64->128 multiplies by fixed odd multipliers, with the key
+// bumped by two Weyl increments between rounds.
+__host__ __device__ __forceinline__ void mul64_hilo(uint64_t a, uint64_t b, uint64_t &hi, uint64_t &lo)
+{
+#ifdef __CUDA_ARCH__
+    hi = __umul64hi(a, b);
+    lo = a * b;
+#else
+    unsigned __int128 p = (unsigned __int128)a * b;
+    hi = (uint64_t)(p >> 64);
+    lo = (uint64_t)p;
+#endif
+}
+
+__host__ __device__ __forceinline__ void philox4x64_10(uint64_t c0, uint64_t c1, uint64_t c2, uint64_t c3,
+                                                       uint64_t k0, uint64_t k1, uint64_t out[4])
+{
+    const uint64_t kMul0 = 0xD2E7470EE14C6C93ULL, kMul1 = 0xCA5A826395121157ULL;
+    const uint64_t kWeyl0 = 0x9E3779B97F4A7C15ULL, kWeyl1 = 0xBB67AE8584CAA73BULL;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        uint64_t h0, l0, h1, l1;
+        mul64_hilo(kMul0, c0, h0, l0);
+        mul64_hilo(kMul1, c2, h1, l1);
+        const uint64_t n0 = h1 ^ c1 ^ k0, n2 = h0 ^ c3 ^ k1;
+        c0 = n0; c1 = l1; c2 = n2; c3 = l0;
+        k0 += kWeyl0; k1 += kWeyl1;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+// Template g (Sec. III): counter (g, 0, 0, 0), key (seed, 0).  Control bins
+// are floor(u * n_f / 2^64) of words 0..2; the delay is
+// tau_max * ((2 (u3 >> 12) + 1) 2^-52 - 1), exact before the one multiply.
+__host__ __device__ __forceinline__ void draw_track(uint64_t seed, uint64_t g, uint32_t n_f, double tau_max,
+                                                    uint32_t f[3], double &tau)
+{
+    uint64_t u[4];
+    philox4x64_10(g, 0, 0, 0, seed, 0, u);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        uint64_t hi, lo;
+        mul64_hilo(u[k], (uint64_t)n_f, hi, lo);
+        f[k] = (uint32_t)hi;
+    }
+    const uint64_t v = u[3] >> 12;
+    const double unit = (double)(2 * v + 1) * 0x1p-52 - 1.0;
+    tau = tau_max * unit;
+}
+
+// ---------------------------------------------------------------- phase in turns
+// theta_j / 2 pi = (f_min + bin_j df) tau = b + bin_j a  (mod 1), with
+// a = frac(df tau) kept as unsigned Q0.64 (a_hi:a_lo) and b = frac(f_min tau)
+// as Q0.32.  Per pixel, turn = umulhi(bin, a_lo) + bin a_hi + b + arg (mod 2^32)
+// is the angle to 2^-32 turns for bins below 2^32.  b carries +2^8 so that the
+// 23-bit float built from turn >> 9 is rounded to nearest rather than truncated.
+struct Phase {
+    uint32_t a_lo, a_hi, b;
+};
+
+__device__ __forceinline__ Phase phase_consts(double f_min, double df, double tau)
+{
+    Phase p;
+    double x = df * tau;
+    x -= floor(x);                                   // [0, 1), exact
+    const unsigned long long a = __double2ull_rz(x * 18446744073709551616.0);  // < 2^64
+    p.a_lo = (uint32_t)a;
+    p.a_hi = (uint32_t)(a >> 32);
+    double y = f_min * tau;
+    y -= floor(y);
+    p.b = (uint32_t)__double2ull_rn(y * 4294967296.0) + 0x100u;   // 2^32 wraps to 0: same angle
+    return p;
+}
+
+// Angle (turns, unsigned Q0.32) -> cos(2 pi turn).  The top 23 bits of the
+// turn, with the sign bit flipped, form the mantissa of a float in [1, 2); minus
+// 1.5 that is the turn mapped to [-0.5, 0.5).  __cosf is accurate to about
+// 2^-21 absolute on [-pi, pi].
+__device__ __forceinline__ float cos_turn(uint32_t t)
+{
+    const float x = __uint_as_float((t >> 9) ^ 0x3fc00000u) - 1.5f;
+    return __cosf(x * 6.28318530717958647692f);
+}
+
+__device__ __forceinline__ uint32_t pixel_turn(uint32_t bin, const Phase &p, uint32_t arg)
+{
+    return __umulhi(bin, p.a_lo) + bin * p.a_hi + p.b + arg;
+}
+
+// ---------------------------------------------------------------- rasteriser state
+// Second-order forward differences of N_j (exact modulo 2^32; every N_j lies in
+// [0, N_max] < 2^32 when fast32 holds):
+//   N_0 = (2 f0 + 1) M^2,  D_0 = 4 M (f1 - f0) + 2 (f0 - 2 f1 + f2),  D2 = 4 (f0 - 2 f1 + f2).
+struct Raster32 {
+    uint32_t N, D, D2;
+};
+
+__device__ __forceinline__ Raster32 raster_init(uint32_t f0, uint32_t f1, uint32_t f2, uint32_t M)
+{
+    const int64_t M2 = (int64_t)M * M;
+    const int64_t c2 = (int64_t)f0 - 2 * (int64_t)f1 + (int64_t)f2;
+    Raster32 r;
+    r.N = (uint32_t)((2 * (int64_t)f0 + 1) * M2);
+    r.D = (uint32_t)(4 * (int64_t)M * ((int64_t)f1 - (int64_t)f0) + 2 * c2);
+    r.D2 = (uint32_t)(4 * c2);
+    return r;
+}
+
+// Wide form for maps where N_max does not fit 32 bits: num_j directly in 64-bit.
+__device__ __forceinline__ uint32_t raster_bin_wide(uint32_t f0, uint32_t f1, uint32_t f2, uint32_t M, uint32_t j,
+                                                    uint64_t d)
+{
+    const uint64_t a = (uint64_t)(M - j), b = (uint64_t)j, M2 = (uint64_t)M * M;
+    const uint64_t num = a * a * f0 + 2 * a * b * f1 + b * b * f2;
+    return (uint32_t)((2 * num + M2) / d);
+}
+
+// ---------------------------------------------------------------- mbarrier + bulk copy
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// One-dimensional bulk copy global -> shared, completing `bytes` on `bar`.
+// dst, src and bytes must be multiples of 16.
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ uint64_t global_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wait for the phase with the given parity to complete; gives up after
+// `limit_ns` nanoseconds and returns false.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint64_t limit_ns)
+{
+    const uint32_t a = smem_u32(bar);
+    uint32_t done = 0;
+    asm volatile("{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+                 : "=r"(done)
+                 : "r"(a), "r"(parity)
+                 : "memory");
+    if (done) return true;
+    const uint64_t t0 = global_ns();
+    while (true) {
+        asm volatile("{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+                     : "=r"(done)
+                     : "r"(a), "r"(parity)
+                     : "memory");
+        if (done) return true;
+        if (global_ns() - t0 > limit_ns) return false;
+    }
+}
+
+// ---------------------------------------------------------------- host-side launchers
+struct ScorePlan {
+    int kernel;       // 1 simple, 2 staged
+    int R;            // templates per thread (staged)
+    int threads;      // threads per block
+    int grid;
+    int S;            // rows per slab (staged)
+    int nstage;       // slab buffers (staged)
+    int nslabs;
+    uint64_t batch;   // templates per batch (staged)
+    uint64_t nbatches;
+    size_t smem;
+};
+
+struct Tuning {
+    int kernel = 0;      // 0 auto
+    int threads = 0;     // 0 auto
+    int max_R = 4;
+    int nstage = 2;
+    int smem_kb = 0;     // 0 auto
+};
+
+// Launch the scoring kernel for generated templates; writes n SNRs to out.
+cudaError_t launch_score_generated(const MapDev &m, const TrackSet &ts, double *out, int *err, const Tuning &tu,
+                                   int num_sms, size_t smem_optin, cudaStream_t st, ScorePlan *plan_out);
+// Explicit templates f3[n][3], tau[n].
+cudaError_t launch_score_explicit(const MapDev &m, const uint32_t *f3, const double *tau, uint64_t n, double *out,
+                                  int *err, cudaStream_t st);
+// Parameters and bins of one template (device buffers).
+cudaError_t launch_track_params(const MapDev &m, const TrackSet &ts, uint64_t g, uint32_t *f_dev, double *tau_dev,
+                                int32_t *bins_dev, cudaStream_t st);
+
+// Top-k selection over snr[0..n): hits get (snr, offset + i, params).  Scratch
+// is caller-provided: see select_scratch_bytes.
+size_t select_scratch_bytes(uint64_t n, int k);
+cudaError_t launch_select_topk(const double *snr, uint64_t n, int k, const TrackSet &ts, const MapDev &m,
+                               void *scratch, stk_hit *out_dev, cudaStream_t st, int *launches);
+
+}  // namespace stk

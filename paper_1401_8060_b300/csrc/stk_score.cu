@@ -1,0 +1,368 @@
+// Scoring kernels: Eq. 7 of the paper for many templates.
+//
+//   SNR_tot = sum over the template's pixels of Re[exp(2 pi i f tau) p(t; f)],
+//   normalised by sqrt(sum sigma^-2) (weighted) or by N (paper form).
+//
+// Two kernels compute the same per-template arithmetic in the same order:
+//   score_simple  one thread per template, pixels read from the L2-resident map;
+//                 used for explicit templates, small jobs and maps whose
+//                 rasteriser needs 64-bit numerators.
+//   score_staged  persistent CTAs; each CTA holds a batch of R * blockDim
+//                 templates in registers and streams the map through shared
+//                 memory in slabs of S time columns (one bulk copy per slab,
+//                 double-buffered on mbarriers), so every gathered pixel is a
+//                 shared-memory load.  The map is read from L2 once per batch.
+#include <algorithm>
+#include <cstdio>
+
+#include "stk_internal.cuh"
+
+namespace stk {
+
+namespace {
+
+constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s per slab wait
+constexpr int kMaxThreads = 1024;
+
+template <int WMODE>
+__device__ __forceinline__ double finalize_snr(float acc, float W, const MapDev &m)
+{
+    if (m.paper) return (double)acc / (double)m.n_t;
+    const double Wd = (WMODE == WMODE_CONST) ? (double)m.n_t * (double)m.w_const : (double)W;
+    return (double)acc / sqrt(Wd);
+}
+
+// ------------------------------------------------------------------ simple kernel
+template <int WMODE, bool EXPLICIT, bool FAST32>
+__global__ void __launch_bounds__(256) score_simple_kernel(MapDev m, TrackSet ts, const uint32_t *__restrict__ f3,
+                                                           const double *__restrict__ tau_in, uint64_t n,
+                                                           double *__restrict__ out, int *err)
+{
+    const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint32_t f[3];
+    double tau;
+    if (EXPLICIT) {
+        bool bad = false;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            f[k] = f3[3 * i + k];
+            if (f[k] >= (uint32_t)m.n_f) { bad = true; f[k] = (uint32_t)m.n_f - 1; }
+        }
+        if (bad) atomicOr(err, ERR_BADTRACK);
+        tau = tau_in[i];
+    } else {
+        draw_track(ts.seed, ts.offset + i, (uint32_t)m.n_f, ts.tau_max, f, tau);
+    }
+    const Phase ph = phase_consts(m.f_min, m.df, tau);
+    float acc = 0.f, W = 0.f;
+    Raster32 r;
+    if (FAST32) r = raster_init(f[0], f[1], f[2], m.M);
+    const uint2 *rec = m.rec;
+    for (int j = 0; j < m.n_t; ++j) {
+        uint32_t bin;
+        if (FAST32) {
+            bin = __umulhi(r.N, m.magic) >> m.shift;
+            r.N += r.D;
+            r.D += r.D2;
+        } else {
+            bin = raster_bin_wide(f[0], f[1], f[2], m.M, (uint32_t)j, m.d);
+        }
+        const uint2 v = __ldg(rec + (size_t)j * m.ldr + bin);
+        acc = fmaf(__uint_as_float(v.x), cos_turn(pixel_turn(bin, ph, v.y)), acc);
+        if (WMODE == WMODE_FREQ) W += __ldg(m.w + bin);
+        if (WMODE == WMODE_PIXEL) W += __ldg(m.w + (size_t)j * m.ldw + bin);
+    }
+    out[i] = finalize_snr<WMODE>(acc, W, m);
+}
+
+// ------------------------------------------------------------------ staged kernel
+struct StagedArgs {
+    int S, nstage, nslabs;
+    uint64_t batch, nbatches;
+    uint32_t slab_recs;    // S * ldr
+    uint32_t slab_ws;      // S * ldw (WMODE_PIXEL)
+    uint32_t wtab_floats;  // n_f rounded to 4 (WMODE_FREQ)
+};
+
+template <int R, int WMODE>
+__global__ void __launch_bounds__(kMaxThreads, 1)
+    score_staged_kernel(MapDev m, TrackSet ts, StagedArgs a, double *__restrict__ out, int *err)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint2 *srec = reinterpret_cast<uint2 *>(smem);
+    float *sw = reinterpret_cast<float *>(srec + (size_t)a.nstage * a.slab_recs);  // WMODE_PIXEL slabs
+    float *swt = sw + (WMODE == WMODE_PIXEL ? (size_t)a.nstage * a.slab_ws : 0);    // WMODE_FREQ table
+    uint64_t *bars = reinterpret_cast<uint64_t *>(swt + (WMODE == WMODE_FREQ ? a.wtab_floats : 0));
+
+    const int tid = threadIdx.x;
+    const int nthr = blockDim.x;
+    if (blockIdx.x >= a.nbatches) return;
+    const uint64_t my_nb = (a.nbatches - blockIdx.x + gridDim.x - 1) / gridDim.x;
+    const uint64_t total = my_nb * (uint64_t)a.nslabs;  // slabs this CTA consumes, over all its batches
+    const uint32_t row_bytes = (uint32_t)m.ldr * 8u;
+    const uint32_t wrow_bytes = (uint32_t)m.ldw * 4u;
+
+    if (tid == 0) {
+        for (int s = 0; s < a.nstage; ++s) mbar_init(&bars[s], 1);
+        fence_mbar_init();
+    }
+    if (WMODE == WMODE_FREQ) {
+        for (int k = tid; k < m.n_f; k += nthr) swt[k] = m.w[k];
+    }
+    __syncthreads();
+
+    // Producer: slab q of this CTA's sequence goes to buffer q % nstage.
+    auto issue = [&](uint64_t q) {
+        const int slot = (int)(q % (uint64_t)a.nstage);
+        const int slab = (int)(q % (uint64_t)a.nslabs);
+        const int row0 = slab * a.S;
+        const int rows = min(a.S, m.n_t - row0);
+        uint32_t bytes = (uint32_t)rows * row_bytes;
+        if (WMODE == WMODE_PIXEL) bytes += (uint32_t)rows * wrow_bytes;
+        mbar_arrive_expect_tx(&bars[slot], bytes);
+        bulk_g2s(srec + (size_t)slot * a.slab_recs, m.rec + (size_t)row0 * m.ldr, (uint32_t)rows * row_bytes,
+                 &bars[slot]);
+        if (WMODE == WMODE_PIXEL)
+            bulk_g2s(sw + (size_t)slot * a.slab_ws, m.w + (size_t)row0 * m.ldw, (uint32_t)rows * wrow_bytes,
+                     &bars[slot]);
+    };
+    if (tid == 0) {
+        const uint64_t pre = total < (uint64_t)a.nstage ? total : (uint64_t)a.nstage;
+        for (uint64_t q = 0; q < pre; ++q) issue(q);
+    }
+
+    const uint32_t magic = m.magic;
+    const int shift = m.shift;
+    uint64_t q = 0;
+    bool failed = false;
+    for (uint64_t ib = 0; ib < my_nb && !failed; ++ib) {
+        const uint64_t b = blockIdx.x + ib * gridDim.x;
+        const uint64_t t0 = b * a.batch;
+        const uint64_t tn = (ts.n - t0) < a.batch ? (ts.n - t0) : a.batch;
+
+        uint32_t N[R], D[R], D2[R];
+        Phase ph[R];
+        float acc[R], W[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            uint64_t i = (uint64_t)tid + (uint64_t)r * nthr;
+            if (i >= tn) i = tn - 1;  // idle slot: repeat a valid template, result discarded
+            uint32_t f[3];
+            double tau;
+            draw_track(ts.seed, ts.offset + t0 + i, (uint32_t)m.n_f, ts.tau_max, f, tau);
+            const Raster32 rs = raster_init(f[0], f[1], f[2], m.M);
+            N[r] = rs.N; D[r] = rs.D; D2[r] = rs.D2;
+            ph[r] = phase_consts(m.f_min, m.df, tau);
+            acc[r] = 0.f;
+            W[r] = 0.f;
+        }
+
+        for (int s = 0; s < a.nslabs; ++s, ++q) {
+            const int slot = (int)(q % (uint64_t)a.nstage);
+            const uint32_t parity = (uint32_t)((q / (uint64_t)a.nstage) & 1ull);
+            const bool ok = mbar_wait(&bars[slot], parity, kWaitLimitNs);
+            const int rows = min(a.S, m.n_t - s * a.S);
+            const uint2 *row = srec + (size_t)slot * a.slab_recs;
+            const float *wrow = sw + (size_t)slot * a.slab_ws;
+#pragma unroll 2
+            for (int jj = 0; jj < rows; ++jj) {
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const uint32_t bin = __umulhi(N[r], magic) >> shift;
+                    const uint2 v = row[bin];
+                    acc[r] = fmaf(__uint_as_float(v.x), cos_turn(pixel_turn(bin, ph[r], v.y)), acc[r]);
+                    if (WMODE == WMODE_FREQ) W[r] += swt[bin];
+                    if (WMODE == WMODE_PIXEL) W[r] += wrow[bin];
+                    N[r] += D[r];
+                    D[r] += D2[r];
+                }
+                row += m.ldr;
+                if (WMODE == WMODE_PIXEL) wrow += m.ldw;
+            }
+            // Everyone is done with this buffer; refill it with slab q + nstage.
+            if (__syncthreads_or(!ok)) {
+                failed = true;
+                break;
+            }
+            if (tid == 0 && q + a.nstage < total) issue(q + a.nstage);
+        }
+        if (failed) break;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const uint64_t i = (uint64_t)tid + (uint64_t)r * nthr;
+            if (i < tn) out[t0 + i] = finalize_snr<WMODE>(acc[r], W[r], m);
+        }
+    }
+    if (failed && tid == 0) {
+        atomicOr(err, ERR_TIMEOUT);
+        // Let copies already in flight land before the CTA's shared memory goes away.
+        for (uint64_t qq = q + 1; qq < q + (uint64_t)a.nstage && qq < total; ++qq)
+            mbar_wait(&bars[qq % a.nstage], (uint32_t)((qq / a.nstage) & 1ull), kWaitLimitNs);
+    }
+}
+
+template <int R, int WMODE>
+cudaError_t launch_staged_R(const MapDev &m, const TrackSet &ts, const StagedArgs &sa, int grid, int threads,
+                            size_t smem, double *out, int *err, cudaStream_t st)
+{
+    auto k = score_staged_kernel<R, WMODE>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k<<<grid, threads, smem, st>>>(m, ts, sa, out, err);
+    return cudaGetLastError();
+}
+
+template <int WMODE>
+cudaError_t launch_staged_W(int R, const MapDev &m, const TrackSet &ts, const StagedArgs &sa, int grid, int threads,
+                            size_t smem, double *out, int *err, cudaStream_t st)
+{
+    switch (R) {
+    case 1: return launch_staged_R<1, WMODE>(m, ts, sa, grid, threads, smem, out, err, st);
+    case 2: return launch_staged_R<2, WMODE>(m, ts, sa, grid, threads, smem, out, err, st);
+    case 3: return launch_staged_R<3, WMODE>(m, ts, sa, grid, threads, smem, out, err, st);
+    case 4: return launch_staged_R<4, WMODE>(m, ts, sa, grid, threads, smem, out, err, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+template <int WMODE, bool EXPLICIT>
+cudaError_t launch_simple_W(const MapDev &m, const TrackSet &ts, const uint32_t *f3, const double *tau, uint64_t n,
+                            double *out, int *err, cudaStream_t st)
+{
+    const int threads = 256;
+    const uint64_t blocks = (n + threads - 1) / threads;
+    if (blocks > 0x7fffffffull) return cudaErrorInvalidValue;
+    if (m.fast32)
+        score_simple_kernel<WMODE, EXPLICIT, true><<<(unsigned)blocks, threads, 0, st>>>(m, ts, f3, tau, n, out, err);
+    else
+        score_simple_kernel<WMODE, EXPLICIT, false><<<(unsigned)blocks, threads, 0, st>>>(m, ts, f3, tau, n, out, err);
+    return cudaGetLastError();
+}
+
+template <bool EXPLICIT>
+cudaError_t launch_simple(const MapDev &m, const TrackSet &ts, const uint32_t *f3, const double *tau, uint64_t n,
+                          double *out, int *err, cudaStream_t st)
+{
+    switch (m.wmode) {
+    case WMODE_CONST: return launch_simple_W<WMODE_CONST, EXPLICIT>(m, ts, f3, tau, n, out, err, st);
+    case WMODE_FREQ: return launch_simple_W<WMODE_FREQ, EXPLICIT>(m, ts, f3, tau, n, out, err, st);
+    default: return launch_simple_W<WMODE_PIXEL, EXPLICIT>(m, ts, f3, tau, n, out, err, st);
+    }
+}
+
+// ------------------------------------------------------------------ template-params kernel
+__global__ void track_params_kernel(MapDev m, TrackSet ts, uint64_t g, uint32_t *f_out, double *tau_out,
+                                    int32_t *bins)
+{
+    uint32_t f[3];
+    double tau;
+    draw_track(ts.seed, g, (uint32_t)m.n_f, ts.tau_max, f, tau);
+    if (threadIdx.x == 0) {
+        f_out[0] = f[0]; f_out[1] = f[1]; f_out[2] = f[2];
+        *tau_out = tau;
+    }
+    if (!bins) return;
+    for (int j = threadIdx.x; j < m.n_t; j += blockDim.x)
+        bins[j] = (int32_t)raster_bin_wide(f[0], f[1], f[2], m.M, (uint32_t)j, m.d);
+}
+
+}  // namespace
+
+cudaError_t launch_score_generated(const MapDev &m, const TrackSet &ts, double *out, int *err, const Tuning &tu,
+                                   int num_sms, size_t smem_optin, cudaStream_t st, ScorePlan *plan)
+{
+    ScorePlan p{};
+    const uint64_t n = ts.n;
+    const uint64_t work = n * (uint64_t)m.n_t;
+    int kernel = tu.kernel;
+    if (kernel == 0) kernel = (!m.fast32 || work < (1ull << 24)) ? 1 : 2;
+    if (kernel == 2 && !m.fast32) kernel = 1;
+
+    if (kernel == 2) {
+        const size_t row_bytes = (size_t)m.ldr * 8;
+        const size_t wrow_bytes = m.wmode == WMODE_PIXEL ? (size_t)m.ldw * 4 : 0;
+        const size_t wtab_bytes = m.wmode == WMODE_FREQ ? (size_t)((m.n_f + 3) / 4 * 4) * 4 : 0;
+        size_t budget = smem_optin;
+        if (tu.smem_kb > 0) budget = std::min(budget, (size_t)tu.smem_kb * 1024);
+        const int nstage = std::max(2, std::min(tu.nstage, 4));
+        const size_t fixed = wtab_bytes + 64;
+        long S = budget > fixed ? (long)((budget - fixed) / (nstage * (row_bytes + wrow_bytes))) : 0;
+        S = std::min<long>(S, m.n_t);
+        if (S < 1) {
+            kernel = 1;  // a single map row does not fit in shared memory
+        } else {
+            const int maxR = std::max(1, std::min(tu.max_R, 4));
+            const uint64_t cap = (uint64_t)maxR * kMaxThreads;
+            const uint64_t G = (uint64_t)std::max(1, num_sms);
+            const uint64_t per_cta = (n + G - 1) / G;
+            const uint64_t nb_per_cta = std::max<uint64_t>(1, (per_cta + cap - 1) / cap);
+            uint64_t nb = G * nb_per_cta;
+            uint64_t batch = (n + nb - 1) / nb;
+            if (batch < 32) batch = 32;
+            nb = (n + batch - 1) / batch;
+            int R, threads;
+            if (tu.threads > 0) {
+                threads = std::min(kMaxThreads, (tu.threads + 31) / 32 * 32);
+                R = (int)((batch + threads - 1) / threads);
+                if (R > maxR) {  // requested block too small for the batch: shrink the batch
+                    R = maxR;
+                    batch = (uint64_t)R * threads;
+                    nb = (n + batch - 1) / batch;
+                }
+            } else {
+                R = (int)std::min<uint64_t>((batch + kMaxThreads - 1) / kMaxThreads, (uint64_t)maxR);
+                threads = (int)(((batch + R - 1) / R + 31) / 32 * 32);
+            }
+            p.kernel = 2;
+            p.R = R;
+            p.threads = threads;
+            p.grid = (int)std::min<uint64_t>(G, nb);
+            p.S = (int)S;
+            p.nstage = nstage;
+            p.nslabs = (int)((m.n_t + S - 1) / S);
+            p.batch = batch;
+            p.nbatches = nb;
+            p.smem = (size_t)nstage * S * (row_bytes + wrow_bytes) + wtab_bytes + (size_t)nstage * 8;
+            StagedArgs sa;
+            sa.S = (int)S;
+            sa.nstage = nstage;
+            sa.nslabs = p.nslabs;
+            sa.batch = batch;
+            sa.nbatches = nb;
+            sa.slab_recs = (uint32_t)(S * m.ldr);
+            sa.slab_ws = m.wmode == WMODE_PIXEL ? (uint32_t)(S * m.ldw) : 0u;
+            sa.wtab_floats = m.wmode == WMODE_FREQ ? (uint32_t)((m.n_f + 3) / 4 * 4) : 0u;
+            if (plan) *plan = p;
+            switch (m.wmode) {
+            case WMODE_CONST:
+                return launch_staged_W<WMODE_CONST>(R, m, ts, sa, p.grid, threads, p.smem, out, err, st);
+            case WMODE_FREQ:
+                return launch_staged_W<WMODE_FREQ>(R, m, ts, sa, p.grid, threads, p.smem, out, err, st);
+            default:
+                return launch_staged_W<WMODE_PIXEL>(R, m, ts, sa, p.grid, threads, p.smem, out, err, st);
+            }
+        }
+    }
+    p.kernel = 1;
+    p.threads = 256;
+    p.grid = (int)std::min<uint64_t>((n + 255) / 256, 0x7fffffffull);
+    if (plan) *plan = p;
+    return launch_simple<false>(m, ts, nullptr, nullptr, n, out, err, st);
+}
+
+cudaError_t launch_score_explicit(const MapDev &m, const uint32_t *f3, const double *tau, uint64_t n, double *out,
+                                  int *err, cudaStream_t st)
+{
+    TrackSet ts{};
+    return launch_simple<true>(m, ts, f3, tau, n, out, err, st);
+}
+
+cudaError_t launch_track_params(const MapDev &m, const TrackSet &ts, uint64_t g, uint32_t *f_dev, double *tau_dev,
+                                int32_t *bins_dev, cudaStream_t st)
+{
+    track_params_kernel<<<1, 256, 0, st>>>(m, ts, g, f_dev, tau_dev, bins_dev);
+    return cudaGetLastError();
+}
+
+}  // namespace stk

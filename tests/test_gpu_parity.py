@@ -1,0 +1,338 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Bit-exact: template parameters and pixel bins.  Floating point: the per-template
+SNR bound of tests/_parity.py (1e-5 relative to the pixel-magnitude scale) and
+plain relative 1e-5 on selected top-k values; winning indices equal unless the
+oracle's own SNRs are closer than that.
+"""
+import numpy as np
+import pytest
+
+from _parity import RTOL, assert_snr_close, assert_topk_matches
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+import oracle  # noqa: E402
+import paper_1401_8060_b300 as stk  # noqa: E402
+from paper_1401_8060_b300 import _lib, synth  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_1401_8060_b300 import build
+    build.build()
+    c = stk.Context(0)
+    yield c
+    c.close()
+
+
+def rand_map(seed, n_t, n_f, mode):
+    """mode: 'pixel' (sigma per pixel), 'freq' (per frequency), 'const' (sigma = 1.7 everywhere)."""
+    rng = np.random.default_rng(seed)
+    if mode == "pixel":
+        sig = rng.uniform(0.4, 2.5, (n_t, n_f)).astype(np.float32)
+    elif mode == "freq":
+        sig = synth.sigma_powerlaw(40.0 + 0.5 * np.arange(n_f), 1.3)
+    else:
+        sig = np.full(n_f, 1.7, np.float32)
+    y = synth.noise_map(n_t, n_f, sig, int(rng.integers(1 << 30)))
+    return y, sig
+
+
+def load_both(ctx, y, sig, f_min, df, paper=False, host=False):
+    per_freq = sig.ndim == 1
+    if host:
+        m = ctx.load_map(y, sig, f_min, df, paper_mode=paper)
+    else:
+        m = ctx.load_map(torch.from_numpy(y).cuda(), torch.from_numpy(sig).cuda(), f_min, df, paper_mode=paper)
+    om = oracle.OracleMap(y, sig, f_min, df, per_freq, paper_mode=paper)
+    return m, om
+
+
+def oracle_params(seed, offset, n, n_f, tau_max):
+    f3, tau = zip(*[oracle.track_params(seed, offset + i, n_f, tau_max) for i in range(n)])
+    return np.array(f3, dtype=np.uint32), np.array(tau)
+
+
+# ------------------------------------------------------------------ bit-exact pieces
+@pytest.mark.parametrize("n_t,n_f", [(200, 100), (500, 1600), (1000, 2000), (1000, 2200), (2, 1), (3, 7)])
+def test_track_params_and_bins_bit_exact(ctx, n_t, n_f):
+    y = np.zeros((n_t, n_f), np.complex64)
+    m = ctx.load_map(torch.from_numpy(y).cuda(), torch.ones(n_f, device="cuda"), 10.0, 1.0)
+    ctx.set_tracks(1, seed=12345, offset=0, tau_max=0.01)
+    for g in [0, 1, 7, 99991, 2 ** 33 + 5, 2 ** 64 - 1]:
+        f, tau, bins = ctx.track_params(m, g)
+        fo, tauo = oracle.track_params(12345, g, n_f, 0.01)
+        assert f == fo and tau == tauo, (g, f, fo, tau, tauo)
+        np.testing.assert_array_equal(bins, oracle.track_bins(fo, n_t))
+
+
+@pytest.mark.parametrize("mode", ["pixel", "freq", "const"])
+@pytest.mark.parametrize("paper", [False, True])
+def test_explicit_bruteforce_tiny(ctx, mode, paper):
+    """Every template (f0, f1, f2) on a 5 x 6 map, at several delays."""
+    n_t, n_f = 5, 6
+    y, sig = rand_map(3, n_t, n_f, mode)
+    m, om = load_both(ctx, y, sig, 100.0, 1.0, paper)
+    trip = np.array([(a, b, c) for a in range(n_f) for b in range(n_f) for c in range(n_f)], np.uint32)
+    for tau in [-0.0099, -0.003, 0.0, 0.0021, 0.0099]:
+        taus = np.full(len(trip), tau)
+        g = ctx.score_explicit(m, torch.from_numpy(trip.astype(np.int32)), torch.from_numpy(taus)).cpu().numpy()
+        o, ex = om.score_explicit(trip, taus, extras=True)
+        assert_snr_close(g, o, ex, paper, n_t, what=f"explicit {mode} paper={paper} tau={tau}")
+    ctx.sync()
+
+
+# ------------------------------------------------------------------ full scoring, both kernels
+@pytest.mark.parametrize("kernel", [1, 2])
+@pytest.mark.parametrize("mode,paper", [("pixel", False), ("freq", False), ("const", False), ("pixel", True)])
+def test_score_all_matches_oracle(ctx, kernel, mode, paper):
+    """Sizes that span several template batches and time slabs with ragged tails."""
+    n_t, n_f, T, seed, off, tmax = 37, 203, 20011, 5, 1000, 0.01
+    y, sig = rand_map(10 + kernel, n_t, n_f, mode)
+    m, om = load_both(ctx, y, sig, 40.0, 0.5, paper)
+    ctx.set_option(_lib.STK_OPT_KERNEL, kernel)
+    ctx.set_option(_lib.STK_OPT_SMEM_KB, 24)   # small budget: several slabs per map
+    try:
+        ctx.set_tracks(T, seed, off, tmax)
+        g = ctx.score_all(m).cpu().numpy()
+        plan = ctx.last_plan()
+        assert plan["kernel"] == kernel
+        if kernel == 2:
+            assert plan["S"] < n_t and plan["nbatches"] > 1
+    finally:
+        ctx.set_option(_lib.STK_OPT_KERNEL, 0)
+        ctx.set_option(_lib.STK_OPT_SMEM_KB, 0)
+    ctx.sync()
+    f3, tau = oracle_params(seed, off, T, n_f, tmax)
+    o, ex = om.score_explicit(f3, tau, extras=True)
+    np.testing.assert_array_equal(o, om.score_range(seed, off, T, tmax))
+    assert_snr_close(g, o, ex, paper, n_t, what=f"score_all kernel={kernel} {mode}")
+
+
+def test_wide_rasteriser_map(ctx):
+    """A map whose Bezier numerators exceed 32 bits (1000 x 2200): the 64-bit path."""
+    n_t, n_f, T = 1000, 2200, 3000
+    y, sig = rand_map(23, n_t, n_f, "freq")
+    m, om = load_both(ctx, y, sig, 40.0, 0.5)
+    ctx.set_tracks(T, 6, 0, 0.01)
+    g = ctx.score_all(m).cpu().numpy()
+    assert ctx.last_plan()["kernel"] == 1
+    f3, tau = oracle_params(6, 0, T, n_f, 0.01)
+    o, ex = om.score_explicit(f3, tau, extras=True)
+    assert_snr_close(g, o, ex, False, n_t, what="wide map")
+
+
+def test_kernels_agree_bitwise(ctx):
+    """Simple and slab kernels, and explicit scoring, run the same per-template
+    arithmetic in the same order: identical doubles."""
+    n_t, n_f, T = 61, 517, 9000
+    y, sig = rand_map(21, n_t, n_f, "freq")
+    m, _ = load_both(ctx, y, sig, 40.0, 0.5)
+    ctx.set_tracks(T, 9, 0, 0.01)
+    res = []
+    for kernel, smem in [(1, 0), (2, 0), (2, 40), (2, 20)]:
+        ctx.set_option(_lib.STK_OPT_KERNEL, kernel)
+        ctx.set_option(_lib.STK_OPT_SMEM_KB, smem)
+        res.append(ctx.score_all(m).cpu().numpy())
+    ctx.set_option(_lib.STK_OPT_KERNEL, 0)
+    ctx.set_option(_lib.STK_OPT_SMEM_KB, 0)
+    f3, tau = oracle_params(9, 0, T, n_f, 0.01)
+    res.append(ctx.score_explicit(m, torch.from_numpy(f3.astype(np.int32)), torch.from_numpy(tau)).cpu().numpy())
+    for r in res[1:]:
+        np.testing.assert_array_equal(r, res[0])
+
+
+@pytest.mark.parametrize("threads,max_r,stages", [(64, 1, 2), (96, 3, 3), (1024, 4, 4), (512, 2, 2)])
+def test_launch_shapes_agree(ctx, threads, max_r, stages):
+    n_t, n_f, T = 45, 300, 30001
+    y, sig = rand_map(22, n_t, n_f, "pixel")
+    m, _ = load_both(ctx, y, sig, 40.0, 0.5)
+    ctx.set_tracks(T, 4, 17, 0.01)
+    ctx.set_option(_lib.STK_OPT_KERNEL, 1)
+    ref = ctx.score_all(m).cpu().numpy()
+    ctx.set_option(_lib.STK_OPT_KERNEL, 2)
+    ctx.set_option(_lib.STK_OPT_THREADS, threads)
+    ctx.set_option(_lib.STK_OPT_MAX_R, max_r)
+    ctx.set_option(_lib.STK_OPT_STAGES, stages)
+    ctx.set_option(_lib.STK_OPT_SMEM_KB, 30)
+    try:
+        got = ctx.score_all(m).cpu().numpy()
+        plan = ctx.last_plan()
+        assert plan["kernel"] == 2 and plan["threads"] == threads and plan["R"] <= max_r
+    finally:
+        for o, v in [(_lib.STK_OPT_KERNEL, 0), (_lib.STK_OPT_THREADS, 0), (_lib.STK_OPT_MAX_R, 4),
+                     (_lib.STK_OPT_STAGES, 2), (_lib.STK_OPT_SMEM_KB, 0)]:
+            ctx.set_option(o, v)
+    np.testing.assert_array_equal(got, ref)
+
+
+# ------------------------------------------------------------------ top-k
+def test_tiny_workload_topk(ctx):
+    """The 200 x 100 workload: 10^4 templates, k = 16, against the full oracle."""
+    w = synth.WORKLOADS["tiny"]
+    fm = synth.tiny_map()
+    m, om = load_both(ctx, fm.y, fm.sigma, fm.f_min, fm.df)
+    ctx.set_tracks(w["n_tracks"], w["seed"], 0, w["tau_max"])
+    hits = ctx.score(m, w["k"])
+    o = om.score_range(w["seed"], 0, w["n_tracks"], w["tau_max"])
+    assert_topk_matches(hits, o, 0, w["k"], what="tiny top-k")
+    f3, tau = oracle_params(w["seed"], 0, w["n_tracks"], fm.n_f, w["tau_max"])
+    for h in hits:  # parameters of each hit are the template's own
+        i = int(h["index"])
+        assert tuple(int(v) for v in h["f"]) == tuple(int(v) for v in f3[i]) and h["tau"] == tau[i]
+    # all SNRs too
+    g = ctx.score_all(m).cpu().numpy()
+    _, ex = om.score_explicit(f3, tau, extras=True)
+    assert_snr_close(g, o, ex, False, fm.n_t, what="tiny all")
+
+
+@pytest.mark.parametrize("k", [1, 2, 100, 1024, 4096])
+def test_topk_sizes_and_device_output(ctx, k):
+    n_t, n_f, T = 50, 400, 50000
+    y, sig = rand_map(31, n_t, n_f, "freq")
+    m, om = load_both(ctx, y, sig, 40.0, 0.5)
+    ctx.set_tracks(T, 77, 3, 0.01)
+    out = torch.zeros(k * 40, dtype=torch.uint8, device="cuda")
+    ctx.score(m, k, out=out)
+    ctx.sync()
+    hits = out.cpu().numpy().view(stk.HIT_DTYPE)
+    o = om.score_range(77, 3, T, 0.01)
+    assert_topk_matches(hits, o, 3, k, what=f"k={k}")
+    host_hits = ctx.score(m, k)
+    np.testing.assert_array_equal(host_hits, hits)
+
+
+def test_split_ranges_merge_exactly(ctx):
+    """Sec. V: runs over disjoint template ranges combine by taking the largest."""
+    n_t, n_f, T, k = 80, 300, 40000, 64
+    y, sig = rand_map(41, n_t, n_f, "pixel")
+    m, _ = load_both(ctx, y, sig, 40.0, 0.5)
+    ctx.set_tracks(T, 5, 0, 0.01)
+    full = ctx.score(m, k)
+    parts = []
+    for lo, hi in [(0, 12345), (12345, 30000), (30000, T)]:
+        ctx.set_tracks(hi - lo, 5, lo, 0.01)
+        parts.append(ctx.score(m, k))
+    allh = np.concatenate(parts)
+    order = np.lexsort((allh["index"], -allh["snr"]))[:k]
+    np.testing.assert_array_equal(allh[order], full)
+
+
+def test_constant_map_ties_take_smallest_index(ctx):
+    n_t, n_f = 20, 30
+    y = np.full((n_t, n_f), 1 + 0j, np.complex64)
+    m = ctx.load_map(torch.from_numpy(y).cuda(), torch.ones(n_f, device="cuda"), 0.0, 1.0)
+    ctx.set_tracks(5000, 1, 1000, 0.0)      # tau = 0: every template scores exactly sqrt(n_t)
+    hits = ctx.score(m, 10)
+    np.testing.assert_array_equal(hits["index"], np.arange(1000, 1010))
+    assert np.all(hits["snr"] == hits["snr"][0])
+    assert abs(hits["snr"][0] - np.sqrt(n_t)) <= 1e-6 * np.sqrt(n_t)
+
+
+# ------------------------------------------------------------------ closed forms through the GPU
+def test_zero_noise_injection_snr(ctx):
+    """Signal on template g's own pixels only, with its own delay: SNR = A sqrt(W)."""
+    n_t, n_f = 120, 700
+    sig = synth.sigma_powerlaw(40.0 + 0.5 * np.arange(n_f))
+    y = np.zeros((n_t, n_f), np.complex64)
+    m0 = ctx.load_map(torch.from_numpy(y).cuda(), torch.from_numpy(sig).cuda(), 40.0, 0.5)
+    ctx.set_tracks(1, 8, 0, 0.01)
+    f, tau, bins = ctx.track_params(m0, 4242)
+    A = 3.0
+    synth.inject(y, bins, A, tau, 40.0, 0.5)
+    m = ctx.load_map(torch.from_numpy(y).cuda(), torch.from_numpy(sig).cuda(), 40.0, 0.5)
+    W = float(np.sum(sig.astype(np.float64)[bins] ** -2.0))
+    g = ctx.score_explicit(m, torch.tensor([list(f)], dtype=torch.int32), torch.tensor([tau])).cpu().numpy()[0]
+    assert g == pytest.approx(A * np.sqrt(W), rel=RTOL)
+
+
+def test_single_frequency_delay_ratio(ctx):
+    """Eq. 3 on the GPU: R = cos(2 pi f dtau) for a constant-frequency signal."""
+    n_t, n_f, c = 64, 1000, 440
+    tau_s = 0.0012
+    y = np.zeros((n_t, n_f), np.complex64)
+    y[:, c] = np.complex64(np.exp(-2j * np.pi * c * tau_s))
+    m = ctx.load_map(torch.from_numpy(y).cuda(), torch.ones(n_f, device="cuda"), 0.0, 1.0)
+    dts = np.array([0.0, -0.004, -0.0005, 0.0001, 0.0007, 0.003])
+    g = ctx.score_explicit(m, torch.tensor([[c, c, c]] * len(dts), dtype=torch.int32),
+                           torch.from_numpy(tau_s + dts)).cpu().numpy()
+    np.testing.assert_allclose(g / g[0], np.cos(2 * np.pi * c * dts), atol=3e-6)
+
+
+# ------------------------------------------------------------------ host pointers, errors
+def test_host_and_device_maps_identical(ctx):
+    y, sig = rand_map(51, 33, 77, "pixel")
+    mh, _ = load_both(ctx, y, sig, 40.0, 0.5, host=True)
+    md, _ = load_both(ctx, y, sig, 40.0, 0.5, host=False)
+    ctx.set_tracks(3000, 1, 0, 0.01)
+    np.testing.assert_array_equal(ctx.score_all(mh).cpu().numpy(), ctx.score_all(md).cpu().numpy())
+
+
+def test_invalid_inputs_rejected(ctx):
+    L = _lib
+    y = np.ones((10, 8), np.complex64)
+    s = np.ones(8, np.float32)
+    for bad_y, bad_s in [(y.copy(), np.zeros(8, np.float32)), (y.copy(), -s), (y.copy(), s * np.inf)]:
+        with pytest.raises(stk.StkError) as e:
+            ctx.load_map(bad_y, bad_s, 40.0, 0.5)
+        assert e.value.code == L.STK_EINVAL
+    ynan = y.copy()
+    ynan[3, 4] = np.nan
+    with pytest.raises(stk.StkError):
+        ctx.load_map(ynan, s, 40.0, 0.5)
+    with pytest.raises(stk.StkError):
+        ctx.load_map(np.ones((1, 8), np.complex64), s, 40.0, 0.5)   # n_t < 2
+    with pytest.raises(stk.StkError):
+        ctx.load_map(y, s, 40.0, 0.0)                               # df <= 0
+    m = ctx.load_map(y, s, 40.0, 0.5)
+    with pytest.raises(stk.StkError):
+        ctx.set_tracks(0, 1, 0, 0.01)
+    with pytest.raises(stk.StkError):
+        ctx.set_tracks(10, 1, 0, -1.0)
+    ctx.set_tracks(10, 1, 0, 0.01)
+    for k in [0, 11, 5000]:
+        with pytest.raises(stk.StkError):
+            ctx.score(m, k)
+    # an explicit template outside the map is reported at the next sync
+    ctx.score_explicit(m, torch.tensor([[1, 2, 8]], dtype=torch.int32), torch.tensor([0.0]))
+    with pytest.raises(stk.StkError) as e:
+        ctx.sync()
+    assert e.value.code == L.STK_EINVAL
+    ctx.sync()   # cleared
+
+
+# ------------------------------------------------------------------ full-size workload, sampled
+@pytest.mark.slow
+def test_realistic_workload_sampled(ctx):
+    """500 x 1600 map, 5 x 10^6 templates, k = 1024, in the benchmark's launch
+    configuration; the oracle checks a sample of templates one by one, every
+    selected template, and the selection against the GPU's own full SNR array."""
+    w = synth.WORKLOADS["realistic"]
+    fm = synth.realistic_map()
+    m, om = load_both(ctx, fm.y, fm.sigma, fm.f_min, fm.df)
+    ctx.set_tracks(w["n_tracks"], w["seed"], 0, w["tau_max"])
+    hits = ctx.score(m, w["k"])
+    plan = ctx.last_plan()
+    assert plan["kernel"] == 2
+    allg = ctx.score_all(m).cpu().numpy()
+    # selection is exactly the top-k of the GPU's own SNRs
+    order = np.lexsort((np.arange(allg.size), -allg))[:w["k"]]
+    np.testing.assert_array_equal(hits["index"], order)
+    np.testing.assert_array_equal(hits["snr"], allg[order])
+    # sampled templates and every selected template against the oracle
+    rng = np.random.default_rng(0)
+    idx = np.unique(np.concatenate([rng.integers(0, w["n_tracks"], 20000), order]))
+    f3 = np.zeros((idx.size, 3), np.uint32)
+    tau = np.zeros(idx.size)
+    for j, i in enumerate(idx):
+        f, t = oracle.track_params(w["seed"], int(i), fm.n_f, w["tau_max"])
+        f3[j], tau[j] = f, t
+    o, ex = om.score_explicit(f3, tau, extras=True)
+    assert_snr_close(allg[idx], o, ex, False, fm.n_t, what="realistic sample")
+    sel = np.searchsorted(idx, order)
+    np.testing.assert_allclose(hits["snr"], o[sel], rtol=RTOL)
