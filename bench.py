@@ -19,7 +19,6 @@ import hashlib
 import json
 import os
 import statistics
-import subprocess
 import sys
 import threading
 import time
@@ -43,6 +42,8 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--tracks", type=int, default=0,
+                    help="profiling aid: templates per GPU other than the workload's 5e6 (reported in config)")
     ap.add_argument("--cpu-sample", type=int, default=400000,
                     help="templates per oracle sample (about 2e8 track-pixels, 10-20 s of one core)")
     return ap.parse_args()
@@ -54,59 +55,72 @@ def dist_env():
 
 
 class ClockSampler:
-    """nvidia-smi clock/throttle sampling while the timed region runs."""
+    """SM clock and throttle-reason samples (NVML reads, every ~2 ms) while the
+    timed region runs.  Read-only: no clock or power setting is touched."""
 
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
-              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    REASONS = [("hw_slowdown", "nvmlClocksEventReasonHwSlowdown"),
+               ("hw_thermal_slowdown", "nvmlClocksEventReasonHwThermalSlowdown"),
+               ("sw_thermal_slowdown", "nvmlClocksEventReasonSwThermalSlowdown"),
+               ("sw_power_cap", "nvmlClocksEventReasonSwPowerCap")]
 
-    def __init__(self, gpu_index):
-        self.gpu = gpu_index
-        self.proc = None
-        self.lines = []
+    def __init__(self, torch_device):
+        self.dev = torch_device
+        self.samples = []
+        self.max_mhz = None
+        self.err = None
+        self._stop = threading.Event()
+
+    def _handle(self, nv):
+        import torch
+        p = torch.cuda.get_device_properties(self.dev)
+        bus = "%08x:%02x:%02x.0" % (p.pci_domain_id, p.pci_bus_id, p.pci_device_id)
+        try:
+            return nv.nvmlDeviceGetHandleByPciBusId(bus)
+        except Exception:
+            return nv.nvmlDeviceGetHandleByIndex(0)
 
     def __enter__(self):
         try:
-            self.proc = subprocess.Popen(
-                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
-            self.t = threading.Thread(target=self._read, daemon=True)
+            import pynvml as nv
+            nv.nvmlInit()
+            self.nv = nv
+            self.h = self._handle(nv)
+            self.max_mhz = nv.nvmlDeviceGetMaxClockInfo(self.h, nv.NVML_CLOCK_SM)
+            self.t = threading.Thread(target=self._run, daemon=True)
             self.t.start()
-        except (OSError, FileNotFoundError):
-            self.proc = None
+        except Exception as e:  # no NVML: report no samples
+            self.err = repr(e)
+            self.nv = None
         return self
 
-    def _read(self):
-        for line in self.proc.stdout:
-            self.lines.append(line.strip())
+    def _run(self):
+        nv = self.nv
+        while not self._stop.is_set():
+            try:
+                mhz = nv.nvmlDeviceGetClockInfo(self.h, nv.NVML_CLOCK_SM)
+                rs = nv.nvmlDeviceGetCurrentClocksEventReasons(self.h)
+                self.samples.append((mhz, rs))
+            except Exception as e:
+                self.err = repr(e)
+                return
+            time.sleep(0.002)
 
     def __exit__(self, *a):
-        if self.proc:
-            self.proc.terminate()
-            try:
-                self.proc.wait(timeout=5)
-            except subprocess.TimeoutExpired:
-                self.proc.kill()
+        self._stop.set()
+        if self.nv:
+            self.t.join(timeout=5)
 
     def summary(self):
-        sm, mx, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
-            p = [x.strip() for x in ln.split(",")]
-            if len(p) < 9:
-                continue
-            try:
-                sm.append(float(p[1]))
-                mx.append(float(p[2]))
-            except ValueError:
-                continue
-            for n, v in zip(names, p[5:9]):
-                if v.lower() == "active":
-                    reasons.add(n)
-        if not sm:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
-                "samples": len(sm)}
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": self.max_mhz, "reasons": [], "samples": 0, "error": self.err}
+        reasons = set()
+        for _, rs in self.samples:
+            for name, attr in self.REASONS:
+                if rs & getattr(self.nv, attr):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(m for m, _ in self.samples), "sm_max_mhz": self.max_mhz,
+                "sm_min_mhz": min(m for m, _ in self.samples), "reasons": sorted(reasons),
+                "samples": len(self.samples), "source": "NVML, every ~2 ms during the timed region"}
 
 
 def kernel_source_hash():
@@ -197,7 +211,7 @@ def main():
 
     w = synth.WORKLOADS[WORKLOAD]
     fm = synth.realistic_map()
-    T, K = w["n_tracks"], w["k"]
+    T, K = (args.tracks or w["n_tracks"]), w["k"]
     stream = torch.cuda.current_stream()
     ctx = stk.Context(local, stream)
     m = ctx.load_map(torch.from_numpy(fm.y).cuda(), torch.from_numpy(fm.sigma).cuda(), fm.f_min, fm.df)
@@ -217,7 +231,7 @@ def main():
         dist.barrier()
     torch.cuda.synchronize()
     wall0 = time.perf_counter()
-    with ClockSampler(torch.cuda.current_device()) as clk:
+    with ClockSampler(local) as clk:
         for s in range(args.steps):
             flush.zero_()                    # evict the map from L2 between steps
             ev[s][0].record(stream)
@@ -288,6 +302,7 @@ def main():
             "config": {"workload": "realistic 500x1600 map (0.5 Hz bins from 40 Hz), per-frequency power-law sigma, "
                                    "one injected chirp; 5e6 Philox templates per GPU, tau in +-10 ms, k=1024",
                        "n_t": fm.n_t, "n_f": fm.n_f, "n_tracks_per_gpu": T, "k": K,
+                       "reduced_for_profiling": bool(args.tracks),
                        "l2": "flushed between steps (256 MB write)", "parallelism": f"template ranges x{world}"},
             "roofline": {"bound": "smem", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
