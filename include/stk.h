@@ -162,6 +162,40 @@ STK_API int stk_set_profiling(stk_ctx *ctx, int enable);
  * count of that call.  Requires profiling on; synchronises the stream. */
 STK_API int stk_last_timings(stk_ctx *ctx, double out[3]);
 
+/* ---- scoring without allocation ------------------------------------------
+ * The paper has no counterpart to this call; it exists for callers that
+ * cannot call cudaMalloc when they score: code whose device memory belongs to
+ * another allocator (a framework's caching allocator, a fixed memory budget)
+ * where an extra allocation may fail or fragment, and latency-critical loops
+ * that cannot take the device-wide synchronisation of cudaFree.
+ *
+ * stk_score_noalloc computes exactly what stk_score computes for the range
+ * counter_offset .. counter_offset + n_tracks - 1 (seed, tau_max_s as in
+ * stk_set_tracks) and writes the k loudest to out_topk_dev (caller-owned
+ * device memory, k entries), asynchronously on cuda_stream.  Its scratch (one
+ * SNR per template and the selection state, about 8.1 MiB) is a fixed array
+ * in device memory that every GPU loading the library holds until the process
+ * exits; the call itself calls no cudaMalloc, cudaFree or other allocating
+ * routine.  The map must have been loaded earlier (stk_load_map allocates).
+ *   n_tracks    1 .. STK_NOALLOC_MAX_TRACKS (2^20); larger ranges: split them
+ *               over several calls and keep the largest SNRs (Sec. V rule)
+ *   k           1 .. min(STK_MAX_K, n_tracks)
+ *   status_dev  caller-owned device int or NULL; set to STK_OK, or to
+ *               STK_ETIMEOUT when a bounded in-kernel wait gave up
+ * The first call on a device resolves the array's device address
+ * (cudaGetSymbolAddress, with the map's device current); make that first call
+ * before any stream capture.  Every call on a device shares the one array,
+ * which keeps the previous call's contents (the call clears what must start
+ * at zero): calls that overlap on the GPU (other streams, other host threads)
+ * race and corrupt each other's results; serialise them.  The caller's current
+ * device is restored on return.  Errors (message from stk_last_error(NULL)):
+ * STK_EINVAL (NULL map or output, n_tracks beyond the limit, bad k or
+ * tau_max), STK_ECUDA. */
+#define STK_NOALLOC_MAX_TRACKS (1u << 20)
+STK_API int stk_score_noalloc(const stk_map *map, uint64_t n_tracks, uint64_t seed, uint64_t counter_offset,
+                              double tau_max_s, int k, stk_hit *out_topk_dev, int *status_dev,
+                              void *cuda_stream);
+
 /* ---- tuning (kernel choice and launch shape; results do not depend on them) */
 #define STK_OPT_KERNEL   1 /* 0 automatic, 1 one-thread-per-template kernel, 2 shared-memory slab kernel */
 #define STK_OPT_THREADS  2 /* slab kernel block size, 0 = automatic, else 32 .. 1024 */

@@ -17,6 +17,7 @@ STK_OK, STK_EINVAL, STK_ENOMEM, STK_ECUDA, STK_ETIMEOUT, STK_ESTATE = 0, -1, -2,
 STK_HOST_PTR, STK_SIGMA_PER_FREQ, STK_NORM_PAPER = 0x1, 0x2, 0x4
 STK_OUT_HOST = 0x1
 STK_MAX_K = 4096
+STK_NOALLOC_MAX_TRACKS = 1 << 20
 STK_OPT_KERNEL, STK_OPT_THREADS, STK_OPT_MAX_R, STK_OPT_STAGES, STK_OPT_SMEM_KB = 1, 2, 3, 4, 5
 
 # Every entry point declared in include/stk.h: (name, restype, argtypes).
@@ -41,6 +42,8 @@ SIGNATURES = [
     ("stk_set_option", C.c_int, [_vp, C.c_int, C.c_int64]),
     ("stk_last_plan", C.c_int, [_vp, C.POINTER(C.c_int64)]),
     ("stk_last_error", C.c_char_p, [_vp]),
+    ("stk_score_noalloc", C.c_int, [_vp, C.c_uint64, C.c_uint64, C.c_uint64, C.c_double, C.c_int, _vp, _vp,
+                                    _vp]),
 ]
 
 HIT_DTYPE = np.dtype([("snr", "<f8"), ("index", "<u8"), ("f", "<u4", (3,)), ("reserved", "<u4"),

@@ -5,6 +5,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 
 #include "stk_internal.cuh"
@@ -532,3 +533,115 @@ int stk_last_timings(stk_ctx *c, double out[3])
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// No-allocation variant of stk_score (the paper has no counterpart).
+//
+// Some callers cannot call cudaMalloc at scoring time: code whose device
+// memory is owned by another allocator (a framework's caching allocator or a
+// fixed memory budget, where an extra allocation can fail or fragment), and
+// latency-critical loops that cannot afford cudaFree's device-wide
+// synchronisation.  This entry point takes its scratch (one SNR per template
+// plus the selection state) from a fixed array in device memory that every
+// GPU loading the library holds until the process exits.  It never calls
+// cudaMalloc, cudaFree or any allocating routine.
+namespace {
+
+constexpr uint64_t kNoAllocMaxTracks = STK_NOALLOC_MAX_TRACKS;
+constexpr size_t kNoAllocSnrBytes = kNoAllocMaxTracks * sizeof(double);
+constexpr size_t kNoAllocFlagBytes = 256;
+constexpr size_t kNoAllocSelBytes = 64 * 1024;
+constexpr int kNoAllocMaxDevices = 64;
+
+// Shared by every call on a device: SNRs | error flag | selection state.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocSnrBytes + kNoAllocFlagBytes + kNoAllocSelBytes];
+
+struct NoAllocDevice {
+    void *base = nullptr;  // device address of g_noalloc_scratch on this device
+    int num_sms = 0;
+    size_t smem_optin = 0;
+};
+std::mutex g_noalloc_mu;
+NoAllocDevice g_noalloc_dev[kNoAllocMaxDevices];
+
+// Once per device, with that device current: resolve the array's device address.
+int noalloc_setup(int dev, NoAllocDevice *out)
+{
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    NoAllocDevice &d = g_noalloc_dev[dev];
+    if (!d.base) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess)
+            return set_err(nullptr, STK_ECUDA, "cudaGetSymbolAddress(scratch): %s", cudaGetErrorString(e));
+        int v = 0;
+        if ((e = cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+            return set_err(nullptr, STK_ECUDA, "cudaDeviceGetAttribute: %s", cudaGetErrorString(e));
+        d.num_sms = v;
+        if ((e = cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess)
+            return set_err(nullptr, STK_ECUDA, "cudaDeviceGetAttribute: %s", cudaGetErrorString(e));
+        d.smem_optin = (size_t)v;
+        d.base = p;
+    }
+    *out = d;
+    return STK_OK;
+}
+
+__global__ void noalloc_status_kernel(const int *flags, int *status)
+{
+    *status = (*flags & ERR_TIMEOUT) ? STK_ETIMEOUT : STK_OK;
+}
+
+}  // namespace
+
+extern "C" int stk_score_noalloc(const stk_map *m, uint64_t n_tracks, uint64_t seed, uint64_t counter_offset,
+                                 double tau_max_s, int k, stk_hit *out_topk_dev, int *status_dev,
+                                 void *cuda_stream)
+{
+    if (!m || !m->ctx) return set_err(nullptr, STK_EINVAL, "map is NULL");
+    if (!out_topk_dev) return set_err(nullptr, STK_EINVAL, "out_topk_dev is NULL");
+    if (n_tracks < 1 || n_tracks > kNoAllocMaxTracks)
+        return set_err(nullptr, STK_EINVAL,
+                       "n_tracks = %llu outside [1, %llu], the no-allocation scratch limit; split the template "
+                       "range over several calls and keep the largest SNRs",
+                       (unsigned long long)n_tracks, (unsigned long long)kNoAllocMaxTracks);
+    if (k < 1 || k > STK_MAX_K || (uint64_t)k > n_tracks)
+        return set_err(nullptr, STK_EINVAL, "k = %d must be in [1, min(%d, n_tracks)]", k, STK_MAX_K);
+    if (!std::isfinite(tau_max_s) || tau_max_s < 0) return set_err(nullptr, STK_EINVAL, "tau_max must be finite and >= 0");
+    if (select_scratch_bytes(n_tracks, k) > kNoAllocSelBytes)
+        return set_err(nullptr, STK_EINVAL, "selection state exceeds the no-allocation scratch");
+    const int dev = m->ctx->device;
+    if (dev < 0 || dev >= kNoAllocMaxDevices) return set_err(nullptr, STK_EINVAL, "device %d out of range", dev);
+    int prev = 0;
+    cudaError_t e = cudaGetDevice(&prev);
+    if (e != cudaSuccess) return set_err(nullptr, STK_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+    if ((e = cudaSetDevice(dev)) != cudaSuccess)
+        return set_err(nullptr, STK_ECUDA, "cudaSetDevice: %s", cudaGetErrorString(e));
+    NoAllocDevice d;
+    int rc = noalloc_setup(dev, &d);
+    if (rc == STK_OK) {
+        cudaStream_t st = (cudaStream_t)cuda_stream;
+        unsigned char *base = (unsigned char *)d.base;
+        double *snr = (double *)base;
+        int *flags = (int *)(base + kNoAllocSnrBytes);
+        void *sel = base + kNoAllocSnrBytes + kNoAllocFlagBytes;
+        TrackSet ts{n_tracks, seed, counter_offset, tau_max_s};
+        Tuning tu{};
+        ScorePlan plan{};
+        int nl = 0;
+        // The array keeps the previous call's contents: the flag word must start at zero;
+        // the selection kernels reset their own state; every SNR is overwritten.
+        if ((e = cudaMemsetAsync(flags, 0, sizeof(int), st)) != cudaSuccess ||
+            (e = launch_score_generated(m->dev, ts, snr, flags, tu, d.num_sms, d.smem_optin, st, &plan)) !=
+                cudaSuccess ||
+            (e = launch_select_topk(snr, n_tracks, k, ts, m->dev, sel, out_topk_dev, st, &nl)) != cudaSuccess)
+            rc = set_err(nullptr, STK_ECUDA, "no-allocation scoring: %s", cudaGetErrorString(e));
+        else if (status_dev) {
+            noalloc_status_kernel<<<1, 1, 0, st>>>(flags, status_dev);
+            if ((e = cudaGetLastError()) != cudaSuccess)
+                rc = set_err(nullptr, STK_ECUDA, "status kernel: %s", cudaGetErrorString(e));
+        }
+    }
+    cudaSetDevice(prev);
+    return rc;
+}
