@@ -54,6 +54,55 @@ def dist_env():
         int(os.environ.get("LOCAL_RANK", "0"))
 
 
+class _NvmlCtypes:
+    """The few read-only NVML calls the sampler needs, through the driver's
+    libnvidia-ml.so.1, for hosts without the pynvml module."""
+
+    NVML_CLOCK_SM = 1
+    nvmlClocksEventReasonSwPowerCap = 0x4
+    nvmlClocksEventReasonHwSlowdown = 0x8
+    nvmlClocksEventReasonSwThermalSlowdown = 0x20
+    nvmlClocksEventReasonHwThermalSlowdown = 0x40
+
+    def __init__(self):
+        import ctypes
+        self.C = ctypes
+        self.lib = ctypes.CDLL("libnvidia-ml.so.1")
+        self._ok(self.lib.nvmlInit_v2())
+
+    def _ok(self, rc):
+        if rc != 0:
+            raise RuntimeError(f"NVML error {rc}")
+
+    def nvmlDeviceGetHandleByPciBusId(self, bus):
+        h = self.C.c_void_p()
+        self._ok(self.lib.nvmlDeviceGetHandleByPciBusId_v2(bus.encode(), self.C.byref(h)))
+        return h
+
+    def nvmlDeviceGetHandleByIndex(self, i):
+        h = self.C.c_void_p()
+        self._ok(self.lib.nvmlDeviceGetHandleByIndex_v2(self.C.c_uint(i), self.C.byref(h)))
+        return h
+
+    def _clock(self, fn, h, kind):
+        v = self.C.c_uint()
+        self._ok(fn(h, self.C.c_int(kind), self.C.byref(v)))
+        return v.value
+
+    def nvmlDeviceGetClockInfo(self, h, kind):
+        return self._clock(self.lib.nvmlDeviceGetClockInfo, h, kind)
+
+    def nvmlDeviceGetMaxClockInfo(self, h, kind):
+        return self._clock(self.lib.nvmlDeviceGetMaxClockInfo, h, kind)
+
+    def nvmlDeviceGetCurrentClocksEventReasons(self, h):
+        v = self.C.c_ulonglong()
+        fn = getattr(self.lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            self.lib.nvmlDeviceGetCurrentClocksThrottleReasons
+        self._ok(fn(h, self.C.byref(v)))
+        return v.value
+
+
 class ClockSampler:
     """SM clock and throttle-reason samples (NVML reads, every ~2 ms) while the
     timed region runs.  Read-only: no clock or power setting is touched."""
@@ -81,8 +130,11 @@ class ClockSampler:
 
     def __enter__(self):
         try:
-            import pynvml as nv
-            nv.nvmlInit()
+            try:
+                import pynvml as nv
+                nv.nvmlInit()
+            except ImportError:
+                nv = _NvmlCtypes()
             self.nv = nv
             self.h = self._handle(nv)
             self.max_mhz = nv.nvmlDeviceGetMaxClockInfo(self.h, nv.NVML_CLOCK_SM)

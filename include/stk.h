@@ -173,7 +173,7 @@ STK_API int stk_last_timings(stk_ctx *ctx, double out[3]);
  * counter_offset .. counter_offset + n_tracks - 1 (seed, tau_max_s as in
  * stk_set_tracks) and writes the k loudest to out_topk_dev (caller-owned
  * device memory, k entries), asynchronously on cuda_stream.  Its scratch (one
- * SNR per template and the selection state, about 8.1 MiB) is a fixed array
+ * SNR per template and the selection state, 9 MiB) is a fixed array
  * in device memory that every GPU loading the library holds until the process
  * exits; the call itself calls no cudaMalloc, cudaFree or other allocating
  * routine.  The map must have been loaded earlier (stk_load_map allocates).

@@ -366,6 +366,8 @@ int stk_load_map(stk_ctx *c, const void *y_c64, const float *sigma, int n_t, int
     } else {
         d.wmode = per_freq ? WMODE_FREQ : WMODE_PIXEL;
     }
+    d.norm = paper ? 1.0 / (double)n_t
+                   : (d.wmode == WMODE_CONST ? 1.0 / std::sqrt((double)n_t * (double)d.w_const) : 0.0);
     d.rec = (const uint2 *)m->rec_buf;
     d.w = d.wmode == WMODE_CONST ? nullptr : (const float *)m->w_buf;
     *out = m;
@@ -550,7 +552,7 @@ namespace {
 constexpr uint64_t kNoAllocMaxTracks = STK_NOALLOC_MAX_TRACKS;
 constexpr size_t kNoAllocSnrBytes = kNoAllocMaxTracks * sizeof(double);
 constexpr size_t kNoAllocFlagBytes = 256;
-constexpr size_t kNoAllocSelBytes = 64 * 1024;
+constexpr size_t kNoAllocSelBytes = 1024 * 1024;
 constexpr int kNoAllocMaxDevices = 64;
 
 // Shared by every call on a device: SNRs | error flag | selection state.

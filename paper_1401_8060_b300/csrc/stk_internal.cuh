@@ -8,6 +8,7 @@
 
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <string.h>
 
 #include "../../include/stk.h"
 
@@ -33,6 +34,7 @@ struct MapDev {
     int paper;        // 1: SNR = S / n_t
     float w_const;    // WMODE_CONST weight (sigma^-2), 1 in paper mode
     double f_min, df; // Hz
+    double norm;      // 1 / n_t (paper form) or 1 / sqrt(n_t w_const) (WMODE_CONST); else unused
     const uint2 *rec; // [n_t][ldr]
     const float *w;   // [n_f] (WMODE_FREQ) or [n_t][ldw] (WMODE_PIXEL), else null
     // Rasteriser: column j of template (f0, f1, f2) sits at bin floor(N_j / d) with
@@ -119,17 +121,46 @@ struct Phase {
     uint32_t a_lo, a_hi, b;
 };
 
-__device__ __forceinline__ Phase phase_consts(double f_min, double df, double tau)
+// frac(x * y) * 2^64 (unsigned, value - floor(value)), from the exact product of
+// two doubles in integer arithmetic: x = mx 2^ex, y = my 2^ey, x y = P 2^e with
+// P = mx my < 2^106.  Truncated to 2^-64 (negative products: within 2^-64).
+__host__ __device__ __forceinline__ uint64_t frac_prod_q64(double x, double y)
+{
+#ifdef __CUDA_ARCH__
+    const uint64_t bx = (uint64_t)__double_as_longlong(x), by = (uint64_t)__double_as_longlong(y);
+#else
+    uint64_t bx, by;
+    memcpy(&bx, &x, 8);
+    memcpy(&by, &y, 8);
+#endif
+    const int fx = (int)((bx >> 52) & 0x7ff), fy = (int)((by >> 52) & 0x7ff);
+    uint64_t mx = bx & 0xFFFFFFFFFFFFFull, my = by & 0xFFFFFFFFFFFFFull;
+    if (fx) mx |= 1ull << 52;
+    if (fy) my |= 1ull << 52;
+    if (mx == 0 || my == 0) return 0;
+    const int e = (fx ? fx : 1) - 1075 + (fy ? fy : 1) - 1075;
+    if (e >= 0) return 0;                       // an integer
+    uint64_t hi, lo;
+    mul64_hilo(mx, my, hi, lo);
+    const int s = -e;                           // value = P / 2^s
+    uint64_t q;
+    if (s < 64) q = lo << (64 - s);
+    else if (s == 64) q = lo;
+    else if (s < 128) q = (lo >> (s - 64)) | (hi << (128 - s));
+    else if (s < 192) q = hi >> (s - 128);
+    else q = 0;
+    if (((bx ^ by) >> 63) && q) q = 0 - q;      // frac(-v) = 1 - frac(v)
+    return q;
+}
+
+__host__ __device__ __forceinline__ Phase phase_consts(double f_min, double df, double tau)
 {
     Phase p;
-    double x = df * tau;
-    x -= floor(x);                                   // [0, 1), exact
-    const unsigned long long a = __double2ull_rz(x * 18446744073709551616.0);  // < 2^64
+    const uint64_t a = frac_prod_q64(df, tau);
+    const uint64_t b = frac_prod_q64(f_min, tau);
     p.a_lo = (uint32_t)a;
     p.a_hi = (uint32_t)(a >> 32);
-    double y = f_min * tau;
-    y -= floor(y);
-    p.b = (uint32_t)__double2ull_rn(y * 4294967296.0) + 0x100u;   // 2^32 wraps to 0: same angle
+    p.b = (uint32_t)((b + 0x80000000ull) >> 32) + 0x100u;
     return p;
 }
 

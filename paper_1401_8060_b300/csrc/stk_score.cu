@@ -24,12 +24,17 @@ namespace {
 constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s per slab wait
 constexpr int kMaxThreads = 1024;
 
+// Normalisation (Eq. 7 with the weighting of the footnote to Eq. 5), FP64 on the
+// GPU.  Weighted form with varying weights: S / sqrt(W), where 1 / sqrt(W) is an
+// FP32 seed refined by one Newton-Raphson step y1 = y0 (3 - W y0^2) / 2 in FP64
+// (relative error ~1e-13).  Constant weight or paper form: S times a constant.
 template <int WMODE>
 __device__ __forceinline__ double finalize_snr(float acc, float W, const MapDev &m)
 {
-    if (m.paper) return (double)acc / (double)m.n_t;
-    const double Wd = (WMODE == WMODE_CONST) ? (double)m.n_t * (double)m.w_const : (double)W;
-    return (double)acc / sqrt(Wd);
+    if (WMODE == WMODE_CONST || m.paper) return (double)acc * m.norm;
+    const double y0 = (double)rsqrtf(W);
+    const double t = (double)W * y0 * y0;
+    return (double)acc * (y0 * fma(-0.5, t, 1.5));
 }
 
 // ------------------------------------------------------------------ simple kernel

@@ -2,14 +2,17 @@
 // cluster", Sec. III, kept to k > 1 so runs can be merged, Sec. V).
 //
 // Exact and deterministic: order by SNR descending, then template index
-// ascending.  Steps, all on the device:
-//   1. radix select: eight passes of 8-bit digits over order-preserving 64-bit
-//      keys of the FP64 SNRs find the k-th largest key exactly;
-//   2. every template with a larger key is collected; of those equal to it, the
-//      ones with the smallest indices fill the remaining places (a block-ordered
-//      compaction over contiguous chunks keeps index order);
-//   3. the k survivors are sorted in shared memory (bitonic) and their
-//      parameters regenerated from their indices.
+// ascending.  The FP64 SNRs are mapped to order-preserving 64-bit keys.
+//   1. two histogram passes over the 12-bit digits key[63:52] and key[51:40]
+//      fix the 24-bit prefix of the k-th largest key;
+//   2. one pass collects every template whose key prefix is at least that one
+//      (the k winners plus the rest of the boundary bucket, usually a few
+//      thousand) into a candidate buffer;
+//   3. one block sorts the candidates in shared memory and keeps the first k.
+// When the boundary bucket is too large for that (many templates agreeing in
+// their top 24 key bits, e.g. a constant map), step 3 instead runs an exact
+// radix select over the keys and then over the indices of the tied keys, in
+// one block, on the full SNR array.
 #include <cstdint>
 
 #include "stk_internal.cuh"
@@ -18,16 +21,19 @@ namespace stk {
 
 namespace {
 
-constexpr int kHistThreads = 512;
-constexpr int kMaxChunks = 1024;
+constexpr int kBins = 4096;           // 12-bit digits
+constexpr int kPassThreads = 512;
+constexpr int kFinalThreads = 1024;
+constexpr uint32_t kCandCap = 65536;  // candidate buffer
+constexpr int kSortCap = 8192;        // candidates sorted in shared memory
 
 struct SelState {
-    unsigned long long prefix;  // digits fixed so far (the k-th key once all passes ran)
-    unsigned long long mask;
-    unsigned int krem;          // places still to fill from keys equal to the prefix
-    unsigned int n_gt;          // keys strictly greater than the k-th, collected
-    unsigned int pad0, pad1;
-    unsigned int hist[256];
+    unsigned int hist[kBins];
+    unsigned int d1, d2;   // digits of the k-th key's 24-bit prefix
+    unsigned int krem;     // places left for keys sharing the prefix being resolved
+    unsigned int ncand;    // candidates collected
+    unsigned int overflow; // candidates exceeded kCandCap
+    unsigned int pad[3];
 };
 
 __device__ __forceinline__ unsigned long long order_key(double x)
@@ -37,144 +43,131 @@ __device__ __forceinline__ unsigned long long order_key(double x)
     return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
 }
 
-__global__ void sel_init(SelState *st, unsigned int k)
+// Block-wide: given hist[0..nbins) in shared or global memory, find the digit d
+// with above(d) < krem <= above(d) + hist[d], where above(d) = sum of bins > d.
+// Returns d and the places left inside bin d (krem - above(d)) through smem.
+// nbins must be a multiple of blockDim.x.
+__device__ void pick_digit(const unsigned int *hist, int nbins, unsigned int krem, unsigned int *out_d,
+                           unsigned int *out_krem)
 {
-    const int t = threadIdx.x;
-    if (t == 0) {
-        st->prefix = 0;
-        st->mask = 0;
-        st->krem = k;
-        st->n_gt = 0;
+    __shared__ unsigned int warp_sum[32];
+    const int per = nbins / blockDim.x;
+    const int t = threadIdx.x, lane = t & 31, wid = t >> 5, nw = blockDim.x >> 5;
+    unsigned int mine = 0;
+    for (int i = 0; i < per; ++i) mine += hist[t * per + i];
+    // exclusive suffix sum over threads: sum of bins owned by threads > t
+    unsigned int incl = mine;
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned int v = __shfl_down_sync(0xffffffffu, incl, o);
+        if (lane + o < 32) incl += v;
     }
-    for (int i = t; i < 256; i += blockDim.x) st->hist[i] = 0;
+    if (lane == 0) warp_sum[wid] = incl;
+    __syncthreads();
+    unsigned int later_warps = 0;
+    for (int w = wid + 1; w < nw; ++w) later_warps += warp_sum[w];
+    unsigned int above = later_warps + incl - mine;
+    for (int i = per - 1; i >= 0; --i) {
+        const unsigned int d = (unsigned int)(t * per + i), c = hist[d];
+        if (above < krem && above + c >= krem) {
+            *out_d = d;
+            *out_krem = krem - above;
+        }
+        above += c;
+    }
+    __syncthreads();
 }
 
-__global__ void __launch_bounds__(kHistThreads) sel_hist(const double *__restrict__ snr, uint64_t n, SelState *st,
-                                                         int shift)
+__global__ void sel_init(SelState *st)
 {
-    __shared__ unsigned int h[256];
-    for (int i = threadIdx.x; i < 256; i += blockDim.x) h[i] = 0;
+    for (int i = threadIdx.x; i < kBins; i += blockDim.x) st->hist[i] = 0;
+    if (threadIdx.x == 0) {
+        st->ncand = 0;
+        st->overflow = 0;
+    }
+}
+
+// PASS 0: histogram of key[63:52]; PASS 1: of key[51:40] among keys with key[63:52] == d1.
+template <int PASS>
+__global__ void __launch_bounds__(kPassThreads) sel_hist(const double *__restrict__ snr, uint64_t n, SelState *st)
+{
+    __shared__ unsigned int h[kBins];
+    for (int i = threadIdx.x; i < kBins; i += blockDim.x) h[i] = 0;
     __syncthreads();
-    const unsigned long long prefix = st->prefix, mask = st->mask;
+    const unsigned int d1 = PASS ? st->d1 : 0u;
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
         const unsigned long long key = order_key(snr[i]);
-        if ((key & mask) == prefix) atomicAdd(&h[(key >> shift) & 255u], 1u);
+        if (PASS == 0) atomicAdd(&h[key >> 52], 1u);
+        else if ((unsigned int)(key >> 52) == d1) atomicAdd(&h[(key >> 40) & 4095u], 1u);
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < 256; i += blockDim.x)
+    for (int i = threadIdx.x; i < kBins; i += blockDim.x)
         if (h[i]) atomicAdd(&st->hist[i], h[i]);
 }
 
-// Fix the digit holding the krem-th largest key among those matching the prefix.
-__global__ void sel_pick(SelState *st, int shift)
+template <int PASS>
+__global__ void __launch_bounds__(kFinalThreads) sel_pick(SelState *st, unsigned int k)
 {
-    if (threadIdx.x != 0) return;
-    unsigned int above = 0, krem = st->krem;
-    int d = 255;
-    for (; d > 0; --d) {
-        const unsigned int c = st->hist[d];
-        if (above + c >= krem) break;
-        above += c;
-    }
-    st->krem = krem - above;
-    st->prefix |= (unsigned long long)d << shift;
-    st->mask |= 255ull << shift;
-    for (int i = 0; i < 256; ++i) st->hist[i] = 0;
-}
-
-// Collect keys > k-th into out_idx[0 .. n_gt); count keys == k-th per contiguous chunk.
-__global__ void __launch_bounds__(kHistThreads) sel_collect(const double *__restrict__ snr, uint64_t n,
-                                                            uint64_t chunk, SelState *st, unsigned int *out_idx,
-                                                            unsigned int *chunk_eq)
-{
-    __shared__ unsigned int ceq;
-    if (threadIdx.x == 0) ceq = 0;
-    __syncthreads();
-    const unsigned long long kth = st->prefix;
-    const uint64_t lo = (uint64_t)blockIdx.x * chunk;
-    const uint64_t hi = lo + chunk < n ? lo + chunk : n;
-    unsigned int eq = 0;
-    for (uint64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-        const unsigned long long key = order_key(snr[i]);
-        if (key > kth) out_idx[atomicAdd(&st->n_gt, 1u)] = (unsigned int)i;
-        eq += (key == kth);
-    }
-    if (eq) atomicAdd(&ceq, eq);
-    __syncthreads();
-    if (threadIdx.x == 0) chunk_eq[blockIdx.x] = ceq;
-}
-
-// Fill the remaining krem places with the lowest-index keys equal to the k-th.
-__global__ void __launch_bounds__(kHistThreads) sel_ties(const double *__restrict__ snr, uint64_t n, uint64_t chunk,
-                                                         const SelState *st, unsigned int *out_idx,
-                                                         const unsigned int *chunk_eq)
-{
-    __shared__ unsigned int warp_tot[kHistThreads / 32];
-    __shared__ unsigned int base_sh;
-    const unsigned int krem = st->krem, ngt = st->n_gt;
-    const unsigned long long kth = st->prefix;
-    // Equal keys before this chunk.
-    unsigned int before = 0;
-    for (unsigned int b = threadIdx.x; b < blockIdx.x; b += blockDim.x) before += chunk_eq[b];
-    for (int o = 16; o; o >>= 1) before += __shfl_xor_sync(0xffffffffu, before, o);
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    if (lane == 0) warp_tot[wid] = before;
-    __syncthreads();
+    __shared__ unsigned int d, kr;
+    const unsigned int krem = PASS ? st->krem : k;
+    pick_digit(st->hist, kBins, krem, &d, &kr);
     if (threadIdx.x == 0) {
-        unsigned int s = 0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += warp_tot[w];
-        base_sh = s;
+        if (PASS == 0) st->d1 = d;
+        else st->d2 = d;
+        st->krem = kr;
     }
     __syncthreads();
-    unsigned int base = base_sh;
-    if (base >= krem || chunk_eq[blockIdx.x] == 0) return;
-    const uint64_t lo = (uint64_t)blockIdx.x * chunk;
-    const uint64_t hi = lo + chunk < n ? lo + chunk : n;
-    for (uint64_t t0 = lo; t0 < hi && base < krem; t0 += blockDim.x) {
-        const uint64_t i = t0 + threadIdx.x;
-        const bool e = i < hi && order_key(snr[i]) == kth;
-        const unsigned int bal = __ballot_sync(0xffffffffu, e);
-        __syncthreads();  // warp_tot reuse
-        if (lane == 0) warp_tot[wid] = __popc(bal);
-        __syncthreads();
-        unsigned int wbase = 0, tot = 0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-            if (w < wid) wbase += warp_tot[w];
-            tot += warp_tot[w];
+    for (int i = threadIdx.x; i < kBins; i += blockDim.x) st->hist[i] = 0;
+}
+
+// Every key whose 24-bit prefix is >= (d1, d2) becomes a candidate.
+__global__ void __launch_bounds__(kPassThreads) sel_collect(const double *__restrict__ snr, uint64_t n, SelState *st,
+                                                            unsigned long long *cand_key, unsigned int *cand_idx)
+{
+    const unsigned int pref = (st->d1 << 12) | st->d2;
+    const int lane = threadIdx.x & 31;
+    const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
+    const uint64_t w0 = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    for (uint64_t base = w0 * 32; base < n; base += warps * 32) {
+        const uint64_t i = base + lane;
+        unsigned long long key = 0;
+        bool p = false;
+        if (i < n) {
+            key = order_key(snr[i]);
+            p = (unsigned int)(key >> 40) >= pref;
         }
-        if (e) {
-            const unsigned int rank = base + wbase + __popc(bal & ((1u << lane) - 1u));
-            if (rank < krem) out_idx[ngt + rank] = (unsigned int)i;
+        const unsigned int m = __ballot_sync(0xffffffffu, p);
+        if (!m) continue;
+        unsigned int pos0 = 0;
+        if (lane == __ffs(m) - 1) pos0 = atomicAdd(&st->ncand, (unsigned int)__popc(m));
+        pos0 = __shfl_sync(0xffffffffu, pos0, __ffs(m) - 1);
+        if (p) {
+            const unsigned int pos = pos0 + __popc(m & ((1u << lane) - 1u));
+            if (pos < kCandCap) {
+                cand_key[pos] = key;
+                cand_idx[pos] = (unsigned int)i;
+            } else {
+                st->overflow = 1;
+            }
         }
-        base += tot;
     }
 }
 
-__global__ void sel_finalize(const double *__restrict__ snr, const unsigned int *idx, int k, int P, TrackSet ts,
-                             MapDev m, stk_hit *out)
+// "a before b": larger key, then smaller index.
+__device__ __forceinline__ bool before(unsigned long long ka, unsigned int ia, unsigned long long kb, unsigned int ib)
 {
-    extern __shared__ unsigned long long sh[];
-    unsigned long long *key = sh;
-    unsigned int *ix = reinterpret_cast<unsigned int *>(sh + P);
-    for (int i = threadIdx.x; i < P; i += blockDim.x) {
-        if (i < k) {
-            key[i] = order_key(snr[idx[i]]);
-            ix[i] = idx[i];
-        } else {
-            key[i] = 0ull;          // below every real key
-            ix[i] = 0xffffffffu;
-        }
-    }
-    __syncthreads();
-    // Bitonic sort, "before" = larger key, then smaller index.
+    return ka > kb || (ka == kb && ia < ib);
+}
+
+// Bitonic sort of P (power of two) entries in shared memory, "before" first.
+__device__ void bitonic_sort(unsigned long long *key, unsigned int *ix, int P)
+{
     for (int size = 2; size <= P; size <<= 1) {
         for (int stride = size >> 1; stride > 0; stride >>= 1) {
             for (int i = threadIdx.x; i < P; i += blockDim.x) {
                 const int j = i ^ stride;
                 if (j > i) {
-                    const bool desc = (i & size) == 0;
-                    const bool i_first = key[i] > key[j] || (key[i] == key[j] && ix[i] < ix[j]);
-                    if (i_first != desc) {
+                    const bool up = (i & size) == 0;
+                    if (before(key[j], ix[j], key[i], ix[i]) == up) {
                         const unsigned long long tk = key[i]; key[i] = key[j]; key[j] = tk;
                         const unsigned int ti = ix[i]; ix[i] = ix[j]; ix[j] = ti;
                     }
@@ -183,26 +176,135 @@ __global__ void sel_finalize(const double *__restrict__ snr, const unsigned int 
             __syncthreads();
         }
     }
+}
+
+// Source of (key, index) pairs for the final step.
+struct Src {
+    const double *snr;
+    const unsigned long long *ckey;
+    const unsigned int *cidx;
+    uint64_t n;
+    bool full;  // true: all templates (key from snr[i], index i); false: the candidates
+    __device__ __forceinline__ unsigned long long key(uint64_t i) const { return full ? order_key(snr[i]) : ckey[i]; }
+    __device__ __forceinline__ unsigned int idx(uint64_t i) const { return full ? (unsigned int)i : cidx[i]; }
+};
+
+// Exact k-th largest key, then the largest index among the tied keys that still
+// fits, by 8-bit radix passes in one block; then gather the k winners.
+// hp: blockDim.x shared counters (the first 256 are the digit histogram).
+__device__ void select_generic(const Src &src, int k, unsigned long long *out_key, unsigned int *out_idx,
+                               unsigned int *hp, unsigned int *cnt)
+{
+    __shared__ unsigned int d, kr;
+    unsigned long long prefix = 0, mask = 0;
+    unsigned int krem = (unsigned int)k;
+    for (int shift = 56; shift >= 0; shift -= 8) {
+        for (int i = threadIdx.x; i < (int)blockDim.x; i += blockDim.x) hp[i] = 0;
+        __syncthreads();
+        for (uint64_t i = threadIdx.x; i < src.n; i += blockDim.x) {
+            const unsigned long long key = src.key(i);
+            if ((key & mask) == prefix) atomicAdd(&hp[(key >> shift) & 255u], 1u);
+        }
+        __syncthreads();
+        pick_digit(hp, blockDim.x, krem, &d, &kr);
+        prefix |= (unsigned long long)d << shift;
+        mask |= 255ull << shift;
+        krem = kr;
+    }
+    const unsigned long long kth = prefix;
+    // among keys equal to kth, the krem smallest indices: digits binned in reverse
+    unsigned int iprefix = 0, imask = 0, irem = krem;
+    for (int shift = 24; shift >= 0; shift -= 8) {
+        for (int i = threadIdx.x; i < (int)blockDim.x; i += blockDim.x) hp[i] = 0;
+        __syncthreads();
+        for (uint64_t i = threadIdx.x; i < src.n; i += blockDim.x) {
+            if (src.key(i) != kth) continue;
+            const unsigned int ix = src.idx(i);
+            if ((ix & imask) == iprefix) atomicAdd(&hp[255u - ((ix >> shift) & 255u)], 1u);
+        }
+        __syncthreads();
+        pick_digit(hp, blockDim.x, irem, &d, &kr);
+        iprefix |= (255u - d) << shift;
+        imask |= 255u << shift;
+        irem = kr;
+    }
+    const unsigned int ithr = iprefix;  // largest index kept among the ties
+    if (threadIdx.x == 0) *cnt = 0;
+    __syncthreads();
+    for (uint64_t i = threadIdx.x; i < src.n; i += blockDim.x) {
+        const unsigned long long key = src.key(i);
+        const unsigned int ix = src.idx(i);
+        if (key > kth || (key == kth && ix <= ithr)) {
+            const unsigned int pos = atomicAdd(cnt, 1u);
+            if (pos < (unsigned int)k) {
+                out_key[pos] = key;
+                out_idx[pos] = ix;
+            }
+        }
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(kFinalThreads)
+    sel_final(const double *__restrict__ snr, uint64_t n, const SelState *st, const unsigned long long *cand_key,
+              const unsigned int *cand_idx, int k, TrackSet ts, MapDev m, stk_hit *out)
+{
+    extern __shared__ unsigned long long sh[];
+    __shared__ unsigned int hp[kFinalThreads];
+    __shared__ unsigned int cnt;
+    const unsigned int ncand = st->ncand;
+    const bool small = !st->overflow && ncand <= (unsigned int)kSortCap;
+    int P = 1;
+    if (small) {
+        while (P < (int)ncand) P <<= 1;
+    } else {
+        while (P < k) P <<= 1;
+    }
+    unsigned long long *key = sh;
+    unsigned int *ix = reinterpret_cast<unsigned int *>(sh + P);
+    if (small) {
+        for (int i = threadIdx.x; i < P; i += blockDim.x) {
+            if (i < (int)ncand) {
+                key[i] = cand_key[i];
+                ix[i] = cand_idx[i];
+            } else {
+                key[i] = 0ull;      // below every real key
+                ix[i] = 0xffffffffu;
+            }
+        }
+        __syncthreads();
+    } else {
+        Src src{snr, cand_key, cand_idx, st->overflow ? n : (uint64_t)ncand, st->overflow != 0};
+        select_generic(src, k, key, ix, hp, &cnt);
+        for (int i = k + threadIdx.x; i < P; i += blockDim.x) {
+            key[i] = 0ull;
+            ix[i] = 0xffffffffu;
+        }
+        __syncthreads();
+    }
+    bitonic_sort(key, ix, P);
     for (int i = threadIdx.x; i < k; i += blockDim.x) {
         const unsigned int t = ix[i];
-        stk_hit h;
-        h.snr = snr[t];
-        h.index = ts.offset + t;
+        stk_hit hit;
+        hit.snr = snr[t];
+        hit.index = ts.offset + t;
         uint32_t f[3];
         double tau;
         draw_track(ts.seed, ts.offset + t, (uint32_t)m.n_f, ts.tau_max, f, tau);
-        h.f[0] = f[0]; h.f[1] = f[1]; h.f[2] = f[2];
-        h.reserved = 0;
-        h.tau = tau;
-        out[i] = h;
+        hit.f[0] = f[0]; hit.f[1] = f[1]; hit.f[2] = f[2];
+        hit.reserved = 0;
+        hit.tau = tau;
+        out[i] = hit;
     }
 }
 
+constexpr size_t align256(size_t x) { return (x + 255) / 256 * 256; }
+
 }  // namespace
 
-size_t select_scratch_bytes(uint64_t /*n*/, int k)
+size_t select_scratch_bytes(uint64_t /*n*/, int /*k*/)
 {
-    return sizeof(SelState) + ((size_t)k * 4 + 255) / 256 * 256 + (size_t)kMaxChunks * 4;
+    return align256(sizeof(SelState)) + align256((size_t)kCandCap * 8) + align256((size_t)kCandCap * 4);
 }
 
 cudaError_t launch_select_topk(const double *snr, uint64_t n, int k, const TrackSet &ts, const MapDev &m,
@@ -211,35 +313,21 @@ cudaError_t launch_select_topk(const double *snr, uint64_t n, int k, const Track
     if (k <= 0 || (uint64_t)k > n || k > STK_MAX_K || n > 0xffffffffull) return cudaErrorInvalidValue;
     unsigned char *p = (unsigned char *)scratch;
     SelState *ss = (SelState *)p;
-    unsigned int *idx = (unsigned int *)(p + sizeof(SelState));
-    unsigned int *chunk_eq = (unsigned int *)(p + sizeof(SelState) + ((size_t)k * 4 + 255) / 256 * 256);
-    int nl = 0;
-    sel_init<<<1, 256, 0, st>>>(ss, (unsigned int)k);
-    ++nl;
-    const uint64_t hb = (n + kHistThreads - 1) / kHistThreads;
-    const int hist_grid = (int)(hb < 1184 ? hb : 1184);
-    for (int pass = 0; pass < 8; ++pass) {
-        const int shift = 56 - 8 * pass;
-        sel_hist<<<hist_grid, kHistThreads, 0, st>>>(snr, n, ss, shift);
-        sel_pick<<<1, 32, 0, st>>>(ss, shift);
-        nl += 2;
-    }
-    uint64_t nchunks = (n + kHistThreads * 8 - 1) / (kHistThreads * 8);
-    if (nchunks > kMaxChunks) nchunks = kMaxChunks;
-    if (nchunks < 1) nchunks = 1;
-    const uint64_t chunk = (n + nchunks - 1) / nchunks;
-    nchunks = (n + chunk - 1) / chunk;
-    sel_collect<<<(unsigned)nchunks, kHistThreads, 0, st>>>(snr, n, chunk, ss, idx, chunk_eq);
-    sel_ties<<<(unsigned)nchunks, kHistThreads, 0, st>>>(snr, n, chunk, ss, idx, chunk_eq);
-    nl += 2;
-    int P = 1;
-    while (P < k) P <<= 1;
-    const size_t smem = (size_t)P * 12;
-    cudaError_t e = cudaFuncSetAttribute(sel_finalize, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    unsigned long long *ckey = (unsigned long long *)(p + align256(sizeof(SelState)));
+    unsigned int *cidx = (unsigned int *)(p + align256(sizeof(SelState)) + align256((size_t)kCandCap * 8));
+    const uint64_t blocks = (n + kPassThreads * 8 - 1) / (kPassThreads * 8);
+    const int grid = (int)(blocks < 296 ? (blocks < 1 ? 1 : blocks) : 296);
+    sel_init<<<1, 1024, 0, st>>>(ss);
+    sel_hist<0><<<grid, kPassThreads, 0, st>>>(snr, n, ss);
+    sel_pick<0><<<1, kFinalThreads, 0, st>>>(ss, (unsigned int)k);
+    sel_hist<1><<<grid, kPassThreads, 0, st>>>(snr, n, ss);
+    sel_pick<1><<<1, kFinalThreads, 0, st>>>(ss, (unsigned int)k);
+    sel_collect<<<grid, kPassThreads, 0, st>>>(snr, n, ss, ckey, cidx);
+    const size_t smem = (size_t)kSortCap * 12;
+    cudaError_t e = cudaFuncSetAttribute(sel_final, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    sel_finalize<<<1, 1024, smem, st>>>(snr, idx, k, P, ts, m, out);
-    ++nl;
-    if (launches) *launches = nl;
+    sel_final<<<1, kFinalThreads, smem, st>>>(snr, n, ss, ckey, cidx, k, ts, m, out);
+    if (launches) *launches = 7;
     return cudaGetLastError();
 }
 

@@ -223,15 +223,34 @@ def test_split_ranges_merge_exactly(ctx):
     np.testing.assert_array_equal(allh[order], full)
 
 
-def test_constant_map_ties_take_smallest_index(ctx):
+@pytest.mark.parametrize("T,k", [(5000, 10), (20000, 4096), (100000, 100)])
+def test_constant_map_ties_take_smallest_index(ctx, T, k):
+    """Every template ties: the smallest indices win.  The three sizes take the
+    three selection routes (shared-memory sort of the candidates; exact select
+    over candidates beyond that sort; candidate-buffer overflow, full array)."""
     n_t, n_f = 20, 30
     y = np.full((n_t, n_f), 1 + 0j, np.complex64)
     m = ctx.load_map(torch.from_numpy(y).cuda(), torch.ones(n_f, device="cuda"), 0.0, 1.0)
-    ctx.set_tracks(5000, 1, 1000, 0.0)      # tau = 0: every template scores exactly sqrt(n_t)
-    hits = ctx.score(m, 10)
-    np.testing.assert_array_equal(hits["index"], np.arange(1000, 1010))
+    ctx.set_tracks(T, 1, 1000, 0.0)      # tau = 0: every template scores exactly sqrt(n_t)
+    hits = ctx.score(m, k)
+    np.testing.assert_array_equal(hits["index"], np.arange(1000, 1000 + k))
     assert np.all(hits["snr"] == hits["snr"][0])
     assert abs(hits["snr"][0] - np.sqrt(n_t)) <= 1e-6 * np.sqrt(n_t)
+
+
+def test_selection_with_many_near_ties(ctx):
+    """SNRs rounded to few values (many exact ties across the boundary) vs numpy's ordering."""
+    n_t, n_f, T, k = 40, 50, 200000, 3000
+    rng = np.random.default_rng(61)
+    y = (np.round(rng.standard_normal((n_t, n_f)) * 2) / 2 + 0j).astype(np.complex64)
+    m = ctx.load_map(torch.from_numpy(y).cuda(), torch.ones(n_f, device="cuda"), 0.0, 1.0)
+    ctx.set_tracks(T, 3, 0, 0.0)
+    allg = ctx.score_all(m).cpu().numpy()
+    assert np.unique(allg).size < T // 10
+    hits = ctx.score(m, k)
+    order = np.lexsort((np.arange(T), -allg))[:k]
+    np.testing.assert_array_equal(hits["index"], order)
+    np.testing.assert_array_equal(hits["snr"], allg[order])
 
 
 # ------------------------------------------------------------------ closed forms through the GPU
