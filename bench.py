@@ -42,6 +42,7 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-variants", action="store_true", help="skip the FP16-storage variant measurement")
     ap.add_argument("--tracks", type=int, default=0,
                     help="profiling aid: templates per GPU other than the workload's 5e6 (reported in config)")
     ap.add_argument("--cpu-sample", type=int, default=400000,
@@ -305,6 +306,40 @@ def main():
     hits = out.cpu().numpy().view(stk.HIT_DTYPE)
     plan = ctx.last_plan()
 
+    # FP16 pixel storage on the same workload (4-byte records), same timing rules
+    variants = {}
+    if not args.no_variants:
+        ctx.set_profiling(True)
+        m16 = ctx.load_map(torch.from_numpy(fm.y).cuda(), torch.from_numpy(fm.sigma).cuda(), fm.f_min, fm.df,
+                           fp16=True)
+        out16 = torch.zeros(K * 40, dtype=torch.uint8, device="cuda")
+        for _ in range(max(args.warmup, 3)):
+            ctx.score(m16, K, out=out16)
+        ev16 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                for _ in range(args.steps)]
+        k16 = []
+        torch.cuda.synchronize()
+        for s in range(args.steps):
+            flush.zero_()
+            ev16[s][0].record(stream)
+            ctx.score(m16, K, out=out16)
+            ev16[s][1].record(stream)
+            k16.append(ctx.last_timings()["score_ms"])
+        torch.cuda.synchronize()
+        ms16 = sum(a.elapsed_time(b) for a, b in ev16) / args.steps
+        h16 = out16.cpu().numpy().view(stk.HIT_DTYPE)
+        common = np.intersect1d(h16["index"], hits["index"])
+        s32 = dict(zip(hits["index"].tolist(), hits["snr"].tolist()))
+        s16 = dict(zip(h16["index"].tolist(), h16["snr"].tolist()))
+        rel = [abs(s16[i] - s32[i]) / abs(s32[i]) for i in common.tolist()]
+        variants["fp16"] = {
+            "value": T * fm.n_t / (ms16 / 1e3), "unit": "track-pixels/s", "ms_per_step": ms16,
+            "kernel_ms": sum(k16) / len(k16), "speedup_vs_fp32": ms / ms16,
+            "topk_overlap_with_fp32": len(common) / K,
+            "max_rel_snr_diff_vs_fp32_on_common_topk": max(rel) if rel else None,
+            "storage": "4 B/pixel: FP16 |y|/sigma (per-frequency scaling) + Q0.16 phase; FP32 sums"}
+        m16.close()
+
     # end to end through the public API with host buffers (pinned), copies timed
     e2e = None
     if not args.no_e2e:
@@ -372,6 +407,8 @@ def main():
         }
         if e2e:
             line["e2e"] = e2e
+        if variants:
+            line["variants"] = variants
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(fm, w, args.cpu_sample)
         print(json.dumps(line), flush=True)

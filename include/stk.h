@@ -51,6 +51,8 @@ extern "C" {
 #define STK_HOST_PTR       0x1u /* y and sigma are host pointers (pageable or pinned) */
 #define STK_SIGMA_PER_FREQ 0x2u /* sigma holds n_f values, one per frequency bin, constant in time */
 #define STK_NORM_PAPER     0x4u /* Eq. 7 as printed: SNR = (1/N) sum Re[e^{2 pi i f tau} y/sigma] */
+#define STK_FP16           0x8u /* store each pixel in 4 bytes: |y|/sigma in FP16 (per-frequency or per-pixel
+                                   scaling by sigma) and the phase in 1/65536 turns; sums stay FP32 */
 
 /* ---- stk_score flags ------------------------------------------------- */
 #define STK_OUT_HOST 0x1u /* out_topk is host memory; the call waits for the result */
@@ -91,14 +93,14 @@ STK_API int stk_set_stream(stk_ctx *ctx, void *cuda_stream);
  *   sigma   float32 [n_t][n_f], or [n_f] with STK_SIGMA_PER_FREQ; every value finite, > 0
  *   n_t     time columns, >= 2 (a template has one pixel per column)
  *   n_f     frequency bins, >= 1; bin k has frequency f_min_hz + k * df_hz
- *   flags   STK_HOST_PTR | STK_SIGMA_PER_FREQ | STK_NORM_PAPER
+ *   flags   STK_HOST_PTR | STK_SIGMA_PER_FREQ | STK_NORM_PAPER | STK_FP16
  * Statistic selected (Eq. 7 and the footnote to Eq. 5 allowing other weights):
  *   default         SNR = sum_j Re[e^{2 pi i f_j tau} y_j sigma_j^-2] / sqrt(sum_j sigma_j^-2)
  *   STK_NORM_PAPER  SNR = (1/n_t) sum_j Re[e^{2 pi i f_j tau} y_j / sigma_j]
  * The library keeps its own packed copy; the caller may free y and sigma when
  * the call returns (it synchronises the stream).  Errors: STK_EINVAL (sizes,
  * NULL pointers, a non-finite y, sigma <= 0 or non-finite, f_min/df
- * non-finite or df <= 0), STK_ENOMEM, STK_ECUDA. */
+ * non-finite or df <= 0, |y|/sigma above 65504 with STK_FP16), STK_ENOMEM, STK_ECUDA. */
 STK_API int stk_load_map(stk_ctx *ctx, const void *y_c64, const float *sigma, int n_t, int n_f,
                  double f_min_hz, double df_hz, unsigned flags, stk_map **out);
 
@@ -199,7 +201,7 @@ STK_API int stk_score_noalloc(const stk_map *map, uint64_t n_tracks, uint64_t se
 /* ---- tuning (kernel choice and launch shape; results do not depend on them) */
 #define STK_OPT_KERNEL   1 /* 0 automatic, 1 one-thread-per-template kernel, 2 shared-memory slab kernel */
 #define STK_OPT_THREADS  2 /* slab kernel block size, 0 = automatic, else 32 .. 1024 */
-#define STK_OPT_MAX_R    3 /* slab kernel: most templates held per thread, 1 .. 4 (default 4) */
+#define STK_OPT_MAX_R    3 /* slab kernel: most templates held per thread, 1 .. 6 (default 6; at most 5 with a varying weight) */
 #define STK_OPT_STAGES   4 /* slab kernel: shared-memory slab buffers, 2 .. 4 (default 2) */
 #define STK_OPT_SMEM_KB  5 /* slab kernel: shared-memory budget in KiB, 0 = the device maximum */
 

@@ -106,9 +106,9 @@ class Context:
             pass
 
     # ---- calls
-    def load_map(self, y, sigma, f_min: float, df: float, paper_mode: bool = False) -> Map:
+    def load_map(self, y, sigma, f_min: float, df: float, paper_mode: bool = False, fp16: bool = False) -> Map:
         """stk_load_map.  y: complex64 [n_t][n_f] (CUDA tensor, or host numpy/tensor);
-        sigma: float32 [n_f] (per frequency) or [n_t][n_f]."""
+        sigma: float32 [n_f] (per frequency) or [n_t][n_f]; fp16: 4-byte pixel storage."""
         self._bind_stream()
         host = not (_is_tensor(y) and y.is_cuda)
         if host:
@@ -133,7 +133,7 @@ class Context:
         if not per_freq and tuple(keep[1].shape) != (n_t, n_f):
             raise ValueError(f"sigma shape {tuple(keep[1].shape)} is neither ({n_f},) nor ({n_t}, {n_f})")
         flags = (L.STK_HOST_PTR if host else 0) | (L.STK_SIGMA_PER_FREQ if per_freq else 0) | \
-            (L.STK_NORM_PAPER if paper_mode else 0)
+            (L.STK_NORM_PAPER if paper_mode else 0) | (L.STK_FP16 if fp16 else 0)
         h = C.c_void_p()
         self._check(lib().stk_load_map(self._h, C.c_void_p(yp), C.c_void_p(sp), int(n_t), int(n_f),
                                        float(f_min), float(df), flags, C.byref(h)))

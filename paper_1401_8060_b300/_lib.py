@@ -14,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libstk.so")
 
 STK_OK, STK_EINVAL, STK_ENOMEM, STK_ECUDA, STK_ETIMEOUT, STK_ESTATE = 0, -1, -2, -3, -4, -5
-STK_HOST_PTR, STK_SIGMA_PER_FREQ, STK_NORM_PAPER = 0x1, 0x2, 0x4
+STK_HOST_PTR, STK_SIGMA_PER_FREQ, STK_NORM_PAPER, STK_FP16 = 0x1, 0x2, 0x4, 0x8
 STK_OUT_HOST = 0x1
 STK_MAX_K = 4096
 STK_NOALLOC_MAX_TRACKS = 1 << 20

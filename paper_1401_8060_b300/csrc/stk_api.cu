@@ -8,6 +8,8 @@
 #include <mutex>
 #include <string>
 
+#include <cuda_fp16.h>
+
 #include "stk_internal.cuh"
 
 using namespace stk;
@@ -107,6 +109,41 @@ __global__ void pack_kernel(const float2 *__restrict__ y, const float *__restric
         if (wout) {
             if (!per_freq) wout[(size_t)t * ldw + k] = (float)w;
             else if (t == 0) wout[k] = (float)w;
+        }
+    }
+    if (flags) atomicOr(err, flags);
+}
+
+// FP16 storage: record = (Q0.16 arg y) << 16 | FP16(|y| / sigma); weights r = 1/sigma.
+__global__ void pack_fp16_kernel(const float2 *__restrict__ y, const float *__restrict__ sigma, int per_freq, int n_t,
+                                 int n_f, int ldr, int ldw, uint32_t *__restrict__ rec, float *__restrict__ rout,
+                                 int *err)
+{
+    const float s0 = sigma[0];
+    int flags = 0;
+    const uint64_t total = (uint64_t)n_t * ldr;
+    for (uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; p < total;
+         p += (uint64_t)gridDim.x * blockDim.x) {
+        const int t = (int)(p / ldr), k = (int)(p % ldr);
+        if (k >= n_f) {
+            rec[p] = 0u;
+            continue;
+        }
+        const size_t q = (size_t)t * n_f + k;
+        const float2 v = y[q];
+        const float s = per_freq ? sigma[k] : sigma[q];
+        if (!isfinite(v.x) || !isfinite(v.y) || !(s > 0.f) || !isfinite(s)) flags |= ERR_BADINPUT;
+        if (s != s0) flags |= FLAG_SIGMA_VARIES;
+        const double h = hypot((double)v.x, (double)v.y) / (double)s;
+        if (!(h <= 65504.0)) flags |= ERR_FP16_RANGE;
+        const double turns = atan2((double)v.y, (double)v.x) / 6.283185307179586476925;  // (-1/2, 1/2]
+        const uint32_t a16 = (uint32_t)llrint(turns * 65536.0) & 0xffffu;
+        const unsigned short hb = __half_as_ushort(__double2half(h));
+        rec[p] = (a16 << 16) | (uint32_t)hb;
+        if (rout) {
+            const float r = (float)(1.0 / (double)s);
+            if (!per_freq) rout[(size_t)t * ldw + k] = r;
+            else if (t == 0) rout[k] = r;
         }
     }
     if (flags) atomicOr(err, flags);
@@ -247,7 +284,7 @@ int stk_set_option(stk_ctx *c, int option, int64_t value)
         c->tune.threads = (int)value;
         return STK_OK;
     case STK_OPT_MAX_R:
-        if (value < 1 || value > 4) return set_err(c, STK_EINVAL, "templates per thread must be in [1, 4]");
+        if (value < 1 || value > 6) return set_err(c, STK_EINVAL, "templates per thread must be in [1, 6]");
         c->tune.max_R = (int)value;
         return STK_OK;
     case STK_OPT_STAGES:
@@ -288,10 +325,11 @@ int stk_load_map(stk_ctx *c, const void *y_c64, const float *sigma, int n_t, int
     }
     if (!std::isfinite(f_min_hz) || !std::isfinite(df_hz) || !(df_hz > 0))
         return set_err(c, STK_EINVAL, "f_min must be finite and df finite and > 0");
-    if (flags & ~(STK_HOST_PTR | STK_SIGMA_PER_FREQ | STK_NORM_PAPER))
+    if (flags & ~(STK_HOST_PTR | STK_SIGMA_PER_FREQ | STK_NORM_PAPER | STK_FP16))
         return set_err(c, STK_EINVAL, "unknown flags 0x%x", flags);
     CUDA_TRY(c, cudaSetDevice(c->device));
     const bool host = flags & STK_HOST_PTR, per_freq = flags & STK_SIGMA_PER_FREQ, paper = flags & STK_NORM_PAPER;
+    const bool fp16 = flags & STK_FP16;
     const size_t npx = (size_t)n_t * n_f;
     const size_t ybytes = npx * 8, sbytes = (per_freq ? (size_t)n_f : npx) * 4;
 
@@ -301,7 +339,8 @@ int stk_load_map(stk_ctx *c, const void *y_c64, const float *sigma, int n_t, int
     MapDev &d = m->dev;
     d.n_t = n_t;
     d.n_f = n_f;
-    d.ldr = (n_f + 1) / 2 * 2;
+    d.prec = fp16 ? PREC_FP16 : PREC_FP32;
+    d.ldr = fp16 ? (n_f + 3) / 4 * 4 : (n_f + 1) / 2 * 2;
     d.ldw = (n_f + 3) / 4 * 4;
     d.paper = paper ? 1 : 0;
     d.f_min = f_min_hz;
@@ -333,7 +372,7 @@ int stk_load_map(stk_ctx *c, const void *y_c64, const float *sigma, int n_t, int
         ysrc = (const float2 *)ytmp;
         ssrc = (const float *)stmp;
     }
-    const size_t recbytes = (size_t)n_t * d.ldr * 8;
+    const size_t recbytes = (size_t)n_t * d.ldr * (fp16 ? 4 : 8);
     if ((e = cudaMalloc(&m->rec_buf, recbytes)) != cudaSuccess)
         return fail(set_err(c, STK_ENOMEM, "map allocation (%zu bytes): %s", recbytes, cudaGetErrorString(e)));
     const size_t wbytes = per_freq ? (size_t)d.ldw * 4 : (size_t)n_t * d.ldw * 4;
@@ -344,13 +383,18 @@ int stk_load_map(stk_ctx *c, const void *y_c64, const float *sigma, int n_t, int
         return fail(set_err(c, STK_ECUDA, "memset: %s", cudaGetErrorString(e)));
     const uint64_t total = (uint64_t)n_t * d.ldr;
     const int blocks = (int)std::min<uint64_t>((total + 255) / 256, (uint64_t)c->num_sms * 8);
-    pack_kernel<<<blocks, 256, 0, c->stream>>>(ysrc, ssrc, per_freq ? 1 : 0, n_t, n_f, d.ldr, d.ldw, d.paper,
-                                                (uint2 *)m->rec_buf, (float *)m->w_buf, c->d_err);
+    if (fp16)
+        pack_fp16_kernel<<<blocks, 256, 0, c->stream>>>(ysrc, ssrc, per_freq ? 1 : 0, n_t, n_f, d.ldr, d.ldw,
+                                                         (uint32_t *)m->rec_buf, (float *)m->w_buf, c->d_err);
+    else
+        pack_kernel<<<blocks, 256, 0, c->stream>>>(ysrc, ssrc, per_freq ? 1 : 0, n_t, n_f, d.ldr, d.ldw, d.paper,
+                                                    (uint2 *)m->rec_buf, (float *)m->w_buf, c->d_err);
     if ((e = cudaGetLastError()) != cudaSuccess)
         return fail(set_err(c, STK_ECUDA, "pack kernel launch: %s", cudaGetErrorString(e)));
     int fl = 0;
     if (read_err_flags(c, &fl) != STK_OK) return fail(STK_ECUDA);
     if (fl & ERR_BADINPUT) return fail(set_err(c, STK_EINVAL, "y has a non-finite value or sigma is <= 0 or non-finite"));
+    if (fl & ERR_FP16_RANGE) return fail(set_err(c, STK_EINVAL, "FP16 storage: |y| / sigma exceeds 65504"));
     cudaFree(ytmp);
     cudaFree(stmp);
     ytmp = stmp = nullptr;
@@ -366,9 +410,13 @@ int stk_load_map(stk_ctx *c, const void *y_c64, const float *sigma, int n_t, int
     } else {
         d.wmode = per_freq ? WMODE_FREQ : WMODE_PIXEL;
     }
-    d.norm = paper ? 1.0 / (double)n_t
-                   : (d.wmode == WMODE_CONST ? 1.0 / std::sqrt((double)n_t * (double)d.w_const) : 0.0);
-    d.rec = (const uint2 *)m->rec_buf;
+    // constant weight: FP32 records hold |y| w0 (SNR = S / sqrt(n_t w0)); FP16 records hold
+    // |y| / sigma0 (SNR = S r0 / sqrt(n_t r0^2) = S / sqrt(n_t)); paper form: S / n_t
+    if (paper) d.norm = 1.0 / (double)n_t;
+    else if (d.wmode == WMODE_CONST) d.norm = fp16 ? 1.0 / std::sqrt((double)n_t)
+                                                   : 1.0 / std::sqrt((double)n_t * (double)d.w_const);
+    else d.norm = 0.0;
+    d.rec = m->rec_buf;
     d.w = d.wmode == WMODE_CONST ? nullptr : (const float *)m->w_buf;
     *out = m;
     return STK_OK;

@@ -15,11 +15,19 @@
 namespace stk {
 
 // ---------------------------------------------------------------- packed map
-// Each pixel is stored once, in polar form, as an 8-byte record:
+// Each pixel is stored once, in polar form.  FP32 storage: an 8-byte record
 //   .x = bits of |z| (float), .y = arg(z) in turns as unsigned Q0.32,
-// where z = y sigma^-2 (weighted statistic) or z = y / sigma (STK_NORM_PAPER).
-// Then Re[e^{i theta} z] = |z| cos(theta + 2 pi arg z): one cosine per pixel.
-// Weights w = sigma^-2 enter only the weighted normaliser sqrt(sum w).
+// where z = y sigma^-2 (weighted statistic) or z = y / sigma (STK_NORM_PAPER);
+// the weight array holds w = sigma^-2.  FP16 storage: a 4-byte record, low
+// half the FP16 value of |y| / sigma (the per-frequency or per-pixel scaling),
+// high half arg(y) in Q0.16 turns; the weight array then holds r = 1/sigma, so
+// |z| = (|y|/sigma) r in the weighted form and the weight is r^2.
+// Re[e^{i theta} z] = |z| cos(theta + 2 pi arg z): one cosine per pixel.
+enum Prec : int {
+    PREC_FP32 = 0,
+    PREC_FP16 = 1,
+};
+
 enum WMode : int {
     WMODE_CONST = 0,  // every pixel has the same weight (w_const), or paper mode
     WMODE_FREQ = 1,   // weight depends on frequency only: table w[n_f]
@@ -28,15 +36,16 @@ enum WMode : int {
 
 struct MapDev {
     int n_t, n_f;
-    int ldr;          // records per row: n_f rounded up to a multiple of 2 (16-byte rows)
+    int prec;         // PREC_FP32 or PREC_FP16
+    int ldr;          // records per row: n_f rounded up so rows are 16-byte multiples
     int ldw;          // floats per weight row (WMODE_PIXEL): n_f rounded up to a multiple of 4
     int wmode;
     int paper;        // 1: SNR = S / n_t
     float w_const;    // WMODE_CONST weight (sigma^-2), 1 in paper mode
     double f_min, df; // Hz
     double norm;      // 1 / n_t (paper form) or 1 / sqrt(n_t w_const) (WMODE_CONST); else unused
-    const uint2 *rec; // [n_t][ldr]
-    const float *w;   // [n_f] (WMODE_FREQ) or [n_t][ldw] (WMODE_PIXEL), else null
+    const void *rec;  // [n_t][ldr] records (uint2 for FP32, uint32 for FP16)
+    const float *w;   // [n_f] (WMODE_FREQ) or [n_t][ldw] (WMODE_PIXEL), else null: sigma^-2 or 1/sigma
     // Rasteriser: column j of template (f0, f1, f2) sits at bin floor(N_j / d) with
     // N_j = 2 num_j + M^2, num_j = (M-j)^2 f0 + 2 (M-j) j f1 + j^2 f2, d = 2 M^2.
     uint32_t M;       // n_t - 1
@@ -57,6 +66,7 @@ enum : int {
     ERR_BADTRACK = 2,  // explicit template with a control bin >= n_f
     ERR_BADINPUT = 4,  // map packing saw a non-finite y or a bad sigma
     FLAG_SIGMA_VARIES = 8,  // map packing saw more than one sigma value
+    ERR_FP16_RANGE = 16,    // |y| / sigma beyond the FP16 range
 };
 
 // ---------------------------------------------------------------- Philox4x64-10
@@ -285,7 +295,7 @@ struct ScorePlan {
 struct Tuning {
     int kernel = 0;      // 0 auto
     int threads = 0;     // 0 auto
-    int max_R = 4;
+    int max_R = 6;       // capped per weight mode by the launcher
     int nstage = 2;
     int smem_kb = 0;     // 0 auto
 };

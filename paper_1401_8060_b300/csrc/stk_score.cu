@@ -12,6 +12,11 @@
 //                 memory in slabs of S time columns (one bulk copy per slab,
 //                 double-buffered on mbarriers), so every gathered pixel is a
 //                 shared-memory load.  The map is read from L2 once per batch.
+// Both come in two storage precisions (PREC): 8-byte FP32 polar records, or
+// 4-byte records holding |y|/sigma in FP16 and the phase in Q0.16 turns, the
+// per-frequency (or per-pixel) scale 1/sigma then doubling as the weight.
+#include <cuda_fp16.h>
+
 #include <algorithm>
 #include <cstdio>
 
@@ -23,6 +28,46 @@ namespace {
 
 constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s per slab wait
 constexpr int kMaxThreads = 1024;
+
+// ------------------------------------------------------------------ pixel records
+template <int PREC>
+struct Pix;
+
+template <>
+struct Pix<PREC_FP32> {  // {float |z|, Q0.32 arg z}; the weight array holds w = sigma^-2
+    using Rec = uint2;
+    __device__ static __forceinline__ float mag(Rec v) { return __uint_as_float(v.x); }
+    __device__ static __forceinline__ uint32_t arg(Rec v) { return v.y; }
+    __device__ static __forceinline__ Rec load_global(const void *p, size_t i) { return __ldg((const uint2 *)p + i); }
+};
+
+template <>
+struct Pix<PREC_FP16> {  // low half: FP16 |y|/sigma; high half: arg in Q0.16 turns; weights hold r = 1/sigma
+    using Rec = uint32_t;
+    __device__ static __forceinline__ float mag(Rec v)
+    {
+        return __half2float(__ushort_as_half((unsigned short)(v & 0xffffu)));
+    }
+    __device__ static __forceinline__ uint32_t arg(Rec v) { return v & 0xffff0000u; }
+    __device__ static __forceinline__ Rec load_global(const void *p, size_t i)
+    {
+        return __ldg((const unsigned int *)p + i);
+    }
+};
+
+// One pixel of Eq. 7: acc += |z| cos(theta + 2 pi arg z), W += weight.
+// FP32 records carry |z| and wv = sigma^-2; FP16 records carry |y|/sigma and
+// wv = 1/sigma, so |z| = mag wv and the weight is wv^2.
+template <int PREC, int WMODE>
+__device__ __forceinline__ void accumulate(typename Pix<PREC>::Rec v, uint32_t bin, const Phase &ph, float wv,
+                                           float &acc, float &W)
+{
+    const float c = cos_turn(pixel_turn(bin, ph, Pix<PREC>::arg(v)));
+    float mg = Pix<PREC>::mag(v);
+    if (PREC == PREC_FP16 && WMODE != WMODE_CONST) mg *= wv;
+    acc = fmaf(mg, c, acc);
+    if (WMODE != WMODE_CONST) W = (PREC == PREC_FP16) ? fmaf(wv, wv, W) : W + wv;
+}
 
 // Normalisation (Eq. 7 with the weighting of the footnote to Eq. 5), FP64 on the
 // GPU.  Weighted form with varying weights: S / sqrt(W), where 1 / sqrt(W) is an
@@ -38,7 +83,7 @@ __device__ __forceinline__ double finalize_snr(float acc, float W, const MapDev 
 }
 
 // ------------------------------------------------------------------ simple kernel
-template <int WMODE, bool EXPLICIT, bool FAST32>
+template <int WMODE, int PREC, bool EXPLICIT, bool FAST32>
 __global__ void __launch_bounds__(256) score_simple_kernel(MapDev m, TrackSet ts, const uint32_t *__restrict__ f3,
                                                            const double *__restrict__ tau_in, uint64_t n,
                                                            double *__restrict__ out, int *err)
@@ -63,7 +108,6 @@ __global__ void __launch_bounds__(256) score_simple_kernel(MapDev m, TrackSet ts
     float acc = 0.f, W = 0.f;
     Raster32 r;
     if (FAST32) r = raster_init(f[0], f[1], f[2], m.M);
-    const uint2 *rec = m.rec;
     for (int j = 0; j < m.n_t; ++j) {
         uint32_t bin;
         if (FAST32) {
@@ -73,10 +117,11 @@ __global__ void __launch_bounds__(256) score_simple_kernel(MapDev m, TrackSet ts
         } else {
             bin = raster_bin_wide(f[0], f[1], f[2], m.M, (uint32_t)j, m.d);
         }
-        const uint2 v = __ldg(rec + (size_t)j * m.ldr + bin);
-        acc = fmaf(__uint_as_float(v.x), cos_turn(pixel_turn(bin, ph, v.y)), acc);
-        if (WMODE == WMODE_FREQ) W += __ldg(m.w + bin);
-        if (WMODE == WMODE_PIXEL) W += __ldg(m.w + (size_t)j * m.ldw + bin);
+        const auto v = Pix<PREC>::load_global(m.rec, (size_t)j * m.ldr + bin);
+        float wv = 0.f;
+        if (WMODE == WMODE_FREQ) wv = __ldg(m.w + bin);
+        if (WMODE == WMODE_PIXEL) wv = __ldg(m.w + (size_t)j * m.ldw + bin);
+        accumulate<PREC, WMODE>(v, bin, ph, wv, acc, W);
     }
     out[i] = finalize_snr<WMODE>(acc, W, m);
 }
@@ -90,12 +135,13 @@ struct StagedArgs {
     uint32_t wtab_floats;  // n_f rounded to 4 (WMODE_FREQ)
 };
 
-template <int R, int WMODE>
+template <int R, int WMODE, int PREC>
 __global__ void __launch_bounds__(kMaxThreads, 1)
     score_staged_kernel(MapDev m, TrackSet ts, StagedArgs a, double *__restrict__ out, int *err)
 {
+    using Rec = typename Pix<PREC>::Rec;
     extern __shared__ __align__(128) unsigned char smem[];
-    uint2 *srec = reinterpret_cast<uint2 *>(smem);
+    Rec *srec = reinterpret_cast<Rec *>(smem);
     float *sw = reinterpret_cast<float *>(srec + (size_t)a.nstage * a.slab_recs);  // WMODE_PIXEL slabs
     float *swt = sw + (WMODE == WMODE_PIXEL ? (size_t)a.nstage * a.slab_ws : 0);    // WMODE_FREQ table
     uint64_t *bars = reinterpret_cast<uint64_t *>(swt + (WMODE == WMODE_FREQ ? a.wtab_floats : 0));
@@ -105,8 +151,9 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
     if (blockIdx.x >= a.nbatches) return;
     const uint64_t my_nb = (a.nbatches - blockIdx.x + gridDim.x - 1) / gridDim.x;
     const uint64_t total = my_nb * (uint64_t)a.nslabs;  // slabs this CTA consumes, over all its batches
-    const uint32_t row_bytes = (uint32_t)m.ldr * 8u;
+    const uint32_t row_bytes = (uint32_t)m.ldr * (uint32_t)sizeof(Rec);
     const uint32_t wrow_bytes = (uint32_t)m.ldw * 4u;
+    const Rec *grec = reinterpret_cast<const Rec *>(m.rec);
 
     if (tid == 0) {
         for (int s = 0; s < a.nstage; ++s) mbar_init(&bars[s], 1);
@@ -126,7 +173,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
         uint32_t bytes = (uint32_t)rows * row_bytes;
         if (WMODE == WMODE_PIXEL) bytes += (uint32_t)rows * wrow_bytes;
         mbar_arrive_expect_tx(&bars[slot], bytes);
-        bulk_g2s(srec + (size_t)slot * a.slab_recs, m.rec + (size_t)row0 * m.ldr, (uint32_t)rows * row_bytes,
+        bulk_g2s(srec + (size_t)slot * a.slab_recs, grec + (size_t)row0 * m.ldr, (uint32_t)rows * row_bytes,
                  &bars[slot]);
         if (WMODE == WMODE_PIXEL)
             bulk_g2s(sw + (size_t)slot * a.slab_ws, m.w + (size_t)row0 * m.ldw, (uint32_t)rows * wrow_bytes,
@@ -168,17 +215,18 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
             const uint32_t parity = (uint32_t)((q / (uint64_t)a.nstage) & 1ull);
             const bool ok = mbar_wait(&bars[slot], parity, kWaitLimitNs);
             const int rows = min(a.S, m.n_t - s * a.S);
-            const uint2 *row = srec + (size_t)slot * a.slab_recs;
+            const Rec *row = srec + (size_t)slot * a.slab_recs;
             const float *wrow = sw + (size_t)slot * a.slab_ws;
 #pragma unroll 2
             for (int jj = 0; jj < rows; ++jj) {
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
                     const uint32_t bin = __umulhi(N[r], magic) >> shift;
-                    const uint2 v = row[bin];
-                    acc[r] = fmaf(__uint_as_float(v.x), cos_turn(pixel_turn(bin, ph[r], v.y)), acc[r]);
-                    if (WMODE == WMODE_FREQ) W[r] += swt[bin];
-                    if (WMODE == WMODE_PIXEL) W[r] += wrow[bin];
+                    const Rec v = row[bin];
+                    float wv = 0.f;
+                    if (WMODE == WMODE_FREQ) wv = swt[bin];
+                    if (WMODE == WMODE_PIXEL) wv = wrow[bin];
+                    accumulate<PREC, WMODE>(v, bin, ph[r], wv, acc[r], W[r]);
                     N[r] += D[r];
                     D[r] += D2[r];
                 }
@@ -201,37 +249,54 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
     }
     if (failed && tid == 0) {
         atomicOr(err, ERR_TIMEOUT);
-        // Let copies already in flight land before the CTA's shared memory goes away.
-        for (uint64_t qq = q + 1; qq < q + (uint64_t)a.nstage && qq < total; ++qq)
+        // Let copies already issued (slab q and up to nstage - 1 after it) land before
+        // the CTA's shared memory goes away; each wait is bounded too.
+        for (uint64_t qq = q; qq < q + (uint64_t)a.nstage && qq < total; ++qq)
             mbar_wait(&bars[qq % a.nstage], (uint32_t)((qq / a.nstage) & 1ull), kWaitLimitNs);
     }
 }
 
-template <int R, int WMODE>
+template <int R, int WMODE, int PREC>
 cudaError_t launch_staged_R(const MapDev &m, const TrackSet &ts, const StagedArgs &sa, int grid, int threads,
                             size_t smem, double *out, int *err, cudaStream_t st)
 {
-    auto k = score_staged_kernel<R, WMODE>;
+    auto k = score_staged_kernel<R, WMODE, PREC>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k<<<grid, threads, smem, st>>>(m, ts, sa, out, err);
     return cudaGetLastError();
 }
 
-template <int WMODE>
+template <int WMODE, int PREC>
 cudaError_t launch_staged_W(int R, const MapDev &m, const TrackSet &ts, const StagedArgs &sa, int grid, int threads,
                             size_t smem, double *out, int *err, cudaStream_t st)
 {
     switch (R) {
-    case 1: return launch_staged_R<1, WMODE>(m, ts, sa, grid, threads, smem, out, err, st);
-    case 2: return launch_staged_R<2, WMODE>(m, ts, sa, grid, threads, smem, out, err, st);
-    case 3: return launch_staged_R<3, WMODE>(m, ts, sa, grid, threads, smem, out, err, st);
-    case 4: return launch_staged_R<4, WMODE>(m, ts, sa, grid, threads, smem, out, err, st);
+    case 1: return launch_staged_R<1, WMODE, PREC>(m, ts, sa, grid, threads, smem, out, err, st);
+    case 2: return launch_staged_R<2, WMODE, PREC>(m, ts, sa, grid, threads, smem, out, err, st);
+    case 3: return launch_staged_R<3, WMODE, PREC>(m, ts, sa, grid, threads, smem, out, err, st);
+    case 4: return launch_staged_R<4, WMODE, PREC>(m, ts, sa, grid, threads, smem, out, err, st);
+    case 5: return launch_staged_R<5, WMODE, PREC>(m, ts, sa, grid, threads, smem, out, err, st);
+    case 6:
+        if (WMODE == WMODE_CONST)
+            return launch_staged_R<6, WMODE_CONST, PREC>(m, ts, sa, grid, threads, smem, out, err, st);
+        return cudaErrorInvalidValue;
     default: return cudaErrorInvalidValue;
     }
 }
 
-template <int WMODE, bool EXPLICIT>
+template <int PREC>
+cudaError_t launch_staged_P(int R, const MapDev &m, const TrackSet &ts, const StagedArgs &sa, int grid, int threads,
+                            size_t smem, double *out, int *err, cudaStream_t st)
+{
+    switch (m.wmode) {
+    case WMODE_CONST: return launch_staged_W<WMODE_CONST, PREC>(R, m, ts, sa, grid, threads, smem, out, err, st);
+    case WMODE_FREQ: return launch_staged_W<WMODE_FREQ, PREC>(R, m, ts, sa, grid, threads, smem, out, err, st);
+    default: return launch_staged_W<WMODE_PIXEL, PREC>(R, m, ts, sa, grid, threads, smem, out, err, st);
+    }
+}
+
+template <int WMODE, int PREC, bool EXPLICIT>
 cudaError_t launch_simple_W(const MapDev &m, const TrackSet &ts, const uint32_t *f3, const double *tau, uint64_t n,
                             double *out, int *err, cudaStream_t st)
 {
@@ -239,21 +304,31 @@ cudaError_t launch_simple_W(const MapDev &m, const TrackSet &ts, const uint32_t 
     const uint64_t blocks = (n + threads - 1) / threads;
     if (blocks > 0x7fffffffull) return cudaErrorInvalidValue;
     if (m.fast32)
-        score_simple_kernel<WMODE, EXPLICIT, true><<<(unsigned)blocks, threads, 0, st>>>(m, ts, f3, tau, n, out, err);
+        score_simple_kernel<WMODE, PREC, EXPLICIT, true>
+            <<<(unsigned)blocks, threads, 0, st>>>(m, ts, f3, tau, n, out, err);
     else
-        score_simple_kernel<WMODE, EXPLICIT, false><<<(unsigned)blocks, threads, 0, st>>>(m, ts, f3, tau, n, out, err);
+        score_simple_kernel<WMODE, PREC, EXPLICIT, false>
+            <<<(unsigned)blocks, threads, 0, st>>>(m, ts, f3, tau, n, out, err);
     return cudaGetLastError();
+}
+
+template <int PREC, bool EXPLICIT>
+cudaError_t launch_simple_P(const MapDev &m, const TrackSet &ts, const uint32_t *f3, const double *tau, uint64_t n,
+                            double *out, int *err, cudaStream_t st)
+{
+    switch (m.wmode) {
+    case WMODE_CONST: return launch_simple_W<WMODE_CONST, PREC, EXPLICIT>(m, ts, f3, tau, n, out, err, st);
+    case WMODE_FREQ: return launch_simple_W<WMODE_FREQ, PREC, EXPLICIT>(m, ts, f3, tau, n, out, err, st);
+    default: return launch_simple_W<WMODE_PIXEL, PREC, EXPLICIT>(m, ts, f3, tau, n, out, err, st);
+    }
 }
 
 template <bool EXPLICIT>
 cudaError_t launch_simple(const MapDev &m, const TrackSet &ts, const uint32_t *f3, const double *tau, uint64_t n,
                           double *out, int *err, cudaStream_t st)
 {
-    switch (m.wmode) {
-    case WMODE_CONST: return launch_simple_W<WMODE_CONST, EXPLICIT>(m, ts, f3, tau, n, out, err, st);
-    case WMODE_FREQ: return launch_simple_W<WMODE_FREQ, EXPLICIT>(m, ts, f3, tau, n, out, err, st);
-    default: return launch_simple_W<WMODE_PIXEL, EXPLICIT>(m, ts, f3, tau, n, out, err, st);
-    }
+    if (m.prec == PREC_FP16) return launch_simple_P<PREC_FP16, EXPLICIT>(m, ts, f3, tau, n, out, err, st);
+    return launch_simple_P<PREC_FP32, EXPLICIT>(m, ts, f3, tau, n, out, err, st);
 }
 
 // ------------------------------------------------------------------ template-params kernel
@@ -285,7 +360,7 @@ cudaError_t launch_score_generated(const MapDev &m, const TrackSet &ts, double *
     if (kernel == 2 && !m.fast32) kernel = 1;
 
     if (kernel == 2) {
-        const size_t row_bytes = (size_t)m.ldr * 8;
+        const size_t row_bytes = (size_t)m.ldr * (m.prec == PREC_FP16 ? 4 : 8);
         const size_t wrow_bytes = m.wmode == WMODE_PIXEL ? (size_t)m.ldw * 4 : 0;
         const size_t wtab_bytes = m.wmode == WMODE_FREQ ? (size_t)((m.n_f + 3) / 4 * 4) * 4 : 0;
         size_t budget = smem_optin;
@@ -297,7 +372,8 @@ cudaError_t launch_score_generated(const MapDev &m, const TrackSet &ts, double *
         if (S < 1) {
             kernel = 1;  // a single map row does not fit in shared memory
         } else {
-            const int maxR = std::max(1, std::min(tu.max_R, 4));
+            // templates held per thread: 6 fit 64 registers without a weight sum, 5 with one
+            const int maxR = std::max(1, std::min(tu.max_R, m.wmode == WMODE_CONST ? 6 : 5));
             const uint64_t cap = (uint64_t)maxR * kMaxThreads;
             const uint64_t G = (uint64_t)std::max(1, num_sms);
             const uint64_t per_cta = (n + G - 1) / G;
@@ -339,14 +415,9 @@ cudaError_t launch_score_generated(const MapDev &m, const TrackSet &ts, double *
             sa.slab_ws = m.wmode == WMODE_PIXEL ? (uint32_t)(S * m.ldw) : 0u;
             sa.wtab_floats = m.wmode == WMODE_FREQ ? (uint32_t)((m.n_f + 3) / 4 * 4) : 0u;
             if (plan) *plan = p;
-            switch (m.wmode) {
-            case WMODE_CONST:
-                return launch_staged_W<WMODE_CONST>(R, m, ts, sa, p.grid, threads, p.smem, out, err, st);
-            case WMODE_FREQ:
-                return launch_staged_W<WMODE_FREQ>(R, m, ts, sa, p.grid, threads, p.smem, out, err, st);
-            default:
-                return launch_staged_W<WMODE_PIXEL>(R, m, ts, sa, p.grid, threads, p.smem, out, err, st);
-            }
+            if (m.prec == PREC_FP16)
+                return launch_staged_P<PREC_FP16>(R, m, ts, sa, p.grid, threads, p.smem, out, err, st);
+            return launch_staged_P<PREC_FP32>(R, m, ts, sa, p.grid, threads, p.smem, out, err, st);
         }
     }
     p.kernel = 1;
