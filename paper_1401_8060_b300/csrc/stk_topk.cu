@@ -8,7 +8,9 @@
 //   2. one pass collects every template whose key prefix is at least that one
 //      (the k winners plus the rest of the boundary bucket, usually a few
 //      thousand) into a candidate buffer;
-//   3. one block sorts the candidates in shared memory and keeps the first k.
+//   3. every candidate counts the candidates ordered before it (all pairs, in
+//      parallel over many blocks); that count is its rank, and ranks below k
+//      write their hit straight to its place.
 // When the boundary bucket is too large for that (many templates agreeing in
 // their top 24 key bits, e.g. a constant map), step 3 instead runs an exact
 // radix select over the keys and then over the indices of the tied keys, in
@@ -25,7 +27,8 @@ constexpr int kBins = 4096;           // 12-bit digits
 constexpr int kPassThreads = 512;
 constexpr int kFinalThreads = 1024;
 constexpr uint32_t kCandCap = 65536;  // candidate buffer
-constexpr int kSortCap = 8192;        // candidates sorted in shared memory
+constexpr int kRankCap = 16384;       // candidates ranked by all-pairs comparison
+constexpr int kRankChunk = 64;        // candidates per ranking block (x 4 comparand lanes)
 
 struct SelState {
     unsigned int hist[kBins];
@@ -87,6 +90,8 @@ __global__ void sel_init(SelState *st)
 }
 
 // PASS 0: histogram of key[63:52]; PASS 1: of key[51:40] among keys with key[63:52] == d1.
+// The leading key bits of SNRs fall into few bins, so lanes of a warp holding the
+// same bin are merged (__match_any_sync) into one shared-memory atomic.
 template <int PASS>
 __global__ void __launch_bounds__(kPassThreads) sel_hist(const double *__restrict__ snr, uint64_t n, SelState *st)
 {
@@ -94,10 +99,27 @@ __global__ void __launch_bounds__(kPassThreads) sel_hist(const double *__restric
     for (int i = threadIdx.x; i < kBins; i += blockDim.x) h[i] = 0;
     __syncthreads();
     const unsigned int d1 = PASS ? st->d1 : 0u;
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
-        const unsigned long long key = order_key(snr[i]);
-        if (PASS == 0) atomicAdd(&h[key >> 52], 1u);
-        else if ((unsigned int)(key >> 52) == d1) atomicAdd(&h[(key >> 40) & 4095u], 1u);
+    const int lane = threadIdx.x & 31;
+    const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
+    const uint64_t w0 = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    for (uint64_t base = w0 * 128; base < n; base += warps * 128) {
+        double v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {   // four independent loads in flight per lane
+            const uint64_t i = base + u * 32 + lane;
+            v[u] = i < n ? snr[i] : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            unsigned int bin = 0xffffffffu;  // no bin
+            if (base + u * 32 + lane < n) {
+                const unsigned long long key = order_key(v[u]);
+                if (PASS == 0) bin = (unsigned int)(key >> 52);
+                else if ((unsigned int)(key >> 52) == d1) bin = (unsigned int)(key >> 40) & 4095u;
+            }
+            const unsigned int peers = __match_any_sync(0xffffffffu, bin);
+            if (bin != 0xffffffffu && lane == __ffs(peers) - 1) atomicAdd(&h[bin], (unsigned int)__popc(peers));
+        }
     }
     __syncthreads();
     for (int i = threadIdx.x; i < kBins; i += blockDim.x)
@@ -127,26 +149,35 @@ __global__ void __launch_bounds__(kPassThreads) sel_collect(const double *__rest
     const int lane = threadIdx.x & 31;
     const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
     const uint64_t w0 = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    for (uint64_t base = w0 * 32; base < n; base += warps * 32) {
-        const uint64_t i = base + lane;
-        unsigned long long key = 0;
-        bool p = false;
-        if (i < n) {
-            key = order_key(snr[i]);
-            p = (unsigned int)(key >> 40) >= pref;
+    for (uint64_t base = w0 * 128; base < n; base += warps * 128) {
+        double v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const uint64_t i = base + u * 32 + lane;
+            v[u] = i < n ? snr[i] : 0.0;
         }
-        const unsigned int m = __ballot_sync(0xffffffffu, p);
-        if (!m) continue;
-        unsigned int pos0 = 0;
-        if (lane == __ffs(m) - 1) pos0 = atomicAdd(&st->ncand, (unsigned int)__popc(m));
-        pos0 = __shfl_sync(0xffffffffu, pos0, __ffs(m) - 1);
-        if (p) {
-            const unsigned int pos = pos0 + __popc(m & ((1u << lane) - 1u));
-            if (pos < kCandCap) {
-                cand_key[pos] = key;
-                cand_idx[pos] = (unsigned int)i;
-            } else {
-                st->overflow = 1;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const uint64_t i = base + u * 32 + lane;
+            unsigned long long key = 0;
+            bool p = false;
+            if (i < n) {
+                key = order_key(v[u]);
+                p = (unsigned int)(key >> 40) >= pref;
+            }
+            const unsigned int msk = __ballot_sync(0xffffffffu, p);
+            if (!msk) continue;
+            unsigned int pos0 = 0;
+            if (lane == __ffs(msk) - 1) pos0 = atomicAdd(&st->ncand, (unsigned int)__popc(msk));
+            pos0 = __shfl_sync(0xffffffffu, pos0, __ffs(msk) - 1);
+            if (p) {
+                const unsigned int pos = pos0 + __popc(msk & ((1u << lane) - 1u));
+                if (pos < kCandCap) {
+                    cand_key[pos] = key;
+                    cand_idx[pos] = (unsigned int)i;
+                } else {
+                    st->overflow = 1;
+                }
             }
         }
     }
@@ -245,57 +276,88 @@ __device__ void select_generic(const Src &src, int k, unsigned long long *out_ke
     __syncthreads();
 }
 
+__device__ __forceinline__ void write_hit(const double *snr, unsigned int t, const TrackSet &ts, const MapDev &m,
+                                          stk_hit *out)
+{
+    stk_hit hit;
+    hit.snr = snr[t];
+    hit.index = ts.offset + t;
+    uint32_t f[3];
+    double tau;
+    draw_track(ts.seed, ts.offset + t, (uint32_t)m.n_f, ts.tau_max, f, tau);
+    hit.f[0] = f[0]; hit.f[1] = f[1]; hit.f[2] = f[2];
+    hit.reserved = 0;
+    hit.tau = tau;
+    *out = hit;
+}
+
+// Rank of each candidate = number of candidates ordered before it; block b
+// ranks candidates [64 b, 64 b + 64), four threads per candidate each taking a
+// quarter of every shared-memory tile of comparands (all lanes of a warp read
+// the same comparand: a broadcast).
+constexpr int kRankTile = 1024;
+
+__global__ void __launch_bounds__(256) sel_rank(const double *__restrict__ snr, const SelState *st,
+                                                const unsigned long long *__restrict__ cand_key,
+                                                const unsigned int *__restrict__ cand_idx, int k, TrackSet ts,
+                                                MapDev m, stk_hit *out)
+{
+    __shared__ unsigned int part[4][kRankChunk];
+    __shared__ unsigned long long tk[kRankTile];
+    __shared__ unsigned int ti[kRankTile];
+    const unsigned int nc = st->ncand;
+    if (st->overflow || nc > (unsigned int)kRankCap) return;
+    const unsigned int c0 = blockIdx.x * kRankChunk;
+    if (c0 >= nc) return;
+    const int c = threadIdx.x & (kRankChunk - 1), qd = threadIdx.x / kRankChunk;
+    const unsigned int me = c0 + c;
+    const bool valid = me < nc;
+    const unsigned long long mk = valid ? cand_key[me] : 0ull;
+    const unsigned int mi = valid ? cand_idx[me] : 0xffffffffu;
+    unsigned int before_me = 0;
+    for (unsigned int t0 = 0; t0 < nc; t0 += kRankTile) {
+        const unsigned int tn = min((unsigned int)kRankTile, nc - t0);
+        for (unsigned int j = threadIdx.x; j < tn; j += blockDim.x) {
+            tk[j] = cand_key[t0 + j];
+            ti[j] = cand_idx[t0 + j];
+        }
+        __syncthreads();
+        for (unsigned int j = qd; j < tn; j += 4) before_me += before(tk[j], ti[j], mk, mi) ? 1u : 0u;
+        __syncthreads();
+    }
+    part[qd][c] = before_me;
+    __syncthreads();
+    if (qd == 0 && valid) {
+        const unsigned int rank = part[0][c] + part[1][c] + part[2][c] + part[3][c];
+        if (rank < (unsigned int)k) write_hit(snr, mi, ts, m, out + rank);
+    }
+}
+
+// Fallback when the candidates overflowed or exceed kRankCap: exact selection in
+// one block (radix select over keys, then over the tied indices), bitonic sort of
+// the k winners.  Returns at once otherwise.
 __global__ void __launch_bounds__(kFinalThreads)
-    sel_final(const double *__restrict__ snr, uint64_t n, const SelState *st, const unsigned long long *cand_key,
-              const unsigned int *cand_idx, int k, TrackSet ts, MapDev m, stk_hit *out)
+    sel_generic(const double *__restrict__ snr, uint64_t n, const SelState *st, const unsigned long long *cand_key,
+                const unsigned int *cand_idx, int k, TrackSet ts, MapDev m, stk_hit *out)
 {
     extern __shared__ unsigned long long sh[];
     __shared__ unsigned int hp[kFinalThreads];
     __shared__ unsigned int cnt;
     const unsigned int ncand = st->ncand;
-    const bool small = !st->overflow && ncand <= (unsigned int)kSortCap;
+    if (!st->overflow && ncand <= (unsigned int)kRankCap) return;
     int P = 1;
-    if (small) {
-        while (P < (int)ncand) P <<= 1;
-    } else {
-        while (P < k) P <<= 1;
-    }
+    while (P < k) P <<= 1;
     unsigned long long *key = sh;
     unsigned int *ix = reinterpret_cast<unsigned int *>(sh + P);
-    if (small) {
-        for (int i = threadIdx.x; i < P; i += blockDim.x) {
-            if (i < (int)ncand) {
-                key[i] = cand_key[i];
-                ix[i] = cand_idx[i];
-            } else {
-                key[i] = 0ull;      // below every real key
-                ix[i] = 0xffffffffu;
-            }
-        }
-        __syncthreads();
-    } else {
-        Src src{snr, cand_key, cand_idx, st->overflow ? n : (uint64_t)ncand, st->overflow != 0};
-        select_generic(src, k, key, ix, hp, &cnt);
-        for (int i = k + threadIdx.x; i < P; i += blockDim.x) {
-            key[i] = 0ull;
-            ix[i] = 0xffffffffu;
-        }
-        __syncthreads();
+    Src src{snr, cand_key, cand_idx, st->overflow ? n : (uint64_t)ncand, st->overflow != 0};
+    select_generic(src, k, key, ix, hp, &cnt);
+    for (int i = k + threadIdx.x; i < P; i += blockDim.x) {
+        key[i] = 0ull;   // below every real key
+        ix[i] = 0xffffffffu;
     }
+    __syncthreads();
     bitonic_sort(key, ix, P);
-    for (int i = threadIdx.x; i < k; i += blockDim.x) {
-        const unsigned int t = ix[i];
-        stk_hit hit;
-        hit.snr = snr[t];
-        hit.index = ts.offset + t;
-        uint32_t f[3];
-        double tau;
-        draw_track(ts.seed, ts.offset + t, (uint32_t)m.n_f, ts.tau_max, f, tau);
-        hit.f[0] = f[0]; hit.f[1] = f[1]; hit.f[2] = f[2];
-        hit.reserved = 0;
-        hit.tau = tau;
-        out[i] = hit;
-    }
+    for (int i = threadIdx.x; i < k; i += blockDim.x) write_hit(snr, ix[i], ts, m, out + i);
 }
 
 constexpr size_t align256(size_t x) { return (x + 255) / 256 * 256; }
@@ -316,18 +378,19 @@ cudaError_t launch_select_topk(const double *snr, uint64_t n, int k, const Track
     unsigned long long *ckey = (unsigned long long *)(p + align256(sizeof(SelState)));
     unsigned int *cidx = (unsigned int *)(p + align256(sizeof(SelState)) + align256((size_t)kCandCap * 8));
     const uint64_t blocks = (n + kPassThreads * 8 - 1) / (kPassThreads * 8);
-    const int grid = (int)(blocks < 296 ? (blocks < 1 ? 1 : blocks) : 296);
+    const int grid = (int)(blocks < 592 ? (blocks < 1 ? 1 : blocks) : 592);
     sel_init<<<1, 1024, 0, st>>>(ss);
     sel_hist<0><<<grid, kPassThreads, 0, st>>>(snr, n, ss);
     sel_pick<0><<<1, kFinalThreads, 0, st>>>(ss, (unsigned int)k);
     sel_hist<1><<<grid, kPassThreads, 0, st>>>(snr, n, ss);
     sel_pick<1><<<1, kFinalThreads, 0, st>>>(ss, (unsigned int)k);
     sel_collect<<<grid, kPassThreads, 0, st>>>(snr, n, ss, ckey, cidx);
-    const size_t smem = (size_t)kSortCap * 12;
-    cudaError_t e = cudaFuncSetAttribute(sel_final, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    sel_rank<<<kRankCap / kRankChunk, 256, 0, st>>>(snr, ss, ckey, cidx, k, ts, m, out);
+    const size_t smem = (size_t)STK_MAX_K * 12;
+    cudaError_t e = cudaFuncSetAttribute(sel_generic, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    sel_final<<<1, kFinalThreads, smem, st>>>(snr, n, ss, ckey, cidx, k, ts, m, out);
-    if (launches) *launches = 7;
+    sel_generic<<<1, kFinalThreads, smem, st>>>(snr, n, ss, ckey, cidx, k, ts, m, out);
+    if (launches) *launches = 8;
     return cudaGetLastError();
 }
 
