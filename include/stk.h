@@ -164,6 +164,53 @@ STK_API int stk_set_profiling(stk_ctx *ctx, int enable);
  * count of that call.  Requires profiling on; synchronises the stream. */
 STK_API int stk_last_timings(stk_ctx *ctx, double out[3]);
 
+/* ---- many maps in one launch --------------------------------------------
+ * A search records the loudest SNR of every map (Sec. V: year-long runs cut
+ * into maps, and unphysical time shifts n_ts of each map for the background;
+ * Eqs. 9-10 count that work).  A batch scores many maps of uneven size with
+ * one persistent kernel: CTAs take (map, template block) tiles from a work
+ * counter, largest maps first, stream each tile's map through shared memory,
+ * and keep every tile's k loudest; a second kernel merges each map's tiles.
+ * The launch sequence is recorded once in a CUDA graph and replayed. */
+typedef struct stk_batch stk_batch; /* opaque */
+
+#define STK_ECANCELED -6           /* a batch call was cancelled through stk_batch_cancel */
+#define STK_BATCH_MAX_K 32         /* largest k per map in stk_batch_score */
+
+/* Group n_maps maps (loaded on ctx; keep them alive while the batch exists)
+ * with per-map template ranges: map i scores templates offsets[i] ..
+ * offsets[i] + n_tracks[i] - 1 drawn with seeds[i] (n_tracks[i] in 1 .. 2^32-1),
+ * all with delays uniform in (-tau_max_s, tau_max_s).  All maps must share the
+ * statistic (weighted or STK_NORM_PAPER), the storage precision and the
+ * weighting pattern, and satisfy (n_t - 1)^2 (2 n_f - 1) < 2^32.
+ * Errors: STK_EINVAL, STK_ENOMEM, STK_ECUDA. */
+STK_API int stk_batch_create(stk_ctx *ctx, const stk_map *const *maps, int n_maps, const uint64_t *n_tracks,
+                             const uint64_t *seeds, const uint64_t *offsets, double tau_max_s, stk_batch **out);
+
+/* Free a batch (waits for the context's stream).  NULL is a no-op. */
+STK_API void stk_batch_destroy(stk_batch *batch);
+
+/* Score every template of every map and write map i's k loudest (SNR
+ * descending, then index ascending) to out[i*k .. i*k + k - 1]; out is device
+ * memory, or host memory with STK_OUT_HOST (the call then waits and returns
+ * the batch's status).  k in 1 .. STK_BATCH_MAX_K and <= every n_tracks[i].
+ * Errors: STK_EINVAL, STK_ENOMEM, STK_ECUDA; STK_ECANCELED or STK_ETIMEOUT
+ * (from this call with STK_OUT_HOST, else from the next stk_sync). */
+STK_API int stk_batch_score(stk_batch *batch, int k, stk_hit *out, unsigned flags);
+
+/* Set (on != 0) or clear the batch's cancel flag.  It lives in host memory the
+ * GPU reads: the persistent kernel checks it before taking each tile, so a
+ * running stk_batch_score stops within one tile and reports STK_ECANCELED.
+ * The flag stays set until cleared. */
+STK_API int stk_batch_cancel(stk_batch *batch, int on);
+
+/* Autotuner: time every candidate launch shape (threads per block, templates
+ * per thread, slab buffers) on a sample of this batch's tiles and keep the
+ * fastest for later stk_batch_score calls.  out (may be NULL) receives
+ * {threads, templates per thread, slab buffers, sample time in ns}.
+ * Errors: STK_EINVAL, STK_ECUDA. */
+STK_API int stk_batch_tune(stk_batch *batch, int k, int64_t out[4]);
+
 /* ---- scoring without allocation ------------------------------------------
  * The paper has no counterpart to this call; it exists for callers that
  * cannot call cudaMalloc when they score: code whose device memory belongs to

@@ -19,7 +19,7 @@ import numpy as np
 from . import _lib as L
 from ._lib import HIT_DTYPE, STK_MAX_K  # noqa: F401
 
-__all__ = ["Context", "Map", "StkError", "HIT_DTYPE", "STK_MAX_K", "lib"]
+__all__ = ["Context", "Map", "Batch", "StkError", "HIT_DTYPE", "STK_MAX_K", "lib"]
 
 lib = L.lib
 
@@ -217,3 +217,61 @@ class Context:
         a = (C.c_double * 3)()
         self._check(lib().stk_last_timings(self._h, a))
         return dict(score_ms=a[0], select_ms=a[1], launches=int(a[2]))
+
+
+class Batch:
+    """Many maps scored in one persistent launch (stk_batch_create / stk_batch_score).
+
+    maps: list of Map (all loaded on ctx, same statistic, precision and weighting);
+    n_tracks, seeds, offsets: one per map; tau_max: seconds.
+    """
+
+    def __init__(self, ctx: Context, maps, n_tracks, seeds, offsets=None, tau_max: float = 0.010):
+        n = len(maps)
+        self._ctx = ctx
+        self._maps = list(maps)           # keep them alive
+        self.n_maps = n
+        hs = (C.c_void_p * n)(*[m.handle for m in maps])
+        nt = np.ascontiguousarray(n_tracks, dtype=np.uint64)
+        sd = np.ascontiguousarray(seeds, dtype=np.uint64)
+        of = np.ascontiguousarray(offsets if offsets is not None else np.zeros(n), dtype=np.uint64)
+        if not (nt.size == sd.size == of.size == n):
+            raise ValueError("n_tracks, seeds and offsets need one entry per map")
+        h = C.c_void_p()
+        ctx._bind_stream()
+        ctx._check(lib().stk_batch_create(ctx._h, hs, n, C.c_void_p(nt.ctypes.data), C.c_void_p(sd.ctypes.data),
+                                          C.c_void_p(of.ctypes.data), float(tau_max), C.byref(h)))
+        self._h = h
+
+    def score(self, k: int, out=None):
+        """Each map's k loudest: numpy HIT_DTYPE [n_maps][k] (waits), or fills a CUDA
+        uint8 tensor of n_maps*k*40 bytes asynchronously."""
+        self._ctx._bind_stream()
+        if out is None:
+            res = np.zeros(self.n_maps * k, dtype=HIT_DTYPE)
+            self._ctx._check(lib().stk_batch_score(self._h, int(k), C.c_void_p(res.ctypes.data), L.STK_OUT_HOST))
+            return res.reshape(self.n_maps, k)
+        if not out.is_cuda or out.numel() * out.element_size() < 40 * k * self.n_maps:
+            raise ValueError("out must be a CUDA tensor of at least n_maps*k*40 bytes")
+        self._ctx._check(lib().stk_batch_score(self._h, int(k), C.c_void_p(out.data_ptr()), 0))
+        return out
+
+    def cancel(self, on: bool = True):
+        self._ctx._check(lib().stk_batch_cancel(self._h, 1 if on else 0))
+
+    def tune(self, k: int) -> dict:
+        self._ctx._bind_stream()
+        a = (C.c_int64 * 4)()
+        self._ctx._check(lib().stk_batch_tune(self._h, int(k), a))
+        return dict(threads=int(a[0]), R=int(a[1]), nstage=int(a[2]), sample_ms=a[3] / 1e6)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().stk_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -13,7 +13,8 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libstk.so")
 
-STK_OK, STK_EINVAL, STK_ENOMEM, STK_ECUDA, STK_ETIMEOUT, STK_ESTATE = 0, -1, -2, -3, -4, -5
+STK_OK, STK_EINVAL, STK_ENOMEM, STK_ECUDA, STK_ETIMEOUT, STK_ESTATE, STK_ECANCELED = 0, -1, -2, -3, -4, -5, -6
+STK_BATCH_MAX_K = 32
 STK_HOST_PTR, STK_SIGMA_PER_FREQ, STK_NORM_PAPER, STK_FP16 = 0x1, 0x2, 0x4, 0x8
 STK_OUT_HOST = 0x1
 STK_MAX_K = 4096
@@ -42,6 +43,11 @@ SIGNATURES = [
     ("stk_set_option", C.c_int, [_vp, C.c_int, C.c_int64]),
     ("stk_last_plan", C.c_int, [_vp, C.POINTER(C.c_int64)]),
     ("stk_last_error", C.c_char_p, [_vp]),
+    ("stk_batch_create", C.c_int, [_vp, _vp, C.c_int, _vp, _vp, _vp, C.c_double, C.POINTER(_vp)]),
+    ("stk_batch_destroy", None, [_vp]),
+    ("stk_batch_score", C.c_int, [_vp, C.c_int, _vp, C.c_uint]),
+    ("stk_batch_cancel", C.c_int, [_vp, C.c_int]),
+    ("stk_batch_tune", C.c_int, [_vp, C.c_int, C.POINTER(C.c_int64)]),
     ("stk_score_noalloc", C.c_int, [_vp, C.c_uint64, C.c_uint64, C.c_uint64, C.c_double, C.c_int, _vp, _vp,
                                     _vp]),
 ]

@@ -11,44 +11,13 @@
 #include <cuda_fp16.h>
 
 #include "stk_internal.cuh"
+#include "stk_objects.cuh"
 
 using namespace stk;
 
-struct stk_ctx {
-    int device = 0;
-    cudaStream_t stream = nullptr;
-    int num_sms = 0;
-    size_t smem_optin = 0;
-    bool have_tracks = false;
-    TrackSet ts{};
-    int *d_err = nullptr;          // device error/flag word
-    double *snr_buf = nullptr;     // scratch: one SNR per template
-    size_t snr_cap = 0;
-    void *sel_buf = nullptr;       // scratch: selection state
-    size_t sel_cap = 0;
-    stk_hit *hits_dev = nullptr;   // STK_MAX_K records
-    uint32_t *small_dev = nullptr; // track_params: f[3] + pad, tau, bins
-    size_t small_cap = 0;
-    Tuning tune{};
-    ScorePlan plan{};
-    bool profiling = false;
-    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
-    bool timed = false;
-    int last_launches = 0;
-    std::string err;
-};
-
-struct stk_map {
-    stk_ctx *ctx = nullptr;
-    MapDev dev{};
-    void *rec_buf = nullptr;
-    void *w_buf = nullptr;
-    unsigned flags = 0;
-};
-
 static thread_local std::string g_create_err;
 
-static int set_err(stk_ctx *c, int code, const char *fmt, ...)
+int set_err(stk_ctx *c, int code, const char *fmt, ...)
 {
     char buf[512];
     va_list ap;
@@ -60,13 +29,23 @@ static int set_err(stk_ctx *c, int code, const char *fmt, ...)
     return code;
 }
 
-#define CUDA_TRY(ctx, call)                                                                                         \
-    do {                                                                                                           \
-        cudaError_t e_ = (call);                                                                                   \
-        if (e_ != cudaSuccess)                                                                                     \
-            return set_err((ctx), e_ == cudaErrorMemoryAllocation ? STK_ENOMEM : STK_ECUDA, "%s: %s (%s:%d)", #call, \
-                           cudaGetErrorString(e_), __FILE__, __LINE__);                                            \
-    } while (0)
+int read_err_flags(stk_ctx *c, int *flags)
+{
+    int h = 0;
+    CUDA_TRY(c, cudaMemcpyAsync(&h, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    CUDA_TRY(c, cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
+    *flags = h;
+    return STK_OK;
+}
+
+int flags_to_status(stk_ctx *c, int f)
+{
+    if (f & ERR_TIMEOUT) return set_err(c, STK_ETIMEOUT, "a bounded in-kernel wait for a map slab gave up");
+    if (f & ERR_CANCELED) return set_err(c, STK_ECANCELED, "batch cancelled through stk_batch_cancel");
+    if (f & ERR_BADTRACK) return set_err(c, STK_EINVAL, "explicit template with a control bin outside [0, n_f)");
+    return STK_OK;
+}
 
 namespace {
 
@@ -183,23 +162,6 @@ int ensure(stk_ctx *c, void **buf, size_t *cap, size_t need)
         return set_err(c, STK_ENOMEM, "cudaMalloc(%zu bytes): %s", need, cudaGetErrorString(e));
     }
     *cap = need;
-    return STK_OK;
-}
-
-int read_err_flags(stk_ctx *c, int *flags)
-{
-    int h = 0;
-    CUDA_TRY(c, cudaMemcpyAsync(&h, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
-    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
-    CUDA_TRY(c, cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
-    *flags = h;
-    return STK_OK;
-}
-
-int flags_to_status(stk_ctx *c, int f)
-{
-    if (f & ERR_TIMEOUT) return set_err(c, STK_ETIMEOUT, "a bounded in-kernel wait for a map slab gave up");
-    if (f & ERR_BADTRACK) return set_err(c, STK_EINVAL, "explicit template with a control bin outside [0, n_f)");
     return STK_OK;
 }
 

@@ -67,6 +67,7 @@ enum : int {
     ERR_BADINPUT = 4,  // map packing saw a non-finite y or a bad sigma
     FLAG_SIGMA_VARIES = 8,  // map packing saw more than one sigma value
     ERR_FP16_RANGE = 16,    // |y| / sigma beyond the FP16 range
+    ERR_CANCELED = 32,      // a batch kernel saw its cancel flag
 };
 
 // ---------------------------------------------------------------- Philox4x64-10

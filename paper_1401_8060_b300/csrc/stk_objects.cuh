@@ -1,0 +1,63 @@
+// Library-private definitions of the opaque handles and error helpers, shared
+// by the C-ABI translation units.
+#pragma once
+
+#include <string>
+
+#include "stk_internal.cuh"
+
+using stk::MapDev;
+using stk::ScorePlan;
+using stk::TrackSet;
+using stk::Tuning;
+
+
+struct stk_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int num_sms = 0;
+    size_t smem_optin = 0;
+    bool have_tracks = false;
+    TrackSet ts{};
+    int *d_err = nullptr;          // device error/flag word
+    double *snr_buf = nullptr;     // scratch: one SNR per template
+    size_t snr_cap = 0;
+    void *sel_buf = nullptr;       // scratch: selection state
+    size_t sel_cap = 0;
+    stk_hit *hits_dev = nullptr;   // STK_MAX_K records
+    uint32_t *small_dev = nullptr; // track_params: f[3] + pad, tau, bins
+    size_t small_cap = 0;
+    Tuning tune{};
+    ScorePlan plan{};
+    bool profiling = false;
+    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+    bool timed = false;
+    int last_launches = 0;
+    std::string err;
+};
+
+struct stk_map {
+    stk_ctx *ctx = nullptr;
+    MapDev dev{};
+    void *rec_buf = nullptr;
+    void *w_buf = nullptr;
+    unsigned flags = 0;
+};
+
+// Record a formatted message on the context (or the thread's creation message
+// when c is NULL) and return code.
+int set_err(stk_ctx *c, int code, const char *fmt, ...);
+
+// Read and clear the device error word (synchronises the stream).
+int read_err_flags(stk_ctx *c, int *flags);
+// Map error bits to a status code (with message).
+int flags_to_status(stk_ctx *c, int flags);
+
+#define CUDA_TRY(ctx, call)                                                                                         \
+    do {                                                                                                           \
+        cudaError_t e_ = (call);                                                                                   \
+        if (e_ != cudaSuccess)                                                                                     \
+            return set_err((ctx), e_ == cudaErrorMemoryAllocation ? STK_ENOMEM : STK_ECUDA, "%s: %s (%s:%d)", #call, \
+                           cudaGetErrorString(e_), __FILE__, __LINE__);                                            \
+    } while (0)
+

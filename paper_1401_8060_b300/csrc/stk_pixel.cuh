@@ -1,0 +1,89 @@
+// Per-pixel and per-template device code shared by the scoring kernels
+// (single map and batched): pixel record decoding, the Eq. 7 accumulation,
+// the normalisation, and the order used for selection.
+#pragma once
+
+#include <cuda_fp16.h>
+
+#include "stk_internal.cuh"
+
+namespace stk {
+
+// ------------------------------------------------------------------ pixel records
+template <int PREC>
+struct Pix;
+
+template <>
+struct Pix<PREC_FP32> {  // {float |z|, Q0.32 arg z}; the weight array holds w = sigma^-2
+    using Rec = uint2;
+    __device__ static __forceinline__ float mag(Rec v) { return __uint_as_float(v.x); }
+    __device__ static __forceinline__ uint32_t arg(Rec v) { return v.y; }
+    __device__ static __forceinline__ Rec load_global(const void *p, size_t i) { return __ldg((const uint2 *)p + i); }
+};
+
+template <>
+struct Pix<PREC_FP16> {  // low half: FP16 |y|/sigma; high half: arg in Q0.16 turns; weights hold r = 1/sigma
+    using Rec = uint32_t;
+    __device__ static __forceinline__ float mag(Rec v)
+    {
+        return __half2float(__ushort_as_half((unsigned short)(v & 0xffffu)));
+    }
+    __device__ static __forceinline__ uint32_t arg(Rec v) { return v & 0xffff0000u; }
+    __device__ static __forceinline__ Rec load_global(const void *p, size_t i)
+    {
+        return __ldg((const unsigned int *)p + i);
+    }
+};
+
+// One pixel of Eq. 7: acc += |z| cos(theta + 2 pi arg z), W += weight.
+// FP32 records carry |z| and wv = sigma^-2; FP16 records carry |y|/sigma and
+// wv = 1/sigma, so |z| = mag wv and the weight is wv^2.
+template <int PREC, int WMODE>
+__device__ __forceinline__ void accumulate(typename Pix<PREC>::Rec v, uint32_t bin, const Phase &ph, float wv,
+                                           float &acc, float &W)
+{
+    const float c = cos_turn(pixel_turn(bin, ph, Pix<PREC>::arg(v)));
+    float mg = Pix<PREC>::mag(v);
+    if (PREC == PREC_FP16 && WMODE != WMODE_CONST) mg *= wv;
+    acc = fmaf(mg, c, acc);
+    if (WMODE != WMODE_CONST) W = (PREC == PREC_FP16) ? fmaf(wv, wv, W) : W + wv;
+}
+
+// Normalisation (Eq. 7 with the weighting of the footnote to Eq. 5), FP64 on the
+// GPU.  Weighted form with varying weights: S / sqrt(W), where 1 / sqrt(W) is an
+// FP32 seed refined by one Newton-Raphson step y1 = y0 (3 - W y0^2) / 2 in FP64
+// (relative error ~1e-13).  Constant weight or paper form: S times a constant.
+template <int WMODE>
+__device__ __forceinline__ double finalize_snr(float acc, float W, const MapDev &m)
+{
+    if (WMODE == WMODE_CONST || m.paper) return (double)acc * m.norm;
+    const double y0 = (double)rsqrtf(W);
+    const double t = (double)W * y0 * y0;
+    return (double)acc * (y0 * fma(-0.5, t, 1.5));
+}
+
+// ------------------------------------------------------------------ selection order
+// Order-preserving 64-bit key of an FP64 SNR (-0 and +0 share one key).
+__device__ __forceinline__ unsigned long long order_key(double x)
+{
+    if (x == 0.0) x = 0.0;
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+
+// "a before b": larger key, then smaller index.
+__device__ __forceinline__ bool before(unsigned long long ka, unsigned int ia, unsigned long long kb, unsigned int ib)
+{
+    return ka > kb || (ka == kb && ia < ib);
+}
+
+// floor(N / d) for N < 2^32 from magic = ceil(2^(32+shift) / d) < 2^32: the
+// multiply-shift estimate is floor(N / d) or one more, and one compare fixes it.
+__device__ __forceinline__ uint32_t div_corrected(uint32_t N, uint32_t magic, int shift, uint32_t d)
+{
+    uint32_t q = __umulhi(N, magic) >> shift;
+    q -= (q * d > N) ? 1u : 0u;
+    return q;
+}
+
+}  // namespace stk

@@ -21,6 +21,7 @@
 #include <cstdio>
 
 #include "stk_internal.cuh"
+#include "stk_pixel.cuh"
 
 namespace stk {
 
@@ -28,59 +29,6 @@ namespace {
 
 constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s per slab wait
 constexpr int kMaxThreads = 1024;
-
-// ------------------------------------------------------------------ pixel records
-template <int PREC>
-struct Pix;
-
-template <>
-struct Pix<PREC_FP32> {  // {float |z|, Q0.32 arg z}; the weight array holds w = sigma^-2
-    using Rec = uint2;
-    __device__ static __forceinline__ float mag(Rec v) { return __uint_as_float(v.x); }
-    __device__ static __forceinline__ uint32_t arg(Rec v) { return v.y; }
-    __device__ static __forceinline__ Rec load_global(const void *p, size_t i) { return __ldg((const uint2 *)p + i); }
-};
-
-template <>
-struct Pix<PREC_FP16> {  // low half: FP16 |y|/sigma; high half: arg in Q0.16 turns; weights hold r = 1/sigma
-    using Rec = uint32_t;
-    __device__ static __forceinline__ float mag(Rec v)
-    {
-        return __half2float(__ushort_as_half((unsigned short)(v & 0xffffu)));
-    }
-    __device__ static __forceinline__ uint32_t arg(Rec v) { return v & 0xffff0000u; }
-    __device__ static __forceinline__ Rec load_global(const void *p, size_t i)
-    {
-        return __ldg((const unsigned int *)p + i);
-    }
-};
-
-// One pixel of Eq. 7: acc += |z| cos(theta + 2 pi arg z), W += weight.
-// FP32 records carry |z| and wv = sigma^-2; FP16 records carry |y|/sigma and
-// wv = 1/sigma, so |z| = mag wv and the weight is wv^2.
-template <int PREC, int WMODE>
-__device__ __forceinline__ void accumulate(typename Pix<PREC>::Rec v, uint32_t bin, const Phase &ph, float wv,
-                                           float &acc, float &W)
-{
-    const float c = cos_turn(pixel_turn(bin, ph, Pix<PREC>::arg(v)));
-    float mg = Pix<PREC>::mag(v);
-    if (PREC == PREC_FP16 && WMODE != WMODE_CONST) mg *= wv;
-    acc = fmaf(mg, c, acc);
-    if (WMODE != WMODE_CONST) W = (PREC == PREC_FP16) ? fmaf(wv, wv, W) : W + wv;
-}
-
-// Normalisation (Eq. 7 with the weighting of the footnote to Eq. 5), FP64 on the
-// GPU.  Weighted form with varying weights: S / sqrt(W), where 1 / sqrt(W) is an
-// FP32 seed refined by one Newton-Raphson step y1 = y0 (3 - W y0^2) / 2 in FP64
-// (relative error ~1e-13).  Constant weight or paper form: S times a constant.
-template <int WMODE>
-__device__ __forceinline__ double finalize_snr(float acc, float W, const MapDev &m)
-{
-    if (WMODE == WMODE_CONST || m.paper) return (double)acc * m.norm;
-    const double y0 = (double)rsqrtf(W);
-    const double t = (double)W * y0 * y0;
-    return (double)acc * (y0 * fma(-0.5, t, 1.5));
-}
 
 // ------------------------------------------------------------------ simple kernel
 template <int WMODE, int PREC, bool EXPLICIT, bool FAST32>

@@ -18,6 +18,7 @@
 #include <cstdint>
 
 #include "stk_internal.cuh"
+#include "stk_pixel.cuh"
 
 namespace stk {
 
@@ -38,13 +39,6 @@ struct SelState {
     unsigned int overflow; // candidates exceeded kCandCap
     unsigned int pad[3];
 };
-
-__device__ __forceinline__ unsigned long long order_key(double x)
-{
-    if (x == 0.0) x = 0.0;  // -0 and +0 compare equal: one key
-    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-    return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
-}
 
 // Block-wide: given hist[0..nbins) in shared or global memory, find the digit d
 // with above(d) < krem <= above(d) + hist[d], where above(d) = sum of bins > d.
@@ -181,12 +175,6 @@ __global__ void __launch_bounds__(kPassThreads) sel_collect(const double *__rest
             }
         }
     }
-}
-
-// "a before b": larger key, then smaller index.
-__device__ __forceinline__ bool before(unsigned long long ka, unsigned int ia, unsigned long long kb, unsigned int ib)
-{
-    return ka > kb || (ka == kb && ia < ib);
 }
 
 // Bitonic sort of P (power of two) entries in shared memory, "before" first.
