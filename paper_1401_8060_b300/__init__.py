@@ -13,6 +13,7 @@ device memory and the CUDA stream.
 from __future__ import annotations
 
 import ctypes as C
+import weakref
 
 import numpy as np
 
@@ -48,6 +49,7 @@ class Map:
 
     def __init__(self, ctx, handle, n_t, n_f, flags):
         self._ctx, self._h, self.n_t, self.n_f, self.flags = ctx, handle, n_t, n_f, flags
+        ctx._children.add(self)
 
     @property
     def handle(self):
@@ -80,6 +82,7 @@ class Context:
             raise StkError(rc, lib().stk_last_error(None).decode())
         self._h = h
         self._torch = torch
+        self._children = weakref.WeakSet()   # maps and batches: freed before the context
 
     # ---- plumbing
     def _stream_ptr(self):
@@ -96,6 +99,8 @@ class Context:
 
     def close(self):
         if getattr(self, "_h", None):
+            for child in sorted(list(self._children), key=lambda c: 0 if isinstance(c, Batch) else 1):
+                child.close()           # batches first, then maps
             lib().stk_destroy(self._h)
             self._h = None
 
@@ -242,6 +247,7 @@ class Batch:
         ctx._check(lib().stk_batch_create(ctx._h, hs, n, C.c_void_p(nt.ctypes.data), C.c_void_p(sd.ctypes.data),
                                           C.c_void_p(of.ctypes.data), float(tau_max), C.byref(h)))
         self._h = h
+        ctx._children.add(self)
 
     def score(self, k: int, out=None):
         """Each map's k loudest: numpy HIT_DTYPE [n_maps][k] (waits), or fills a CUDA

@@ -321,7 +321,15 @@ cudaError_t launch_batch_R(const BatchArgs &a, int grid, int threads, size_t sme
 {
     auto k = score_batch_kernel<R, WMODE, PREC>;
     if (set_attr) {
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncAttributes fa;
+        cudaError_t e = cudaFuncGetAttributes(&fa, k);
+        if (e != cudaSuccess) return e;
+        int dev = 0, optin = 0;
+        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+        if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess)
+            return e;
+        if (smem + fa.sharedSizeBytes > (size_t)optin) return cudaErrorInvalidConfiguration;
+        e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
     k<<<grid, threads, smem, st>>>(a);
@@ -417,7 +425,8 @@ int configure(stk_batch *b, int threads, int R, int nstage)
     uint32_t max_nf = 0;
     for (auto *m : b->maps) max_nf = std::max<uint32_t>(max_nf, (uint32_t)m->dev.n_f);
     const uint32_t wtab = b->wmode == WMODE_FREQ ? (max_nf + 3) / 4 * 4 : 0;
-    const size_t fixed = (size_t)wtab * 4 + (size_t)nstage * 8 + (size_t)kMaxWarps * STK_BATCH_MAX_K * 12 + 64;
+    // room for the kernel's own static shared memory (the tile index, aligned) and slack
+    const size_t fixed = (size_t)wtab * 4 + (size_t)nstage * 8 + (size_t)kMaxWarps * STK_BATCH_MAX_K * 12 + 1024;
     if (c->smem_optin <= fixed) return set_err(c, STK_EINVAL, "shared memory too small for the batch");
     const uint32_t slot = (uint32_t)((c->smem_optin - fixed) / nstage / 16 * 16);
     const uint32_t tile = (uint32_t)(R * threads);
