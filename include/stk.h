@@ -150,6 +150,30 @@ STK_API int stk_track_params(stk_ctx *ctx, const stk_map *map, uint64_t g, uint3
 STK_API int stk_score_explicit(stk_ctx *ctx, const stk_map *map, const uint32_t *f3_dev, const double *tau_dev,
                        uint64_t n, double *out_snr_dev);
 
+/* ---- continuous templates (refinement of the loudest) -------------------
+ * The follow-up of the loudest events (Sec. V) refines a template's control
+ * frequencies and delay continuously.  Control frequencies f0, f1, f2 are real
+ * numbers in bins; column j of the curve sits at
+ *   x_j = ((M-j)^2 f0 + 2 (M-j) j f1 + j^2 f2) / M^2   (clamped to [0, n_f - 1]),
+ * the map is interpolated linearly in frequency between bins floor(x_j) and
+ * floor(x_j) + 1, and the phase uses the continuous frequency f_min + x_j df:
+ *   S = sum_j Re[exp(2 pi i (f_min + x_j df) tau) z(j, x_j)],  W = sum_j w(j, x_j),
+ *   SNR = S / sqrt(W), or S / N with STK_NORM_PAPER (Eq. 7 at integer bins).
+ * f3_dev: float [n][3]; tau_dev: float [n] seconds; device memory, caller-owned.
+ * Arithmetic is FP32 except the curve position and phase argument (FP64). */
+
+/* snr_dev[i] = SNR of continuous template i (float [n]).  Errors: STK_EINVAL, STK_ECUDA. */
+STK_API int stk_interp_forward(stk_ctx *ctx, const stk_map *map, const float *f3_dev, const float *tau_dev,
+                               uint64_t n, float *snr_dev);
+
+/* Adjoint of stk_interp_forward: for g_dev[i] = dL/dSNR_i writes
+ * grad_f3_dev[i][q] = g_i dSNR_i/df_q and grad_tau_dev[i] = g_i dSNR_i/dtau
+ * (zero contribution from columns clamped to the band edge; at bin knots the
+ * statistic has a kink and the one-sided derivative from above is used).
+ * Errors: STK_EINVAL, STK_ECUDA. */
+STK_API int stk_interp_adjoint(stk_ctx *ctx, const stk_map *map, const float *f3_dev, const float *tau_dev,
+                               const float *g_dev, uint64_t n, float *grad_f3_dev, float *grad_tau_dev);
+
 /* Wait for the context's stream and report the first deferred error raised
  * by a kernel since the last stk_sync (bounded-wait timeout, bad explicit
  * template).  Clears it. */

@@ -41,6 +41,7 @@ def lib():
         L.orc_score_range.argtypes = [C.c_void_p, C.c_uint64, C.c_uint64, C.c_uint64, C.c_double,
                                       C.c_int, dp]
         L.orc_score_range.restype = C.c_int
+        L.orc_interp_explicit.argtypes = [C.c_void_p, dp, dp, C.c_uint64, dp, dp]
         L.orc_topk.argtypes = [dp, C.c_uint64, C.c_uint64, C.c_int, dp, u64p]
         L.orc_topk.restype = C.c_int
         _lib = L
@@ -121,6 +122,18 @@ class OracleMap:
         if extras:
             return snr, dict(S=S, W=W, absterm=A, absz=Z)
         return snr
+
+    def interp_score(self, f3, tau, grad: bool = False):
+        """Interpolated statistic of continuous templates (real f0, f1, f2 in bins;
+        tau in s) and optionally its analytic gradient d SNR / d (f0, f1, f2, tau)."""
+        f3 = np.ascontiguousarray(f3, dtype=np.float64).reshape(-1, 3)
+        tau = np.ascontiguousarray(tau, dtype=np.float64).reshape(-1)
+        n = f3.shape[0]
+        snr = np.zeros(n)
+        g = np.zeros((n, 4))
+        lib().orc_interp_explicit(self._h, _ptr(f3, C.c_double), _ptr(tau, C.c_double), n, _ptr(snr, C.c_double),
+                                  _ptr(g, C.c_double))
+        return (snr, g) if grad else snr
 
     def score_range(self, seed: int, offset: int, n_tracks: int, tau_max: float,
                     nthreads: int | None = None) -> np.ndarray:

@@ -259,3 +259,73 @@ int orc_topk(const double *snr, uint64_t T, uint64_t offset, int K,
     free(r);
     return 0;
 }
+
+/* ------------------------------------------------- interpolated statistic */
+/* Refinement of loud templates (the follow-up of Sec. V): the control
+ * frequencies become real numbers (in bins) and the delay stays continuous.
+ * The curve's frequency at column j is x_j = ((M-j)^2 f0 + 2 (M-j) j f1 + j^2 f2) / M^2
+ * (bins, clamped to [0, n_f - 1]).  The map between bins is interpolated
+ * linearly in frequency: with k = floor(x_j) (at most n_f - 2) and a = x_j - k,
+ *   z(j, x) = (1 - a) z[j][k] + a z[j][k+1],  w(j, x) = (1 - a) w[j][k] + a w[j][k+1].
+ * The statistic is Eq. 7 with the continuous frequency f = f_min + x df:
+ *   S = sum_j Re[exp(2 pi i f(x_j) tau) z(j, x_j)],  W = sum_j w(j, x_j),
+ *   SNR = S / sqrt(W) (weighted) or S / N (paper form).
+ * At integer x_j this is the discrete statistic.  grad[0..3] receives
+ * d SNR / d (f0, f1, f2, tau), by differentiating each step above (zero
+ * where x_j is clamped). */
+double orc_interp_score(const orc_map *m, const double f[3], double tau, double grad[4])
+{
+    const int n_t = m->n_t, n_f = m->n_f;
+    const double M = (double)(n_t - 1), M2 = M * M;
+    double S = 0, W = 0, dS[4] = {0, 0, 0, 0}, dW[3] = {0, 0, 0};
+    for (int j = 0; j < n_t; ++j) {
+        const double cj[3] = {(M - j) * (M - j) / M2, 2.0 * (M - j) * j / M2, (double)j * j / M2};
+        double x = cj[0] * f[0] + cj[1] * f[1] + cj[2] * f[2];
+        int clamped = 0;
+        if (x < 0) { x = 0; clamped = 1; }
+        if (x > n_f - 1) { x = n_f - 1; clamped = 1; }
+        int k = (int)floor(x);
+        if (k > n_f - 2) k = n_f - 2;
+        if (k < 0) k = 0;
+        const double a = n_f > 1 ? x - k : 0.0;
+        const size_t p0 = (size_t)j * n_f + k, p1 = n_f > 1 ? p0 + 1 : p0;
+        const double zr = (1 - a) * m->z[2 * p0] + a * m->z[2 * p1];
+        const double zi = (1 - a) * m->z[2 * p0 + 1] + a * m->z[2 * p1 + 1];
+        const double dzr = m->z[2 * p1] - m->z[2 * p0], dzi = m->z[2 * p1 + 1] - m->z[2 * p0 + 1];
+        const double w = (1 - a) * m->w[p0] + a * m->w[p1], dw = m->w[p1] - m->w[p0];
+        const double fr = m->f_min + x * m->df;
+        const double ph = 2.0 * M_PI * fr * tau;
+        const double c = cos(ph), s = sin(ph);
+        const double re = c * zr - s * zi;      /* Re[e^{i ph} z] */
+        const double im = s * zr + c * zi;      /* Im[e^{i ph} z] */
+        S += re;
+        W += w;
+        /* d re / d x = -im * (2 pi df tau) + Re[e^{i ph} dz/dx]; d re / d tau = -im * 2 pi f */
+        const double dre_dx = clamped ? 0.0 : (-im * 2.0 * M_PI * m->df * tau + (c * dzr - s * dzi));
+        const double dw_dx = clamped ? 0.0 : dw;
+        for (int q = 0; q < 3; ++q) {
+            dS[q] += dre_dx * cj[q];
+            dW[q] += dw_dx * cj[q];
+        }
+        dS[3] += -im * 2.0 * M_PI * fr;
+    }
+    double snr;
+    if (m->paper_mode) {
+        snr = S / n_t;
+        if (grad) for (int q = 0; q < 4; ++q) grad[q] = dS[q] / n_t;
+    } else {
+        const double rw = 1.0 / sqrt(W);
+        snr = S * rw;
+        if (grad) {
+            for (int q = 0; q < 3; ++q) grad[q] = dS[q] * rw - 0.5 * S * rw * rw * rw * dW[q];
+            grad[3] = dS[3] * rw;
+        }
+    }
+    return snr;
+}
+
+void orc_interp_explicit(const orc_map *m, const double *f3, const double *tau, uint64_t n, double *snr,
+                         double *grad4)
+{
+    for (uint64_t i = 0; i < n; ++i) snr[i] = orc_interp_score(m, f3 + 3 * i, tau[i], grad4 ? grad4 + 4 * i : NULL);
+}

@@ -202,6 +202,31 @@ class Context:
                                              C.c_void_p(tau.data_ptr()), n, C.c_void_p(out.data_ptr())))
         return out
 
+    def interp_forward(self, m: Map, f3, tau):
+        """stk_interp_forward: SNR of continuous templates (f3 float32 [n][3] bins, tau float32 [n] s)."""
+        torch = self._torch
+        self._bind_stream()
+        f3 = f3.detach().to(torch.float32).contiguous()
+        tau = tau.detach().to(torch.float32).contiguous()
+        out = torch.empty(tau.numel(), dtype=torch.float32, device=tau.device)
+        self._check(lib().stk_interp_forward(self._h, m.handle, C.c_void_p(f3.data_ptr()), C.c_void_p(tau.data_ptr()),
+                                             tau.numel(), C.c_void_p(out.data_ptr())))
+        return out
+
+    def interp_adjoint(self, m: Map, f3, tau, g):
+        """stk_interp_adjoint: (g * dSNR/df3, g * dSNR/dtau)."""
+        torch = self._torch
+        self._bind_stream()
+        f3 = f3.detach().to(torch.float32).contiguous()
+        tau = tau.detach().to(torch.float32).contiguous()
+        g = g.detach().to(torch.float32).contiguous()
+        gf = torch.empty_like(f3)
+        gt = torch.empty_like(tau)
+        self._check(lib().stk_interp_adjoint(self._h, m.handle, C.c_void_p(f3.data_ptr()), C.c_void_p(tau.data_ptr()),
+                                             C.c_void_p(g.data_ptr()), tau.numel(), C.c_void_p(gf.data_ptr()),
+                                             C.c_void_p(gt.data_ptr())))
+        return gf, gt
+
     def sync(self):
         """stk_sync: wait and raise the first deferred kernel error."""
         self._check(lib().stk_sync(self._h))
@@ -281,3 +306,54 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def _autograd_function():
+    import torch
+
+    class InterpSNR(torch.autograd.Function):
+        """SNR of continuous templates with the library's forward and adjoint kernels."""
+
+        @staticmethod
+        def forward(fctx, f3, tau, stk_ctx, m):
+            fctx.save_for_backward(f3, tau)
+            fctx.stk = (stk_ctx, m)
+            return stk_ctx.interp_forward(m, f3, tau)
+
+        @staticmethod
+        def backward(fctx, g):
+            f3, tau = fctx.saved_tensors
+            stk_ctx, m = fctx.stk
+            gf, gt = stk_ctx.interp_adjoint(m, f3, tau, g)
+            return gf, gt, None, None
+
+    return InterpSNR
+
+
+def interp_snr(ctx: Context, m: Map, f3, tau):
+    """Differentiable SNR of continuous templates (torch.autograd)."""
+    return _autograd_function().apply(f3, tau, ctx, m)
+
+
+def refine(ctx: Context, m: Map, f3, tau, tau_max: float, steps: int = 50, lr_bins: float = 0.25,
+           lr_tau_frac: float = 0.02):
+    """Gradient ascent of the interpolated SNR over (f0, f1, f2, tau) of each template
+    (Adam; f in bins, tau in units of tau_max), projected onto f in [0, n_f - 1] and
+    |tau| <= tau_max.  Returns (f3, tau, snr_history [steps + 1][n]) as tensors."""
+    import torch
+    f = f3.detach().to(torch.float32).clone().requires_grad_(True)
+    u = (tau.detach().to(torch.float32) / tau_max).clone().requires_grad_(True)
+    opt = torch.optim.Adam([{"params": [f], "lr": lr_bins}, {"params": [u], "lr": lr_tau_frac}])
+    hist = []
+    for _ in range(steps):
+        opt.zero_grad()
+        snr = interp_snr(ctx, m, f, u * tau_max)
+        hist.append(snr.detach().clone())
+        (-snr.sum()).backward()
+        opt.step()
+        with torch.no_grad():
+            f.clamp_(0.0, float(m.n_f - 1))
+            u.clamp_(-1.0, 1.0)
+    final = ctx.interp_forward(m, f.detach(), u.detach() * tau_max)
+    hist.append(final)
+    return f.detach(), (u.detach() * tau_max), torch.stack(hist)

@@ -43,6 +43,8 @@ SIGNATURES = [
     ("stk_set_option", C.c_int, [_vp, C.c_int, C.c_int64]),
     ("stk_last_plan", C.c_int, [_vp, C.POINTER(C.c_int64)]),
     ("stk_last_error", C.c_char_p, [_vp]),
+    ("stk_interp_forward", C.c_int, [_vp, _vp, _vp, _vp, C.c_uint64, _vp]),
+    ("stk_interp_adjoint", C.c_int, [_vp, _vp, _vp, _vp, _vp, C.c_uint64, _vp, _vp]),
     ("stk_batch_create", C.c_int, [_vp, _vp, C.c_int, _vp, _vp, _vp, C.c_double, C.POINTER(_vp)]),
     ("stk_batch_destroy", None, [_vp]),
     ("stk_batch_score", C.c_int, [_vp, C.c_int, _vp, C.c_uint]),

@@ -512,6 +512,31 @@ int stk_score_explicit(stk_ctx *c, const stk_map *m, const uint32_t *f3, const d
     return STK_OK;
 }
 
+int stk_interp_forward(stk_ctx *c, const stk_map *m, const float *f3, const float *tau, uint64_t n, float *snr)
+{
+    if (!c) return STK_EINVAL;
+    if (!m || m->ctx != c) return set_err(c, STK_EINVAL, "map is NULL or belongs to another context");
+    if (n == 0) return STK_OK;
+    if (!f3 || !tau || !snr) return set_err(c, STK_EINVAL, "NULL pointer");
+    CUDA_TRY(c, cudaSetDevice(c->device));
+    cudaError_t e = launch_interp(m->dev, f3, tau, nullptr, n, snr, nullptr, nullptr, false, c->stream);
+    if (e != cudaSuccess) return set_err(c, STK_ECUDA, "interpolated forward launch: %s", cudaGetErrorString(e));
+    return STK_OK;
+}
+
+int stk_interp_adjoint(stk_ctx *c, const stk_map *m, const float *f3, const float *tau, const float *g, uint64_t n,
+                       float *grad_f3, float *grad_tau)
+{
+    if (!c) return STK_EINVAL;
+    if (!m || m->ctx != c) return set_err(c, STK_EINVAL, "map is NULL or belongs to another context");
+    if (n == 0) return STK_OK;
+    if (!f3 || !tau || !g || !grad_f3 || !grad_tau) return set_err(c, STK_EINVAL, "NULL pointer");
+    CUDA_TRY(c, cudaSetDevice(c->device));
+    cudaError_t e = launch_interp(m->dev, f3, tau, g, n, nullptr, grad_f3, grad_tau, true, c->stream);
+    if (e != cudaSuccess) return set_err(c, STK_ECUDA, "interpolated adjoint launch: %s", cudaGetErrorString(e));
+    return STK_OK;
+}
+
 int stk_sync(stk_ctx *c)
 {
     if (!c) return STK_EINVAL;

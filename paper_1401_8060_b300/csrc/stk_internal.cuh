@@ -311,6 +311,10 @@ cudaError_t launch_score_explicit(const MapDev &m, const uint32_t *f3, const dou
 cudaError_t launch_track_params(const MapDev &m, const TrackSet &ts, uint64_t g, uint32_t *f_dev, double *tau_dev,
                                 int32_t *bins_dev, cudaStream_t st);
 
+// Interpolated statistic of continuous templates (forward: snr; adjoint: g * gradient).
+cudaError_t launch_interp(const MapDev &m, const float *f3, const float *tau, const float *g, uint64_t n, float *snr,
+                          float *gf3, float *gtau, bool adjoint, cudaStream_t st);
+
 // Top-k selection over snr[0..n): hits get (snr, offset + i, params).  Scratch
 // is caller-provided: see select_scratch_bytes.
 size_t select_scratch_bytes(uint64_t n, int k);

@@ -308,3 +308,87 @@ def test_topk_order_and_split(orc):
     # all ties: the smallest indices win
     v, i = orc.topk(np.zeros(300), 7, 10)
     np.testing.assert_array_equal(i, np.arange(7, 17))
+
+
+# ---------------------------------------------------------------- interpolated statistic (refinement)
+def _bezier_x(f, n_t):
+    M = n_t - 1
+    j = np.arange(n_t)
+    return ((M - j) ** 2 * f[0] + 2 * (M - j) * j * f[1] + j ** 2 * f[2]) / M ** 2
+
+
+def test_interp_reduces_to_discrete_at_integer_bins(orc):
+    n_t, n_f = 40, 60
+    y, sig = _tiny_map(30, n_t, n_f)
+    for paper in (False, True):
+        om = orc.OracleMap(y, sig, 70.0, 0.5, False, paper_mode=paper)
+        for c in (0, 7, 31, 59):
+            for tau in (-0.006, 0.0, 0.0041):
+                d = om.score_explicit(np.array([(c, c, c)]), np.array([tau]))[0]
+                s = om.interp_score(np.array([(c, c, c)], float), np.array([tau]))[0]
+                assert s == pytest.approx(d, rel=1e-12, abs=1e-12)
+
+
+def test_interp_exact_on_maps_linear_in_frequency(orc):
+    """z(j, k) = A_j + B_j k: linear interpolation is exact, so the statistic is
+    the plain sum over the continuous curve."""
+    n_t, n_f, f_min, df = 30, 80, 50.0, 0.5
+    rng = np.random.default_rng(31)
+    A = rng.standard_normal(n_t) + 1j * rng.standard_normal(n_t)
+    B = (rng.standard_normal(n_t) + 1j * rng.standard_normal(n_t)) * 0.05
+    k = np.arange(n_f)
+    y = (A[:, None] + B[:, None] * k[None, :]).astype(np.complex64)
+    om = orc.OracleMap(y, np.ones(n_f, np.float32), f_min, df, True)
+    yd = y.astype(np.complex128)
+    for _ in range(20):
+        f = rng.uniform(1, n_f - 2, 3)
+        tau = rng.uniform(-0.01, 0.01)
+        x = _bezier_x(f, n_t)
+        kk = np.minimum(np.floor(x).astype(int), n_f - 2)
+        a = x - kk
+        z = (1 - a) * yd[np.arange(n_t), kk] + a * yd[np.arange(n_t), kk + 1]
+        S = np.sum((np.exp(2j * np.pi * (f_min + x * df) * tau) * z).real)
+        assert om.interp_score(f[None], np.array([tau]))[0] == pytest.approx(S / np.sqrt(n_t), rel=1e-9)
+
+
+def test_interp_constant_frequency_closed_form(orc):
+    """A map constant along frequency: any real constant template c sees
+    sum_j Re[exp(2 pi i (f_min + c df) tau) z_j] (continuous Eq. 3 phase)."""
+    n_t, n_f, f_min, df = 25, 40, 100.0, 1.0
+    rng = np.random.default_rng(32)
+    zj = (rng.standard_normal(n_t) + 1j * rng.standard_normal(n_t)).astype(np.complex64)
+    y = np.repeat(zj[:, None], n_f, axis=1)
+    om = orc.OracleMap(y, np.full(n_f, 2.0, np.float32), f_min, df, True)
+    for c in (3.25, 17.5, 38.9):
+        for tau in (-0.0031, 0.0077):
+            S = np.sum((np.exp(2j * np.pi * (f_min + c * df) * tau) * zj.astype(np.complex128) / 4.0).real)
+            W = n_t / 4.0
+            got = om.interp_score(np.array([(c, c, c)]), np.array([tau]))[0]
+            assert got == pytest.approx(S / np.sqrt(W), rel=1e-10)
+
+
+@pytest.mark.parametrize("paper", [False, True])
+def test_interp_gradient_matches_finite_differences(orc, paper):
+    n_t, n_f = 50, 120
+    y, sig = _tiny_map(33, n_t, n_f)
+    om = orc.OracleMap(y, sig, 40.0, 0.5, False, paper_mode=paper)
+    rng = np.random.default_rng(34)
+    checked = 0
+    while checked < 25:
+        f = rng.uniform(2, n_f - 3, 3)
+        tau = rng.uniform(-0.01, 0.01)
+        x = _bezier_x(f, n_t)
+        if np.min(np.abs(x - np.round(x))) < 1e-3:      # stay off the bin knots
+            continue
+        _, g = om.interp_score(f[None], np.array([tau]), grad=True)
+        hf, ht = 1e-6, 1e-10
+        fd = []
+        for q in range(3):
+            e = np.zeros(3)
+            e[q] = hf
+            fd.append((om.interp_score((f + e)[None], np.array([tau]))[0] -
+                       om.interp_score((f - e)[None], np.array([tau]))[0]) / (2 * hf))
+        fd.append((om.interp_score(f[None], np.array([tau + ht]))[0] -
+                   om.interp_score(f[None], np.array([tau - ht]))[0]) / (2 * ht))
+        np.testing.assert_allclose(g[0], fd, rtol=2e-5, atol=2e-5 * np.max(np.abs(fd)))
+        checked += 1
