@@ -342,6 +342,34 @@ def main():
             "storage": "4 B/pixel: FP16 |y|/sigma (per-frequency scaling) + Q0.16 phase; FP32 sums"}
         m16.close()
 
+    # general templates (random start / middle / end times, duration >= 25 columns = 100 s)
+    if not args.no_variants:
+        Tg, tmin_g = 1_000_000, 25
+        ctx.set_template_shape(True, tmin_g)
+        ctx.set_tracks(Tg, w["seed"], 0, w["tau_max"])
+        outg = torch.zeros(K * 40, dtype=torch.uint8, device="cuda")
+        for _ in range(max(args.warmup, 3)):
+            ctx.score(m, K, out=outg)
+        ctx.sync()
+        evg = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(3)]
+        kg = []
+        for s_ in range(3):
+            flush.zero_()
+            evg[s_][0].record(stream)
+            ctx.score(m, K, out=outg)
+            evg[s_][1].record(stream)
+            kg.append(ctx.last_timings()["score_ms"])
+        torch.cuda.synchronize()
+        msg = sum(a.elapsed_time(b_) for a, b_ in evg) / 3
+        M_ = fm.n_t - 1
+        pxg = Tg * ((tmin_g + M_) / 2 + 1)            # expected pixels: duration uniform on [t_min, M]
+        variants["general_templates"] = {
+            "value": pxg / (msg / 1e3), "unit": "track-pixels/s (expected pixels)", "ms_per_step": msg,
+            "kernel_ms": sum(kg) / len(kg), "templates": Tg, "t_min_columns": tmin_g,
+            "rasteriser": "exact integer nearest-bin test per column, one thread per template, L2 gathers"}
+        ctx.set_template_shape(False)
+        ctx.set_tracks(T, w["seed"], offset, w["tau_max"])
+
     # refinement of the k loudest: 50 gradient-ascent steps on the interpolated statistic
     if not args.no_variants:
         ctx.set_profiling(False)

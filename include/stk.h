@@ -150,6 +150,45 @@ STK_API int stk_track_params(stk_ctx *ctx, const stk_map *map, uint64_t g, uint3
 STK_API int stk_score_explicit(stk_ctx *ctx, const stk_map *map, const uint32_t *f3_dev, const double *tau_dev,
                        uint64_t n, double *out_snr_dev);
 
+/* ---- general templates and delay priors ---------------------------------
+ * Sec. III describes each template by three time-frequency control points
+ * P0 (t_start, f_start), P1 (t_mid, f_mid), P2 (t_end, f_end) drawn from six
+ * random numbers, the curve persisting at least t_min.  The default templates
+ * pin the times to the first, middle and last column; general templates draw
+ * integer times t0 <= t1 <= t2 as well: duration t2 - t0 uniform on
+ * [t_min, n_t - 1], start uniform on [0, n_t - 1 - duration], t1 uniform on
+ * [t0, t2] (Philox block (g, 1, 0, 0); bins and delay as before).  Column j of
+ * [t0, t2] takes the bin nearest f(xi_j), t(xi_j) = j (halves up), decided
+ * exactly in integer arithmetic; N = t2 - t0 + 1 pixels.  General templates
+ * need n_t <= 4096 and n_f <= 8192 and are scored one thread per template
+ * (not in batches).
+ * Sec. VI suggests drawing the delay from a sky patch's distribution instead of
+ * the isotropic uniform one: a delay prior is given as quantiles. */
+
+/* general = 0: pinned times (default); general = 1: random times with
+ * t2 - t0 >= t_min columns (t_min >= 1).  Applies to later scoring calls of
+ * ctx.  Errors: STK_EINVAL. */
+STK_API int stk_set_template_shape(stk_ctx *ctx, int general, int t_min);
+
+/* Delay prior for later scoring calls: quantiles_host[i] is the delay (s) at
+ * cumulative probability i / (n - 1), non-decreasing, n in 2 .. 65536; the delay
+ * of template g is the linear interpolation at probability (u3 >> 11) 2^-53 of
+ * its Philox word u3.  NULL or n = 0 restores the uniform prior on
+ * (-tau_max, tau_max).  The table is copied.  Errors: STK_EINVAL, STK_ENOMEM. */
+STK_API int stk_set_tau_prior(stk_ctx *ctx, const double *quantiles_host, int n);
+
+/* Control times t[3] of template g under the current shape (0, (n_t-1)/2,
+ * n_t - 1 for pinned templates).  Synchronous.  Errors: as stk_track_params. */
+STK_API int stk_track_times(stk_ctx *ctx, const stk_map *map, uint64_t g, uint32_t t[3]);
+
+/* Score n explicit general templates: t3_dev [n][3] control times (t0 <= t1 <=
+ * t2 < n_t, t0 < t2), f3_dev [n][3] control bins (< n_f), tau_dev [n] delays;
+ * SNRs to out_snr_dev [n]; device pointers.  Invalid templates are flagged
+ * (STK_EINVAL at the next stk_sync).  Errors: STK_EINVAL, STK_ECUDA. */
+STK_API int stk_score_explicit_general(stk_ctx *ctx, const stk_map *map, const uint32_t *t3_dev,
+                                       const uint32_t *f3_dev, const double *tau_dev, uint64_t n,
+                                       double *out_snr_dev);
+
 /* ---- continuous templates (refinement of the loudest) -------------------
  * The follow-up of the loudest events (Sec. V) refines a template's control
  * frequencies and delay continuously.  Control frequencies f0, f1, f2 are real

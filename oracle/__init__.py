@@ -42,6 +42,13 @@ def lib():
                                       C.c_int, dp]
         L.orc_score_range.restype = C.c_int
         L.orc_interp_explicit.argtypes = [C.c_void_p, dp, dp, C.c_uint64, dp, dp]
+        L.orc_track_times.argtypes = [C.c_uint64, C.c_uint64, C.c_int, C.c_int, u32p]
+        L.orc_track_params_prior.argtypes = [C.c_uint64, C.c_uint64, C.c_int, dp, C.c_int, u32p, dp]
+        L.orc_track_bins_general.argtypes = [u32p, u32p, C.c_int, C.c_int, i32p]
+        L.orc_score_explicit_general.argtypes = [C.c_void_p, u32p, u32p, dp, C.c_uint64, dp]
+        L.orc_score_range_ext.argtypes = [C.c_void_p, C.c_uint64, C.c_uint64, C.c_uint64, C.c_double, C.c_int,
+                                          C.c_int, dp, C.c_int, C.c_int, dp]
+        L.orc_score_range_ext.restype = C.c_int
         L.orc_topk.argtypes = [dp, C.c_uint64, C.c_uint64, C.c_int, dp, u64p]
         L.orc_topk.restype = C.c_int
         _lib = L
@@ -74,6 +81,31 @@ def track_bins(f, n_t: int) -> np.ndarray:
     fa = np.asarray(f, dtype=np.uint32).reshape(3).copy()
     out = np.zeros(n_t, dtype=np.int32)
     lib().orc_track_bins(_ptr(fa, C.c_uint32), n_t, _ptr(out, C.c_int32))
+    return out
+
+
+def track_times(seed: int, g: int, n_t: int, t_min: int):
+    """Control times (t0, t1, t2) of general template g (Sec. III, six random numbers)."""
+    t = np.zeros(3, dtype=np.uint32)
+    lib().orc_track_times(seed, g, n_t, t_min, _ptr(t, C.c_uint32))
+    return tuple(int(v) for v in t)
+
+
+def track_params_prior(seed: int, g: int, n_f: int, quantiles):
+    """Control bins and a delay drawn from a quantile table (Sec. VI sky-patch prior)."""
+    q = np.ascontiguousarray(quantiles, dtype=np.float64)
+    f = np.zeros(3, dtype=np.uint32)
+    tau = C.c_double()
+    lib().orc_track_params_prior(seed, g, n_f, _ptr(q, C.c_double), q.size, _ptr(f, C.c_uint32), C.byref(tau))
+    return tuple(int(v) for v in f), float(tau.value)
+
+
+def track_bins_general(t, f, n_t: int, n_f: int) -> np.ndarray:
+    """Pixels of a general template: the nearest bin in each column t0..t2, -1 elsewhere."""
+    ta = np.asarray(t, dtype=np.uint32).reshape(3).copy()
+    fa = np.asarray(f, dtype=np.uint32).reshape(3).copy()
+    out = np.zeros(n_t, dtype=np.int32)
+    lib().orc_track_bins_general(_ptr(ta, C.c_uint32), _ptr(fa, C.c_uint32), n_t, n_f, _ptr(out, C.c_int32))
     return out
 
 
@@ -134,6 +166,30 @@ class OracleMap:
         lib().orc_interp_explicit(self._h, _ptr(f3, C.c_double), _ptr(tau, C.c_double), n, _ptr(snr, C.c_double),
                                   _ptr(g, C.c_double))
         return (snr, g) if grad else snr
+
+    def score_explicit_general(self, t3, f3, tau):
+        """Eq. 7 for explicit general templates (t3, f3 [n][3]; tau [n])."""
+        t3 = np.ascontiguousarray(t3, dtype=np.uint32).reshape(-1, 3)
+        f3 = np.ascontiguousarray(f3, dtype=np.uint32).reshape(-1, 3)
+        tau = np.ascontiguousarray(tau, dtype=np.float64).reshape(-1)
+        out = np.zeros(tau.size)
+        lib().orc_score_explicit_general(self._h, _ptr(t3, C.c_uint32), _ptr(f3, C.c_uint32), _ptr(tau, C.c_double),
+                                         tau.size, _ptr(out, C.c_double))
+        return out
+
+    def score_range_ext(self, seed: int, offset: int, n_tracks: int, tau_max: float, general: bool = False,
+                        t_min: int = 1, quantiles=None, nthreads: int | None = None) -> np.ndarray:
+        """score_range with general templates and/or a delay prior."""
+        if nthreads is None:
+            nthreads = os.cpu_count() or 1
+        q = np.ascontiguousarray(quantiles if quantiles is not None else np.zeros(1), dtype=np.float64)
+        nq = int(q.size) if quantiles is not None else 0
+        out = np.zeros(n_tracks)
+        rc = lib().orc_score_range_ext(self._h, seed, offset, n_tracks, tau_max, int(general), int(t_min),
+                                       _ptr(q, C.c_double), nq, int(nthreads), _ptr(out, C.c_double))
+        if rc != 0:
+            raise RuntimeError("oracle score_range_ext failed (%d)" % rc)
+        return out
 
     def score_range(self, seed: int, offset: int, n_tracks: int, tau_max: float,
                     nthreads: int | None = None) -> np.ndarray:

@@ -329,3 +329,169 @@ void orc_interp_explicit(const orc_map *m, const double *f3, const double *tau, 
 {
     for (uint64_t i = 0; i < n; ++i) snr[i] = orc_interp_score(m, f3 + 3 * i, tau[i], grad4 ? grad4 + 4 * i : NULL);
 }
+
+/* ------------------------------------------------------ general templates */
+/* Sec. III: three time-frequency control points (t_k, f_k) from six random
+ * numbers, persisting at least t_min columns.  Reading: integer control times
+ * t0 <= t1 <= t2 from Philox block (g, 1, 0, 0): duration d = t2 - t0 uniform on
+ * [t_min, n_t - 1] (word 0), start uniform on [0, n_t - 1 - d] (word 1), t1 - t0
+ * uniform on [0, d] (word 2); each as floor(word * range / 2^64). */
+void orc_track_times(uint64_t seed, uint64_t g, int n_t, int t_min, uint32_t t[3])
+{
+    uint64_t ctr[4] = {g, 1, 0, 0};
+    uint64_t key[2] = {seed, 0};
+    uint64_t v[4];
+    orc_philox4x64_10(ctr, key, v);
+    uint64_t M = (uint64_t)n_t - 1;
+    uint64_t d = (uint64_t)t_min + (uint64_t)(((unsigned __int128)v[0] * (M - (uint64_t)t_min + 1)) >> 64);
+    uint64_t t0 = (uint64_t)(((unsigned __int128)v[1] * (M - d + 1)) >> 64);
+    uint64_t t1 = t0 + (uint64_t)(((unsigned __int128)v[2] * (d + 1)) >> 64);
+    t[0] = (uint32_t)t0; t[1] = (uint32_t)t1; t[2] = (uint32_t)(t0 + d);
+}
+
+/* A delay prior given by quantiles (Sec. VI: a sky patch instead of the
+ * isotropic sky): the delay at probability p = (u3 >> 11) / 2^53 is the linear
+ * interpolation of the table at p (n_q - 1).  Bins as orc_track_params. */
+void orc_track_params_prior(uint64_t seed, uint64_t g, int n_f, const double *tq, int n_q, uint32_t f[3],
+                            double *tau)
+{
+    uint64_t ctr[4] = {g, 0, 0, 0};
+    uint64_t key[2] = {seed, 0};
+    uint64_t u[4];
+    orc_philox4x64_10(ctr, key, u);
+    for (int k = 0; k < 3; ++k)
+        f[k] = (uint32_t)(((unsigned __int128)u[k] * (uint64_t)n_f) >> 64);
+    double p = (double)(u[3] >> 11) / 9007199254740992.0;   /* 2^53 */
+    double q = p * (double)(n_q - 1);
+    int i = (int)floor(q);
+    if (i > n_q - 2) i = n_q - 2;
+    double fr = q - (double)i;
+    *tau = tq[i] + fr * (tq[i + 1] - tq[i]);
+}
+
+/* The curve of a general template: t(xi) = (1-xi)^2 t0 + 2 (1-xi) xi t1 + xi^2 t2,
+ * f(xi) likewise.  For column j in [t0, t2] the point xi_j in [0, 1] with
+ * t(xi_j) = j, and the pixel is the nearest bin to f(xi_j), halves rounded up.
+ * Test "f(xi_j) >= y" for a half-integer y exactly: write a = t0 - 2 t1 + t2,
+ * b = 2 (t1 - t0), F = f0 - 2 f1 + f2, G = 2 (f1 - f0), u = 2 (j - t0),
+ * Delta = b^2 + 4 a (j - t0) and s = sqrt(Delta); then xi_j = u / (s + b) and
+ * (2 f(xi_j) - 2 y) (s + b)^2 = P + Q s with
+ * P = 2 F u^2 + 2 G u b + e (Delta + b^2), Q = 2 G u + 2 e b, e = 2 f0 - 2 y,
+ * whose sign is fixed by the signs of P, Q and, when they differ, P^2 - Q^2 Delta. */
+static int orc_half_ge(const int64_t tt[3], const int64_t ff[3], int64_t j, int64_t twice_y)
+{
+    __int128 a = tt[0] - 2 * tt[1] + tt[2], b = 2 * (tt[1] - tt[0]);
+    __int128 F = ff[0] - 2 * ff[1] + ff[2], G = 2 * (ff[1] - ff[0]);
+    __int128 u = 2 * (j - tt[0]);
+    __int128 Delta = b * b + 4 * a * (j - tt[0]);
+    __int128 e = 2 * ff[0] - twice_y;
+    __int128 P = 2 * F * u * u + 2 * G * u * b + e * (Delta + b * b);
+    __int128 Q = 2 * G * u + 2 * e * b;
+    if (P >= 0 && Q >= 0) return 1;
+    if (P <= 0 && Q <= 0) return P == 0 && Q == 0;
+    __int128 lhs = P * P, rhs = Q * Q * Delta;
+    return P > 0 ? lhs >= rhs : rhs >= lhs;
+}
+
+/* Pixels of a general template: bins[j] for j in [t0, t2], -1 elsewhere.  An FP64
+ * estimate of f(xi_j), then the exact test moves it to the nearest bin. */
+void orc_track_bins_general(const uint32_t t[3], const uint32_t f[3], int n_t, int n_f, int32_t *bins)
+{
+    int64_t tt[3] = {t[0], t[1], t[2]}, ff[3] = {f[0], f[1], f[2]};
+    double a = (double)(tt[0] - 2 * tt[1] + tt[2]), b = (double)(2 * (tt[1] - tt[0]));
+    double F = (double)(ff[0] - 2 * ff[1] + ff[2]), G = (double)(2 * (ff[1] - ff[0]));
+    for (int j = 0; j < n_t; ++j) {
+        if (j < (int)t[0] || j > (int)t[2]) { bins[j] = -1; continue; }
+        if (j == (int)t[0]) { bins[j] = (int32_t)f[0]; continue; }
+        double Delta = b * b + 4.0 * a * (double)(j - (int64_t)t[0]);
+        double xi = 2.0 * (double)(j - (int64_t)t[0]) / (sqrt(Delta > 0 ? Delta : 0) + b);
+        double fx = (double)ff[0] + xi * (G + F * xi);
+        int64_t k = (int64_t)floor(fx + 0.5);
+        if (k < 0) k = 0;
+        if (k > n_f - 1) k = n_f - 1;
+        /* exact: the largest k with f >= k - 1/2 */
+        while (k > 0 && !orc_half_ge(tt, ff, j, 2 * k - 1)) --k;
+        while (k + 1 < n_f && orc_half_ge(tt, ff, j, 2 * (k + 1) - 1)) ++k;
+        bins[j] = (int32_t)k;
+    }
+}
+
+/* Eq. 7 over a general template's N = t2 - t0 + 1 pixels. */
+double orc_score_general(const orc_map *m, const uint32_t t[3], const uint32_t f[3], double tau)
+{
+    int32_t *bins = (int32_t *)malloc(sizeof(int32_t) * (size_t)m->n_t);
+    orc_track_bins_general(t, f, m->n_t, m->n_f, bins);
+    double S = 0.0, W = 0.0;
+    int N = 0;
+    for (int j = 0; j < m->n_t; ++j) {
+        if (bins[j] < 0) continue;
+        size_t p = (size_t)j * m->n_f + (size_t)bins[j];
+        double th = 2.0 * M_PI * (m->f_min + (double)bins[j] * m->df) * tau;
+        S += cos(th) * m->z[2 * p] - sin(th) * m->z[2 * p + 1];
+        W += m->w[p];
+        ++N;
+    }
+    free(bins);
+    return m->paper_mode ? S / (double)N : S / sqrt(W);
+}
+
+void orc_score_explicit_general(const orc_map *m, const uint32_t *t3, const uint32_t *f3, const double *tau,
+                                uint64_t n, double *snr)
+{
+    for (uint64_t i = 0; i < n; ++i) snr[i] = orc_score_general(m, t3 + 3 * i, f3 + 3 * i, tau[i]);
+}
+
+/* Templates offset .. offset + T - 1 with general times and optionally a delay
+ * prior (n_q >= 2); threads take contiguous slices. */
+typedef struct {
+    const orc_map *m;
+    uint64_t seed, g0, n;
+    double tau_max;
+    int general, t_min, n_q;
+    const double *tq;
+    double *out;
+} orc_gjob;
+
+static void *orc_general_worker(void *arg)
+{
+    orc_gjob *jb = (orc_gjob *)arg;
+    for (uint64_t i = 0; i < jb->n; ++i) {
+        uint32_t f[3], t[3];
+        double tau;
+        uint64_t g = jb->g0 + i;
+        if (jb->n_q >= 2) orc_track_params_prior(jb->seed, g, jb->m->n_f, jb->tq, jb->n_q, f, &tau);
+        else orc_track_params(jb->seed, g, jb->m->n_f, jb->tau_max, f, &tau);
+        if (jb->general) {
+            orc_track_times(jb->seed, g, jb->m->n_t, jb->t_min, t);
+            jb->out[i] = orc_score_general(jb->m, t, f, tau);
+        } else {
+            jb->out[i] = orc_score_track(jb->m, f, tau, NULL, NULL, NULL, NULL);
+        }
+    }
+    return NULL;
+}
+
+int orc_score_range_ext(const orc_map *m, uint64_t seed, uint64_t offset, uint64_t T, double tau_max, int general,
+                        int t_min, const double *tq, int n_q, int nthreads, double *snr_out)
+{
+    if (nthreads < 1) nthreads = 1;
+    if ((uint64_t)nthreads > T) nthreads = T ? (int)T : 1;
+    pthread_t *th = (pthread_t *)malloc(sizeof(pthread_t) * (size_t)nthreads);
+    orc_gjob *jobs = (orc_gjob *)malloc(sizeof(orc_gjob) * (size_t)nthreads);
+    if (!th || !jobs) { free(th); free(jobs); return -1; }
+    uint64_t base = T / (uint64_t)nthreads, rem = T % (uint64_t)nthreads, start = 0;
+    for (int t = 0; t < nthreads; ++t) {
+        uint64_t n = base + ((uint64_t)t < rem ? 1 : 0);
+        orc_gjob j = {m, seed, offset + start, n, tau_max, general, t_min, n_q, tq, snr_out + start};
+        jobs[t] = j;
+        start += n;
+    }
+    int rc = 0, started = 0;
+    for (int t = 0; t < nthreads; ++t) {
+        if (pthread_create(&th[t], NULL, orc_general_worker, &jobs[t]) != 0) { rc = -2; break; }
+        ++started;
+    }
+    for (int t = 0; t < started; ++t) pthread_join(th[t], NULL);
+    free(th); free(jobs);
+    return rc;
+}

@@ -202,6 +202,40 @@ class Context:
                                              C.c_void_p(tau.data_ptr()), n, C.c_void_p(out.data_ptr())))
         return out
 
+    def set_template_shape(self, general: bool, t_min: int = 1):
+        """stk_set_template_shape: random start / middle / end times (duration >= t_min columns)."""
+        self._check(lib().stk_set_template_shape(self._h, 1 if general else 0, int(t_min)))
+
+    def set_tau_prior(self, quantiles=None):
+        """stk_set_tau_prior: delay quantiles (s) at probabilities i/(n-1); None: uniform."""
+        if quantiles is None:
+            self._check(lib().stk_set_tau_prior(self._h, None, 0))
+            return
+        q = np.ascontiguousarray(quantiles, dtype=np.float64)
+        self._check(lib().stk_set_tau_prior(self._h, C.c_void_p(q.ctypes.data), int(q.size)))
+
+    def track_times(self, m: Map, g: int):
+        """stk_track_times: control times (t0, t1, t2) of template g."""
+        t = np.zeros(3, dtype=np.uint32)
+        self._check(lib().stk_track_times(self._h, m.handle, int(g), C.c_void_p(t.ctypes.data)))
+        return tuple(int(v) for v in t)
+
+    def score_explicit_general(self, m: Map, t3, f3, tau, out=None):
+        """stk_score_explicit_general on [n][3] times, [n][3] bins and [n] delays."""
+        torch = self._torch
+        self._bind_stream()
+        dev = f"cuda:{self.device}"
+        t3 = torch.as_tensor(t3).to(device=dev, dtype=torch.int32).contiguous()
+        f3 = torch.as_tensor(f3).to(device=dev, dtype=torch.int32).contiguous()
+        tau = torch.as_tensor(tau, dtype=torch.float64).to(device=dev).contiguous()
+        n = tau.numel()
+        if out is None:
+            out = torch.empty(n, dtype=torch.float64, device=dev)
+        self._check(lib().stk_score_explicit_general(self._h, m.handle, C.c_void_p(t3.data_ptr()),
+                                                     C.c_void_p(f3.data_ptr()), C.c_void_p(tau.data_ptr()), n,
+                                                     C.c_void_p(out.data_ptr())))
+        return out
+
     def interp_forward(self, m: Map, f3, tau):
         """stk_interp_forward: SNR of continuous templates (f3 float32 [n][3] bins, tau float32 [n] s)."""
         torch = self._torch

@@ -43,6 +43,10 @@ SIGNATURES = [
     ("stk_set_option", C.c_int, [_vp, C.c_int, C.c_int64]),
     ("stk_last_plan", C.c_int, [_vp, C.POINTER(C.c_int64)]),
     ("stk_last_error", C.c_char_p, [_vp]),
+    ("stk_set_template_shape", C.c_int, [_vp, C.c_int, C.c_int]),
+    ("stk_set_tau_prior", C.c_int, [_vp, _vp, C.c_int]),
+    ("stk_track_times", C.c_int, [_vp, _vp, C.c_uint64, _vp]),
+    ("stk_score_explicit_general", C.c_int, [_vp, _vp, _vp, _vp, _vp, C.c_uint64, _vp]),
     ("stk_interp_forward", C.c_int, [_vp, _vp, _vp, _vp, C.c_uint64, _vp]),
     ("stk_interp_adjoint", C.c_int, [_vp, _vp, _vp, _vp, _vp, C.c_uint64, _vp, _vp]),
     ("stk_batch_create", C.c_int, [_vp, _vp, C.c_int, _vp, _vp, _vp, C.c_double, C.POINTER(_vp)]),

@@ -165,10 +165,21 @@ int ensure(stk_ctx *c, void **buf, size_t *cap, size_t need)
     return STK_OK;
 }
 
+int check_general(stk_ctx *c, const stk_map *m)
+{
+    if (m->dev.n_t > 4096 || m->dev.n_f > 8192)
+        return set_err(c, STK_EINVAL, "general templates need n_t <= 4096 and n_f <= 8192 (map is %d x %d)",
+                       m->dev.n_t, m->dev.n_f);
+    if (c->ts.t_min > m->dev.n_t - 1)
+        return set_err(c, STK_EINVAL, "t_min = %d exceeds the map's n_t - 1 = %d", c->ts.t_min, m->dev.n_t - 1);
+    return STK_OK;
+}
+
 int check_ready(stk_ctx *c, const stk_map *m)
 {
     if (!m || m->ctx != c) return set_err(c, STK_EINVAL, "map is NULL or belongs to another context");
     if (!c->have_tracks) return set_err(c, STK_ESTATE, "stk_set_tracks has not been called");
+    if (c->ts.general) return check_general(c, m);
     return STK_OK;
 }
 
@@ -221,6 +232,7 @@ void stk_destroy(stk_ctx *c)
     cudaFree(c->sel_buf);
     cudaFree(c->hits_dev);
     cudaFree(c->small_dev);
+    cudaFree(c->tauq_dev);
     for (auto &ev : c->ev)
         if (ev) cudaEventDestroy(ev);
     delete c;
@@ -486,9 +498,10 @@ int stk_track_params(stk_ctx *c, const stk_map *m, uint64_t g, uint32_t f[3], do
     const size_t need = 32 + (size_t)m->dev.n_t * 4;
     rc = ensure(c, (void **)&c->small_dev, &c->small_cap, need);
     if (rc) return rc;
-    uint32_t *fd = c->small_dev;
-    double *td = (double *)((char *)c->small_dev + 16);
+    uint32_t *fd = c->small_dev;                            // 3 bins, 3 times
+    double *td = (double *)((char *)c->small_dev + 24);
     int32_t *bd = (int32_t *)((char *)c->small_dev + 32);
+    if (c->ts.general && (rc = check_general(c, m)) != STK_OK) return rc;
     cudaError_t e = launch_track_params(m->dev, c->ts, g, fd, td, bins_host ? bd : nullptr, c->stream);
     if (e != cudaSuccess) return set_err(c, STK_ECUDA, "params launch: %s", cudaGetErrorString(e));
     CUDA_TRY(c, cudaMemcpyAsync(f, fd, 12, cudaMemcpyDeviceToHost, c->stream));
@@ -509,6 +522,65 @@ int stk_score_explicit(stk_ctx *c, const stk_map *m, const uint32_t *f3, const d
     CUDA_TRY(c, cudaSetDevice(c->device));
     cudaError_t e = launch_score_explicit(m->dev, f3, tau, n, out, c->d_err, c->stream);
     if (e != cudaSuccess) return set_err(c, STK_ECUDA, "explicit scoring launch: %s", cudaGetErrorString(e));
+    return STK_OK;
+}
+
+int stk_set_template_shape(stk_ctx *c, int general, int t_min)
+{
+    if (!c) return STK_EINVAL;
+    if (general && t_min < 1) return set_err(c, STK_EINVAL, "t_min must be >= 1 column for general templates");
+    c->ts.general = general ? 1 : 0;
+    c->ts.t_min = general ? t_min : 0;
+    return STK_OK;
+}
+
+int stk_set_tau_prior(stk_ctx *c, const double *q, int n)
+{
+    if (!c) return STK_EINVAL;
+    if (!q || n == 0) {
+        c->ts.tau_q = nullptr;
+        c->ts.n_q = 0;
+        return STK_OK;
+    }
+    if (n < 2 || n > 65536) return set_err(c, STK_EINVAL, "the delay prior needs 2 .. 65536 quantiles");
+    for (int i = 0; i < n; ++i) {
+        if (!std::isfinite(q[i])) return set_err(c, STK_EINVAL, "delay quantile %d is not finite", i);
+        if (i && q[i] < q[i - 1]) return set_err(c, STK_EINVAL, "delay quantiles must not decrease (at %d)", i);
+    }
+    CUDA_TRY(c, cudaSetDevice(c->device));
+    int rc = ensure(c, (void **)&c->tauq_dev, &c->tauq_cap, sizeof(double) * (size_t)n);
+    if (rc) return rc;
+    CUDA_TRY(c, cudaMemcpyAsync(c->tauq_dev, q, sizeof(double) * (size_t)n, cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    c->ts.tau_q = c->tauq_dev;
+    c->ts.n_q = n;
+    return STK_OK;
+}
+
+int stk_track_times(stk_ctx *c, const stk_map *m, uint64_t g, uint32_t t[3])
+{
+    if (!c) return STK_EINVAL;
+    if (!t) return set_err(c, STK_EINVAL, "t is NULL");
+    uint32_t f[3];
+    double tau;
+    int rc = stk_track_params(c, m, g, f, &tau, nullptr);
+    if (rc) return rc;
+    CUDA_TRY(c, cudaMemcpy(t, (char *)c->small_dev + 12, 12, cudaMemcpyDeviceToHost));
+    return STK_OK;
+}
+
+int stk_score_explicit_general(stk_ctx *c, const stk_map *m, const uint32_t *t3, const uint32_t *f3,
+                               const double *tau, uint64_t n, double *out)
+{
+    if (!c) return STK_EINVAL;
+    if (!m || m->ctx != c) return set_err(c, STK_EINVAL, "map is NULL or belongs to another context");
+    if (n == 0) return STK_OK;
+    if (!t3 || !f3 || !tau || !out) return set_err(c, STK_EINVAL, "NULL pointer");
+    if (m->dev.n_t > 4096 || m->dev.n_f > 8192)
+        return set_err(c, STK_EINVAL, "general templates need n_t <= 4096 and n_f <= 8192");
+    CUDA_TRY(c, cudaSetDevice(c->device));
+    cudaError_t e = launch_score_explicit_general(m->dev, t3, f3, tau, n, out, c->d_err, c->stream);
+    if (e != cudaSuccess) return set_err(c, STK_ECUDA, "explicit general scoring launch: %s", cudaGetErrorString(e));
     return STK_OK;
 }
 

@@ -58,6 +58,10 @@ struct MapDev {
 struct TrackSet {
     uint64_t n, seed, offset;
     double tau_max;
+    const double *tau_q = nullptr;  // delay prior: n_q quantiles (tau at probability i/(n_q-1)); null: uniform
+    int n_q = 0;
+    int general = 0;                // 1: random start / middle / end times (six random numbers)
+    int t_min = 0;                  // general templates: end - start >= t_min columns
 };
 
 // ---------------------------------------------------------------- error bits (device flag)
@@ -120,6 +124,133 @@ __host__ __device__ __forceinline__ void draw_track(uint64_t seed, uint64_t g, u
     const uint64_t v = u[3] >> 12;
     const double unit = (double)(2 * v + 1) * 0x1p-52 - 1.0;
     tau = tau_max * unit;
+}
+
+// Delay from the prior's quantile table: q = (u >> 11) 2^-53 (n_q - 1), then linear
+// interpolation between quantiles floor(q) and floor(q) + 1.  Every step is one
+// IEEE operation, written out so no compiler fuses two of them.
+__host__ __device__ __forceinline__ double tau_from_prior(uint64_t u, const double *tq, int n_q)
+{
+#ifdef __CUDA_ARCH__
+    const double q = __dmul_rn((double)(u >> 11) * 0x1p-53, (double)(n_q - 1));
+    int i = (int)floor(q);
+    if (i > n_q - 2) i = n_q - 2;
+    const double fr = __dsub_rn(q, (double)i);
+    return __dadd_rn(tq[i], __dmul_rn(fr, __dsub_rn(tq[i + 1], tq[i])));
+#else
+    volatile double q = (double)(u >> 11) * 0x1p-53 * (double)(n_q - 1);
+    int i = (int)floor(q);
+    if (i > n_q - 2) i = n_q - 2;
+    volatile double fr = q - (double)i;
+    volatile double d = tq[i + 1] - tq[i];
+    volatile double p = fr * d;
+    return tq[i] + p;
+#endif
+}
+
+// Template with a delay prior: as draw_track, with tau from the quantile table.
+__host__ __device__ __forceinline__ void draw_track_ts(const TrackSet &ts, uint64_t g, uint32_t n_f, uint32_t f[3],
+                                                       double &tau)
+{
+    if (ts.n_q < 2) {
+        draw_track(ts.seed, g, n_f, ts.tau_max, f, tau);
+        return;
+    }
+    uint64_t u[4];
+    philox4x64_10(g, 0, 0, 0, ts.seed, 0, u);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        uint64_t hi, lo;
+        mul64_hilo(u[k], (uint64_t)n_f, hi, lo);
+        f[k] = (uint32_t)hi;
+    }
+    tau = tau_from_prior(u[3], ts.tau_q, ts.n_q);
+}
+
+// ---------------------------------------------------------------- general templates
+// Sec. III: three time-frequency control points P_k = (t_k, f_k) from six random
+// numbers, the curve persisting at least t_min.  Integer times t0 <= t1 <= t2,
+// t2 - t0 >= t_min: Philox block (g, 1, 0, 0) gives the duration d = t2 - t0
+// uniform on [t_min, n_t - 1], the start uniform on [0, n_t - 1 - d] and t1
+// uniform on [t0, t2]; frequencies and delay come from block (g, 0, 0, 0) as for
+// the pinned templates.
+__host__ __device__ __forceinline__ void draw_times(uint64_t seed, uint64_t g, uint32_t n_t, uint32_t t_min,
+                                                    uint32_t t[3])
+{
+    uint64_t v[4];
+    philox4x64_10(g, 1, 0, 0, seed, 0, v);
+    const uint64_t M = n_t - 1;
+    uint64_t hi, lo;
+    mul64_hilo(v[0], M - t_min + 1, hi, lo);
+    const uint64_t d = t_min + hi;
+    mul64_hilo(v[1], M - d + 1, hi, lo);
+    t[0] = (uint32_t)hi;
+    t[2] = (uint32_t)(hi + d);
+    mul64_hilo(v[2], d + 1, hi, lo);
+    t[1] = (uint32_t)(t[0] + hi);
+}
+
+// The curve t(xi) = A xi^2 + B xi + t0, f(xi) = F xi^2 + G xi + f0 (integer
+// coefficients).  Column j in [t0, t2] sits at the xi_j in [0, 1] with t(xi_j) = j:
+// xi_j = 2 (j - t0) / (sqrt(Delta_j) + B), Delta_j = B^2 + 4 A (j - t0) >= 0.  Its
+// pixel is the nearest bin to f(xi_j), halves rounded up: the largest b with
+// f(xi_j) >= b - 1/2.  With u = 2 (j - t0), s = sqrt(Delta_j), D = s + B and
+// E = 2 f0 - 2 b + 1:
+//   (2 f(xi_j) - (2b - 1)) D^2 = P + Q s,
+//   P = 2 F u^2 + 2 G u B + E (Delta_j + B^2),  Q = 2 G u + 2 E B,
+// whose sign is decided exactly in integers (|P| < 2^44, |Q| < 2^30 for
+// n_t <= 4096, n_f <= 8192; the squares compared need 128 bits).
+struct GenCurve {
+    int32_t t0, t2, A, B, F, G, f0;
+};
+
+__host__ __device__ __forceinline__ GenCurve gen_curve(const uint32_t t[3], const uint32_t f[3])
+{
+    GenCurve c;
+    c.t0 = (int32_t)t[0];
+    c.t2 = (int32_t)t[2];
+    c.A = (int32_t)t[0] - 2 * (int32_t)t[1] + (int32_t)t[2];
+    c.B = 2 * ((int32_t)t[1] - (int32_t)t[0]);
+    c.F = (int32_t)f[0] - 2 * (int32_t)f[1] + (int32_t)f[2];
+    c.G = 2 * ((int32_t)f[1] - (int32_t)f[0]);
+    c.f0 = (int32_t)f[0];
+    return c;
+}
+
+// x^2 (x < 2^63 in magnitude) and x * y (x, y >= 0) as 128-bit (hi, lo).
+__host__ __device__ __forceinline__ void umul128(uint64_t x, uint64_t y, uint64_t &hi, uint64_t &lo)
+{
+    mul64_hilo(x, y, hi, lo);
+}
+
+// f(xi_j) >= b - 1/2 ?  (j in (t0, t2])
+__host__ __device__ __forceinline__ bool gen_ge(const GenCurve &c, int64_t j, int64_t b)
+{
+    const int64_t du = j - c.t0;
+    const int64_t u = 2 * du;
+    const int64_t B = c.B;
+    const int64_t Dl = B * B + 4 * (int64_t)c.A * du;
+    const int64_t E = 2 * (int64_t)c.f0 - 2 * b + 1;
+    const int64_t P = 2 * (int64_t)c.F * u * u + 2 * (int64_t)c.G * u * B + E * (Dl + B * B);
+    const int64_t Q = 2 * (int64_t)c.G * u + 2 * E * B;
+    if (P >= 0 && Q >= 0) return true;
+    if (P <= 0 && Q <= 0) return P == 0 && Q == 0;
+    const uint64_t aP = (uint64_t)(P < 0 ? -P : P), aQ = (uint64_t)(Q < 0 ? -Q : Q);
+    uint64_t ph, pl, rh, rl;
+    umul128(aP, aP, ph, pl);                       // P^2
+    umul128(aQ * aQ, (uint64_t)Dl, rh, rl);        // Q^2 Delta  (Q^2 < 2^60)
+    const bool p_ge = ph > rh || (ph == rh && pl >= rl);
+    const bool r_ge = rh > ph || (rh == ph && rl >= pl);
+    return P > 0 ? p_ge : r_ge;                    // P > 0 > Q: P >= |Q| s;  Q > 0 > P: Q s >= |P|
+}
+
+// Pixel of column j given the previous column's pixel (bins move a few per column).
+__host__ __device__ __forceinline__ int32_t gen_step(const GenCurve &c, int64_t j, int32_t prev, int32_t n_f)
+{
+    int32_t b = prev;
+    while (b + 1 < n_f && gen_ge(c, j, b + 1)) ++b;
+    while (b > 0 && !gen_ge(c, j, b)) --b;
+    return b;
 }
 
 // ---------------------------------------------------------------- phase in turns
@@ -281,7 +412,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint64
 
 // ---------------------------------------------------------------- host-side launchers
 struct ScorePlan {
-    int kernel;       // 1 simple, 2 staged
+    int kernel;       // 1 simple, 2 staged, 3 general templates
     int R;            // templates per thread (staged)
     int threads;      // threads per block
     int grid;
@@ -307,7 +438,10 @@ cudaError_t launch_score_generated(const MapDev &m, const TrackSet &ts, double *
 // Explicit templates f3[n][3], tau[n].
 cudaError_t launch_score_explicit(const MapDev &m, const uint32_t *f3, const double *tau, uint64_t n, double *out,
                                   int *err, cudaStream_t st);
-// Parameters and bins of one template (device buffers).
+// Explicit general templates: t3[n][3] control times, f3[n][3] control bins.
+cudaError_t launch_score_explicit_general(const MapDev &m, const uint32_t *t3, const uint32_t *f3, const double *tau,
+                                          uint64_t n, double *out, int *err, cudaStream_t st);
+// Parameters (f_dev: 3 bins then 3 times), delay and bins of one template (device buffers).
 cudaError_t launch_track_params(const MapDev &m, const TrackSet &ts, uint64_t g, uint32_t *f_dev, double *tau_dev,
                                 int32_t *bins_dev, cudaStream_t st);
 

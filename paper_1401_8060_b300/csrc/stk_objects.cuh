@@ -25,8 +25,10 @@ struct stk_ctx {
     void *sel_buf = nullptr;       // scratch: selection state
     size_t sel_cap = 0;
     stk_hit *hits_dev = nullptr;   // STK_MAX_K records
-    uint32_t *small_dev = nullptr; // track_params: f[3] + pad, tau, bins
+    uint32_t *small_dev = nullptr; // track_params: f[3], t[3], tau, bins
     size_t small_cap = 0;
+    double *tauq_dev = nullptr;    // delay prior quantiles
+    size_t tauq_cap = 0;
     Tuning tune{};
     ScorePlan plan{};
     bool profiling = false;

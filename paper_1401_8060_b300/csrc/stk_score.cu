@@ -50,7 +50,7 @@ __global__ void __launch_bounds__(256) score_simple_kernel(MapDev m, TrackSet ts
         if (bad) atomicOr(err, ERR_BADTRACK);
         tau = tau_in[i];
     } else {
-        draw_track(ts.seed, ts.offset + i, (uint32_t)m.n_f, ts.tau_max, f, tau);
+        draw_track_ts(ts, ts.offset + i, (uint32_t)m.n_f, f, tau);
     }
     const Phase ph = phase_consts(m.f_min, m.df, tau);
     float acc = 0.f, W = 0.f;
@@ -72,6 +72,92 @@ __global__ void __launch_bounds__(256) score_simple_kernel(MapDev m, TrackSet ts
         accumulate<PREC, WMODE>(v, bin, ph, wv, acc, W);
     }
     out[i] = finalize_snr<WMODE>(acc, W, m);
+}
+
+// ------------------------------------------------------------------ general templates
+// Templates with random start, middle and end times (Sec. III: six random numbers,
+// duration >= t_min): one thread per template, pixels of its own columns t0 .. t2
+// only, from the L2-resident map; the exact integer rasteriser (gen_step) moves the
+// pixel from column to column.  N = t2 - t0 + 1 pixels.
+template <int WMODE, int PREC>
+__device__ __forceinline__ double finalize_general(float acc, float W, const MapDev &m, int N)
+{
+    if (m.paper) return (double)acc / (double)N;
+    if (WMODE == WMODE_CONST)
+        return (double)acc / sqrt((double)N * (PREC == PREC_FP16 ? 1.0 : (double)m.w_const));
+    const double y0 = (double)rsqrtf(W);
+    const double t = (double)W * y0 * y0;
+    return (double)acc * (y0 * fma(-0.5, t, 1.5));
+}
+
+template <int WMODE, int PREC, bool EXPLICIT>
+__global__ void __launch_bounds__(256) score_general_kernel(MapDev m, TrackSet ts, const uint32_t *__restrict__ t3,
+                                                            const uint32_t *__restrict__ f3,
+                                                            const double *__restrict__ tau_in, uint64_t n,
+                                                            double *__restrict__ out, int *err)
+{
+    const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint32_t f[3], t[3];
+    double tau;
+    if (EXPLICIT) {
+        bool bad = false;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            f[k] = f3[3 * i + k];
+            t[k] = t3[3 * i + k];
+            if (f[k] >= (uint32_t)m.n_f) { bad = true; f[k] = (uint32_t)m.n_f - 1; }
+            if (t[k] >= (uint32_t)m.n_t) { bad = true; t[k] = (uint32_t)m.n_t - 1; }
+        }
+        if (!(t[0] <= t[1] && t[1] <= t[2] && t[0] < t[2])) {  // not a valid time ordering: use the full span
+            bad = true;
+            t[0] = 0; t[2] = (uint32_t)m.n_t - 1; t[1] = t[2] / 2;
+        }
+        if (bad) atomicOr(err, ERR_BADTRACK);
+        tau = tau_in[i];
+    } else {
+        draw_track_ts(ts, ts.offset + i, (uint32_t)m.n_f, f, tau);
+        draw_times(ts.seed, ts.offset + i, (uint32_t)m.n_t, (uint32_t)ts.t_min, t);
+    }
+    const Phase ph = phase_consts(m.f_min, m.df, tau);
+    const GenCurve c = gen_curve(t, f);
+    float acc = 0.f, W = 0.f;
+    int32_t b = (int32_t)f[0];
+    for (int j = (int)t[0]; j <= (int)t[2]; ++j) {
+        if (j > (int)t[0]) b = gen_step(c, j, b, m.n_f);
+        const auto v = Pix<PREC>::load_global(m.rec, (size_t)j * m.ldr + (uint32_t)b);
+        float wv = 0.f;
+        if (WMODE == WMODE_FREQ) wv = __ldg(m.w + b);
+        if (WMODE == WMODE_PIXEL) wv = __ldg(m.w + (size_t)j * m.ldw + b);
+        accumulate<PREC, WMODE>(v, (uint32_t)b, ph, wv, acc, W);
+    }
+    out[i] = finalize_general<WMODE, PREC>(acc, W, m, (int)(t[2] - t[0] + 1));
+}
+
+template <int WMODE, int PREC, bool EXPLICIT>
+cudaError_t launch_general_W(const MapDev &m, const TrackSet &ts, const uint32_t *t3, const uint32_t *f3,
+                             const double *tau, uint64_t n, double *out, int *err, cudaStream_t st)
+{
+    const uint64_t blocks = (n + 255) / 256;
+    if (blocks > 0x7fffffffull) return cudaErrorInvalidValue;
+    score_general_kernel<WMODE, PREC, EXPLICIT><<<(unsigned)blocks, 256, 0, st>>>(m, ts, t3, f3, tau, n, out, err);
+    return cudaGetLastError();
+}
+
+template <bool EXPLICIT>
+cudaError_t launch_general(const MapDev &m, const TrackSet &ts, const uint32_t *t3, const uint32_t *f3,
+                           const double *tau, uint64_t n, double *out, int *err, cudaStream_t st)
+{
+#define STK_GEN(W, P) return launch_general_W<W, P, EXPLICIT>(m, ts, t3, f3, tau, n, out, err, st)
+    if (m.prec == PREC_FP16) {
+        if (m.wmode == WMODE_CONST) STK_GEN(WMODE_CONST, PREC_FP16);
+        if (m.wmode == WMODE_FREQ) STK_GEN(WMODE_FREQ, PREC_FP16);
+        STK_GEN(WMODE_PIXEL, PREC_FP16);
+    }
+    if (m.wmode == WMODE_CONST) STK_GEN(WMODE_CONST, PREC_FP32);
+    if (m.wmode == WMODE_FREQ) STK_GEN(WMODE_FREQ, PREC_FP32);
+    STK_GEN(WMODE_PIXEL, PREC_FP32);
+#undef STK_GEN
 }
 
 // ------------------------------------------------------------------ staged kernel
@@ -150,7 +236,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
             if (i >= tn) i = tn - 1;  // idle slot: repeat a valid template, result discarded
             uint32_t f[3];
             double tau;
-            draw_track(ts.seed, ts.offset + t0 + i, (uint32_t)m.n_f, ts.tau_max, f, tau);
+            draw_track_ts(ts, ts.offset + t0 + i, (uint32_t)m.n_f, f, tau);
             const Raster32 rs = raster_init(f[0], f[1], f[2], m.M);
             N[r] = rs.N; D[r] = rs.D; D2[r] = rs.D2;
             ph[r] = phase_consts(m.f_min, m.df, tau);
@@ -280,19 +366,36 @@ cudaError_t launch_simple(const MapDev &m, const TrackSet &ts, const uint32_t *f
 }
 
 // ------------------------------------------------------------------ template-params kernel
+// f_out[0..2] control bins, f_out[3..5] control times (general templates; else 0, M/2, M),
+// *tau_out the delay, bins[n_t] the pixels (-1 outside a general template's span).
 __global__ void track_params_kernel(MapDev m, TrackSet ts, uint64_t g, uint32_t *f_out, double *tau_out,
                                     int32_t *bins)
 {
-    uint32_t f[3];
+    uint32_t f[3], t[3] = {0u, (uint32_t)(m.n_t - 1) / 2, (uint32_t)(m.n_t - 1)};
     double tau;
-    draw_track(ts.seed, g, (uint32_t)m.n_f, ts.tau_max, f, tau);
+    draw_track_ts(ts, g, (uint32_t)m.n_f, f, tau);
+    if (ts.general) draw_times(ts.seed, g, (uint32_t)m.n_t, (uint32_t)ts.t_min, t);
     if (threadIdx.x == 0) {
         f_out[0] = f[0]; f_out[1] = f[1]; f_out[2] = f[2];
+        f_out[3] = t[0]; f_out[4] = t[1]; f_out[5] = t[2];
         *tau_out = tau;
     }
     if (!bins) return;
+    if (!ts.general) {
+        for (int j = threadIdx.x; j < m.n_t; j += blockDim.x)
+            bins[j] = (int32_t)raster_bin_wide(f[0], f[1], f[2], m.M, (uint32_t)j, m.d);
+        return;
+    }
     for (int j = threadIdx.x; j < m.n_t; j += blockDim.x)
-        bins[j] = (int32_t)raster_bin_wide(f[0], f[1], f[2], m.M, (uint32_t)j, m.d);
+        if (j < (int)t[0] || j > (int)t[2]) bins[j] = -1;
+    if (threadIdx.x == 0) {   // the rasteriser walks the columns in order
+        const GenCurve c = gen_curve(t, f);
+        int32_t b = (int32_t)f[0];
+        for (int j = (int)t[0]; j <= (int)t[2]; ++j) {
+            if (j > (int)t[0]) b = gen_step(c, j, b, m.n_f);
+            bins[j] = b;
+        }
+    }
 }
 
 }  // namespace
@@ -302,6 +405,13 @@ cudaError_t launch_score_generated(const MapDev &m, const TrackSet &ts, double *
 {
     ScorePlan p{};
     const uint64_t n = ts.n;
+    if (ts.general) {
+        p.kernel = 3;
+        p.threads = 256;
+        p.grid = (int)std::min<uint64_t>((n + 255) / 256, 0x7fffffffull);
+        if (plan) *plan = p;
+        return launch_general<false>(m, ts, nullptr, nullptr, nullptr, n, out, err, st);
+    }
     const uint64_t work = n * (uint64_t)m.n_t;
     int kernel = tu.kernel;
     if (kernel == 0) kernel = (!m.fast32 || work < (1ull << 24)) ? 1 : 2;
@@ -380,6 +490,13 @@ cudaError_t launch_score_explicit(const MapDev &m, const uint32_t *f3, const dou
 {
     TrackSet ts{};
     return launch_simple<true>(m, ts, f3, tau, n, out, err, st);
+}
+
+cudaError_t launch_score_explicit_general(const MapDev &m, const uint32_t *t3, const uint32_t *f3, const double *tau,
+                                          uint64_t n, double *out, int *err, cudaStream_t st)
+{
+    TrackSet ts{};
+    return launch_general<true>(m, ts, t3, f3, tau, n, out, err, st);
 }
 
 cudaError_t launch_track_params(const MapDev &m, const TrackSet &ts, uint64_t g, uint32_t *f_dev, double *tau_dev,

@@ -272,7 +272,7 @@ __device__ __forceinline__ void write_hit(const double *snr, unsigned int t, con
     hit.index = ts.offset + t;
     uint32_t f[3];
     double tau;
-    draw_track(ts.seed, ts.offset + t, (uint32_t)m.n_f, ts.tau_max, f, tau);
+    draw_track_ts(ts, ts.offset + t, (uint32_t)m.n_f, f, tau);
     hit.f[0] = f[0]; hit.f[1] = f[1]; hit.f[2] = f[2];
     hit.reserved = 0;
     hit.tau = tau;

@@ -392,3 +392,138 @@ def test_interp_gradient_matches_finite_differences(orc, paper):
                    om.interp_score(f[None], np.array([tau - ht]))[0]) / (2 * ht))
         np.testing.assert_allclose(g[0], fd, rtol=2e-5, atol=2e-5 * np.max(np.abs(fd)))
         checked += 1
+
+
+# ---------------------------------------------------------------- general templates (six random numbers)
+from decimal import Decimal, getcontext  # noqa: E402
+
+
+def general_bins_decimal(t, f, n_t):
+    """Independent rasteriser: solve t(xi) = j with 60-digit decimals, take the
+    nearest bin of f(xi_j) (halves up).  Columns where f(xi_j) is within 1e-40
+    of a half-integer are decided exactly with fractions when Delta is a square,
+    else reported as None (undecided here)."""
+    getcontext().prec = 60
+    t0, t1, t2 = (Decimal(v) for v in t)
+    f0, f1, f2 = (Decimal(v) for v in f)
+    a, b = t0 - 2 * t1 + t2, 2 * (t1 - t0)
+    out = []
+    for j in range(n_t):
+        if j < t[0] or j > t[2]:
+            out.append(-1)
+            continue
+        if j == t[0]:
+            out.append(int(f[0]))
+            continue
+        dj = Decimal(j) - t0
+        delta = b * b + 4 * a * dj
+        xi = 2 * dj / (delta.sqrt() + b)
+        fx = (1 - xi) ** 2 * f0 + 2 * (1 - xi) * xi * f1 + xi ** 2 * f2
+        k = int((fx + Decimal("0.5")).to_integral_value(rounding="ROUND_FLOOR"))
+        frac = fx + Decimal("0.5") - k
+        if frac < Decimal("1e-40") or frac > 1 - Decimal("1e-40"):
+            di = int(b * b + 4 * a * dj)
+            r = math.isqrt(di)
+            if r * r != di:
+                out.append(None)
+                continue
+            xr = Fraction(2 * (j - t[0]), r + int(b))
+            fr = (1 - xr) ** 2 * f[0] + 2 * (1 - xr) * xr * f[1] + xr ** 2 * f[2]
+            k = math.floor(fr + Fraction(1, 2))
+        out.append(k)
+    return out
+
+
+def _same_except_undecided(got, ref):
+    for g, r in zip(got, ref):
+        if r is not None:
+            assert g == r, (list(got), ref)
+
+
+def test_general_times_definition(orc):
+    n_t, t_min, seed = 200, 30, 5
+    M = n_t - 1
+    for g in [0, 1, 17, 123456, 2 ** 50 + 1]:
+        prev = [g - 1, 1, 0, 0] if g else [2 ** 64 - 1, 0, 0, 0]       # numpy steps the counter first
+        v = [int(x) for x in np.random.Philox(key=np.array([seed, 0], dtype=np.uint64),
+                                              counter=np.array(prev, dtype=np.uint64)).random_raw(4)]
+        t = orc.track_times(seed, g, n_t, t_min)
+        d = t[2] - t[0]
+        assert (d - t_min) * 2 ** 64 <= v[0] * (M - t_min + 1) < (d - t_min + 1) * 2 ** 64
+        assert t[0] * 2 ** 64 <= v[1] * (M - d + 1) < (t[0] + 1) * 2 ** 64
+        assert (t[1] - t[0]) * 2 ** 64 <= v[2] * (d + 1) < (t[1] - t[0] + 1) * 2 ** 64
+        assert 0 <= t[0] <= t[1] <= t[2] <= M and d >= t_min
+
+
+@pytest.mark.parametrize("n_t", [3, 5, 9])
+def test_general_rasteriser_exhaustive_tiny(orc, n_t):
+    n_f = 6
+    for t0 in range(n_t):
+        for t2 in range(t0 + 1, n_t):
+            for t1 in range(t0, t2 + 1):
+                for f in [(0, 5, 2), (3, 3, 3), (5, 0, 5), (1, 4, 0), (2, 2, 5)]:
+                    got = orc.track_bins_general((t0, t1, t2), f, n_t, n_f)
+                    _same_except_undecided(got, general_bins_decimal((t0, t1, t2), f, n_t))
+
+
+def test_general_rasteriser_random_and_invariants(orc):
+    rng = np.random.default_rng(40)
+    for _ in range(60):
+        n_t = int(rng.integers(3, 400))
+        n_f = int(rng.integers(2, 3000))
+        t0, t2 = sorted(int(v) for v in rng.choice(n_t, 2, replace=False))
+        t1 = int(rng.integers(t0, t2 + 1))
+        f = [int(v) for v in rng.integers(0, n_f, 3)]
+        b = orc.track_bins_general((t0, t1, t2), f, n_t, n_f)
+        _same_except_undecided(b, general_bins_decimal((t0, t1, t2), f, n_t))
+        assert b[t0] == f[0] and b[t2] == f[2]
+        span = b[t0:t2 + 1]
+        assert span.min() >= min(f) and span.max() <= max(f) and np.all(b[:t0] == -1) and np.all(b[t2 + 1:] == -1)
+        M = n_t - 1   # time reversal: the same curve traversed backwards
+        rb = orc.track_bins_general((M - t2, M - t1, M - t0), f[::-1], n_t, n_f)
+        np.testing.assert_array_equal(rb[::-1], b)
+    # middle time at the midpoint: the pinned rasteriser
+    for n_t in (5, 21, 201):
+        M = n_t - 1
+        for f in [(3, 90, 40), (0, 0, 77), (99, 1, 50)]:
+            np.testing.assert_array_equal(orc.track_bins_general((0, M // 2, M), f, n_t, 100), orc.track_bins(f, n_t))
+
+
+def test_general_score_bruteforce(orc):
+    n_t, n_f = 30, 40
+    y, sig = _tiny_map(41, n_t, n_f)
+    rng = np.random.default_rng(42)
+    for paper in (False, True):
+        om = orc.OracleMap(y, sig, 60.0, 0.5, False, paper_mode=paper)
+        t3, f3, taus, ref = [], [], [], []
+        for _ in range(40):
+            t0, t2 = sorted(int(v) for v in rng.choice(n_t, 2, replace=False))
+            t1 = int(rng.integers(t0, t2 + 1))
+            f = [int(v) for v in rng.integers(0, n_f, 3)]
+            tau = float(rng.uniform(-0.01, 0.01))
+            bins = orc.track_bins_general((t0, t1, t2), f, n_t, n_f)
+            j = np.nonzero(bins >= 0)[0]
+            yv = y[j, bins[j]].astype(np.complex128)
+            s = sig[j, bins[j]].astype(np.float64)
+            rot = np.exp(2j * np.pi * (60.0 + bins[j] * 0.5) * tau)
+            ref.append(np.sum((rot * yv / s).real) / len(j) if paper else
+                       np.sum((rot * yv / s ** 2).real) / np.sqrt(np.sum(s ** -2.0)))
+            t3.append((t0, t1, t2)); f3.append(f); taus.append(tau)
+        np.testing.assert_allclose(om.score_explicit_general(t3, f3, taus), ref, rtol=1e-12, atol=1e-12)
+
+
+def test_delay_prior_quantiles(orc):
+    """Delays drawn through a quantile table follow its piecewise-linear CDF (KS),
+    and a two-point table from -tau_max to tau_max is the uniform prior."""
+    from scipy import stats
+    q = np.array([-0.004, -0.0035, -0.001, 0.0, 0.0005, 0.0042])
+    taus = np.array([orc.track_params_prior(7, g, 100, q)[1] for g in range(20000)])
+    assert taus.min() >= q[0] and taus.max() <= q[-1]
+    probs = np.linspace(0, 1, q.size)
+    cdf = lambda x: np.interp(x, q, probs)   # noqa: E731
+    assert stats.kstest(taus, cdf).pvalue > 1e-4
+    uni = np.array([orc.track_params_prior(7, g, 100, [-0.01, 0.01])[1] for g in range(200)])
+    ref = np.array([orc.track_params(7, g, 100, 0.01)[1] for g in range(200)])
+    np.testing.assert_allclose(uni, ref, rtol=0, atol=1e-17)
+    # bins do not depend on the prior
+    assert orc.track_params_prior(7, 5, 100, q)[0] == orc.track_params(7, 5, 100, 0.01)[0]
