@@ -366,7 +366,8 @@ def main():
         variants["general_templates"] = {
             "value": pxg / (msg / 1e3), "unit": "track-pixels/s (expected pixels)", "ms_per_step": msg,
             "kernel_ms": sum(kg) / len(kg), "templates": Tg, "t_min_columns": tmin_g,
-            "rasteriser": "exact integer nearest-bin test per column, one thread per template, L2 gathers"}
+            "rasteriser": "FP32 estimate of the curve's frequency, exact integer test within a proven error "
+                          "margin of a rounding boundary; one thread per template, L2 gathers"}
         ctx.set_template_shape(False)
         ctx.set_tracks(T, w["seed"], offset, w["tau_max"])
 

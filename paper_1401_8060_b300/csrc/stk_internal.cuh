@@ -253,6 +253,45 @@ __host__ __device__ __forceinline__ int32_t gen_step(const GenCurve &c, int64_t 
     return b;
 }
 
+// Filtered pixel: an FP32 estimate of f(xi_j) decides the bin when it lies
+// farther than `margin` from a rounding boundary; otherwise the exact test does.
+// Error of the estimate (IEEE sqrt and divide, FMA evaluation): Delta_j < 2^27 is
+// rounded once (2^-24), s = sqrt once more, D = s + B and xi = u / D each add one
+// rounding, so |d xi| <= 4 2^-24 xi; f = f0 + xi (G + F xi) then errs by at most
+// (|G| + 2|F|) |d xi| + 3 ulp(f0 + |G| + |F|) < 2.4e-7 (|G| + 2|F|) + 3.6e-7 (f0 + |G| + |F|),
+// and f + 1/2 one more ulp.  The margin takes four times that.
+struct GenFilter {
+    float F, G, f0, B, margin;
+};
+
+__host__ __device__ __forceinline__ GenFilter gen_filter(const GenCurve &c)
+{
+    GenFilter g;
+    g.F = (float)c.F;
+    g.G = (float)c.G;
+    g.f0 = (float)c.f0;
+    g.B = (float)c.B;
+    const float aF = fabsf(g.F), aG = fabsf(g.G);
+    g.margin = 4.f * (2.4e-7f * (aG + 2.f * aF) + 3.6e-7f * (g.f0 + aG + aF + 1.f)) + 1e-6f;
+    return g;
+}
+
+__device__ __forceinline__ int32_t gen_pixel(const GenCurve &c, const GenFilter &g, int64_t j, int32_t n_f)
+{
+    const int32_t du = (int32_t)(j - c.t0);
+    const int32_t Dl = c.B * c.B + 4 * c.A * du;   // exact, < 2^27
+    const float s = __fsqrt_rn((float)Dl);
+    const float xi = __fdiv_rn((float)(2 * du), __fadd_rn(s, g.B));
+    const float fx = fmaf(xi, fmaf(g.F, xi, g.G), g.f0);
+    const float h = fx + 0.5f;
+    const float k = floorf(h);
+    const float d = h - k;
+    int32_t b = (int32_t)k;
+    b = b < 0 ? 0 : (b > n_f - 1 ? n_f - 1 : b);
+    if (d > g.margin && d < 1.f - g.margin) return b;
+    return gen_step(c, j, b, n_f);                 // near a boundary: exact
+}
+
 // ---------------------------------------------------------------- phase in turns
 // theta_j / 2 pi = (f_min + bin_j df) tau = b + bin_j a  (mod 1), with
 // a = frac(df tau) kept as unsigned Q0.64 (a_hi:a_lo) and b = frac(f_min tau)

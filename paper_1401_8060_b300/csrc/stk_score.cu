@@ -121,10 +121,11 @@ __global__ void __launch_bounds__(256) score_general_kernel(MapDev m, TrackSet t
     }
     const Phase ph = phase_consts(m.f_min, m.df, tau);
     const GenCurve c = gen_curve(t, f);
+    const GenFilter gf = gen_filter(c);
     float acc = 0.f, W = 0.f;
     int32_t b = (int32_t)f[0];
     for (int j = (int)t[0]; j <= (int)t[2]; ++j) {
-        if (j > (int)t[0]) b = gen_step(c, j, b, m.n_f);
+        if (j > (int)t[0]) b = gen_pixel(c, gf, j, m.n_f);
         const auto v = Pix<PREC>::load_global(m.rec, (size_t)j * m.ldr + (uint32_t)b);
         float wv = 0.f;
         if (WMODE == WMODE_FREQ) wv = __ldg(m.w + b);
@@ -390,9 +391,10 @@ __global__ void track_params_kernel(MapDev m, TrackSet ts, uint64_t g, uint32_t 
         if (j < (int)t[0] || j > (int)t[2]) bins[j] = -1;
     if (threadIdx.x == 0) {   // the rasteriser walks the columns in order
         const GenCurve c = gen_curve(t, f);
+        const GenFilter gf = gen_filter(c);
         int32_t b = (int32_t)f[0];
         for (int j = (int)t[0]; j <= (int)t[2]; ++j) {
-            if (j > (int)t[0]) b = gen_step(c, j, b, m.n_f);
+            if (j > (int)t[0]) b = gen_pixel(c, gf, j, m.n_f);
             bins[j] = b;
         }
     }
