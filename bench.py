@@ -256,7 +256,7 @@ def main():
 
     import torch
     import paper_1401_8060_b300 as stk
-    from paper_1401_8060_b300 import build, synth
+    from paper_1401_8060_b300 import build, search, synth
 
     if world > 1:
         import torch.distributed as dist
@@ -476,8 +476,7 @@ def main():
         gathered = [None] * world
         dist.all_gather_object(gathered, hits.tobytes())
         if rank == 0:
-            allh = np.concatenate([np.frombuffer(b, dtype=stk.HIT_DTYPE) for b in gathered])
-            hits = allh[np.lexsort((allh["index"], -allh["snr"]))[:K]]
+            hits = search.merge_hits([np.frombuffer(b, dtype=stk.HIT_DTYPE) for b in gathered], K)
 
     if rank == 0:
         clocks = clk.summary()

@@ -314,6 +314,10 @@ STK_API int stk_score_noalloc(const stk_map *map, uint64_t n_tracks, uint64_t se
 #define STK_OPT_MAX_R    3 /* slab kernel: most templates held per thread, 1 .. 6 (default 6; at most 5 with a varying weight) */
 #define STK_OPT_STAGES   4 /* slab kernel: shared-memory slab buffers, 2 .. 4 (default 2) */
 #define STK_OPT_SMEM_KB  5 /* slab kernel: shared-memory budget in KiB, 0 = the device maximum */
+#define STK_OPT_WAIT_MS  6 /* slab kernel: limit of each in-kernel wait for a slab copy, ms (0 = 2000) */
+#define STK_OPT_WITHHOLD_SLAB 7 /* test of the bounded waits: the first CTA never issues the copy of its
+                                   slab number value (-1 = off, the default); the call then ends with
+                                   STK_ETIMEOUT after the wait limit and the context stays usable */
 
 /* Set a tuning option for later scoring calls.  Errors: STK_EINVAL. */
 STK_API int stk_set_option(stk_ctx *ctx, int option, int64_t value);

@@ -269,6 +269,14 @@ int stk_set_option(stk_ctx *c, int option, int64_t value)
         if (value < 0 || value > 1024) return set_err(c, STK_EINVAL, "shared-memory budget out of range");
         c->tune.smem_kb = (int)value;
         return STK_OK;
+    case STK_OPT_WAIT_MS:
+        if (value < 0 || value > 60000) return set_err(c, STK_EINVAL, "wait limit must be in [0, 60000] ms");
+        c->tune.wait_ms = (int)value;
+        return STK_OK;
+    case STK_OPT_WITHHOLD_SLAB:
+        if (value < -1 || value > (1 << 30)) return set_err(c, STK_EINVAL, "slab index out of range");
+        c->tune.withhold_slab = (int)value;
+        return STK_OK;
     default: return set_err(c, STK_EINVAL, "unknown option %d", option);
     }
 }

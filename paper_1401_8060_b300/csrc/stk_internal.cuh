@@ -469,6 +469,8 @@ struct Tuning {
     int max_R = 6;       // capped per weight mode by the launcher
     int nstage = 2;
     int smem_kb = 0;     // 0 auto
+    int wait_ms = 0;     // slab wait limit, 0: 2000 ms
+    int withhold_slab = -1;  // test of the bounded waits: CTA 0 withholds this slab copy (-1: off)
 };
 
 // Launch the scoring kernel for generated templates; writes n SNRs to out.

@@ -168,6 +168,8 @@ struct StagedArgs {
     uint32_t slab_recs;    // S * ldr
     uint32_t slab_ws;      // S * ldw (WMODE_PIXEL)
     uint32_t wtab_floats;  // n_f rounded to 4 (WMODE_FREQ)
+    uint64_t wait_ns;      // limit of each slab wait
+    uint64_t withhold_q;   // test of the bounded waits: CTA 0 never issues its slab number withhold_q
 };
 
 template <int R, int WMODE, int PREC>
@@ -201,6 +203,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
 
     // Producer: slab q of this CTA's sequence goes to buffer q % nstage.
     auto issue = [&](uint64_t q) {
+        if (blockIdx.x == 0 && q == a.withhold_q) return;  // a copy that never comes: the wait must give up
         const int slot = (int)(q % (uint64_t)a.nstage);
         const int slab = (int)(q % (uint64_t)a.nslabs);
         const int row0 = slab * a.S;
@@ -248,7 +251,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
         for (int s = 0; s < a.nslabs; ++s, ++q) {
             const int slot = (int)(q % (uint64_t)a.nstage);
             const uint32_t parity = (uint32_t)((q / (uint64_t)a.nstage) & 1ull);
-            const bool ok = mbar_wait(&bars[slot], parity, kWaitLimitNs);
+            const bool ok = mbar_wait(&bars[slot], parity, a.wait_ns);
             const int rows = min(a.S, m.n_t - s * a.S);
             const Rec *row = srec + (size_t)slot * a.slab_recs;
             const float *wrow = sw + (size_t)slot * a.slab_ws;
@@ -287,7 +290,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
         // Let copies already issued (slab q and up to nstage - 1 after it) land before
         // the CTA's shared memory goes away; each wait is bounded too.
         for (uint64_t qq = q; qq < q + (uint64_t)a.nstage && qq < total; ++qq)
-            mbar_wait(&bars[qq % a.nstage], (uint32_t)((qq / a.nstage) & 1ull), kWaitLimitNs);
+            mbar_wait(&bars[qq % a.nstage], (uint32_t)((qq / a.nstage) & 1ull), a.wait_ns);
     }
 }
 
@@ -474,6 +477,8 @@ cudaError_t launch_score_generated(const MapDev &m, const TrackSet &ts, double *
             sa.slab_recs = (uint32_t)(S * m.ldr);
             sa.slab_ws = m.wmode == WMODE_PIXEL ? (uint32_t)(S * m.ldw) : 0u;
             sa.wtab_floats = m.wmode == WMODE_FREQ ? (uint32_t)((m.n_f + 3) / 4 * 4) : 0u;
+            sa.wait_ns = tu.wait_ms > 0 ? (uint64_t)tu.wait_ms * 1000000ull : kWaitLimitNs;
+            sa.withhold_q = tu.withhold_slab >= 0 ? (uint64_t)tu.withhold_slab : ~0ull;
             if (plan) *plan = p;
             if (m.prec == PREC_FP16)
                 return launch_staged_P<PREC_FP16>(R, m, ts, sa, p.grid, threads, p.smem, out, err, st);
