@@ -104,10 +104,19 @@ STK_API int stk_set_stream(stk_ctx *ctx, void *cuda_stream);
 STK_API int stk_load_map(stk_ctx *ctx, const void *y_c64, const float *sigma, int n_t, int n_f,
                  double f_min_hz, double df_hz, unsigned flags, stk_map **out);
 
+/* Replace a map's data with new y and sigma of the same shape, statistic and
+ * precision (flags must equal the map's, STK_HOST_PTR aside), packing into the
+ * map's existing device buffers: nothing is allocated except, on the first
+ * host-pointer update of a context, its staging buffers.  For streams of
+ * same-sized maps (time windows, time shifts).  Synchronous.  Errors:
+ * STK_EINVAL (as stk_load_map, or flags differing from the map's), STK_ECUDA;
+ * after an error the map's contents are undefined until an update succeeds. */
+STK_API int stk_update_map(stk_ctx *ctx, stk_map *map, const void *y_c64, const float *sigma, unsigned flags);
+
 /* Free a packed map (waits for the context's stream).  NULL is a no-op. */
 STK_API void stk_free_map(stk_map *map);
 
-/* Report a map's shape and flags (any pointer may be NULL). */
+/* Report a map's shape and flags (STK_HOST_PTR cleared; any pointer may be NULL). */
 STK_API int stk_map_info(const stk_map *map, int *n_t, int *n_f, unsigned *flags);
 
 /* Set the template range scored by later calls (Sec. III: T templates drawn at

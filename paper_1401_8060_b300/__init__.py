@@ -145,6 +145,23 @@ class Context:
         del keep
         return Map(self, h, int(n_t), int(n_f), flags)
 
+    def update_map(self, m: Map, y, sigma):
+        """stk_update_map: new data of the same shape into an existing map (no allocation)."""
+        self._bind_stream()
+        host = not (_is_tensor(y) and y.is_cuda)
+        if host:
+            ya = np.ascontiguousarray(y.numpy() if _is_tensor(y) else y, dtype=np.complex64)
+            sa = np.ascontiguousarray(sigma.numpy() if _is_tensor(sigma) else sigma, dtype=np.float32)
+            yp, sp, keep = ya.ctypes.data, sa.ctypes.data, (ya, sa)
+        else:
+            y, sigma = y.contiguous(), sigma.contiguous()
+            yp, sp, keep = y.data_ptr(), sigma.data_ptr(), (y, sigma)
+        if tuple(keep[0].shape) != (m.n_t, m.n_f):
+            raise ValueError("y shape differs from the map's")
+        flags = (m.flags & ~L.STK_HOST_PTR) | (L.STK_HOST_PTR if host else 0)
+        self._check(lib().stk_update_map(self._h, m.handle, C.c_void_p(yp), C.c_void_p(sp), flags))
+        del keep
+
     def set_tracks(self, n_tracks: int, seed: int, offset: int = 0, tau_max: float = 0.010):
         """stk_set_tracks: templates offset .. offset+n_tracks-1 drawn with `seed`."""
         self._check(lib().stk_set_tracks(self._h, int(n_tracks), int(seed), int(offset), float(tau_max)))

@@ -31,6 +31,7 @@ SIGNATURES = [
     ("stk_set_stream", C.c_int, [_vp, _vp]),
     ("stk_load_map", C.c_int, [_vp, _vp, _vp, C.c_int, C.c_int, C.c_double, C.c_double, C.c_uint,
                                C.POINTER(_vp)]),
+    ("stk_update_map", C.c_int, [_vp, _vp, _vp, _vp, C.c_uint]),
     ("stk_free_map", None, [_vp]),
     ("stk_map_info", C.c_int, [_vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_uint)]),
     ("stk_set_tracks", C.c_int, [_vp, C.c_uint64, C.c_uint64, C.c_uint64, C.c_double]),

@@ -233,6 +233,8 @@ void stk_destroy(stk_ctx *c)
     cudaFree(c->hits_dev);
     cudaFree(c->small_dev);
     cudaFree(c->tauq_dev);
+    cudaFree(c->stage_y);
+    cudaFree(c->stage_s);
     for (auto &ev : c->ev)
         if (ev) cudaEventDestroy(ev);
     delete c;
@@ -290,6 +292,67 @@ int stk_last_plan(const stk_ctx *c, int64_t out[8])
     return STK_OK;
 }
 
+// Copy (host pointers: through the context's staging buffers) and pack y, sigma
+// into the map's buffers; set the weighting mode and normalisation.  Synchronises.
+static int pack_into(stk_ctx *c, stk_map *m, const void *y_c64, const float *sigma, unsigned flags)
+{
+    MapDev &d = m->dev;
+    const int n_t = d.n_t, n_f = d.n_f;
+    const bool host = flags & STK_HOST_PTR, per_freq = flags & STK_SIGMA_PER_FREQ, paper = flags & STK_NORM_PAPER;
+    const bool fp16 = flags & STK_FP16;
+    const size_t npx = (size_t)n_t * n_f;
+    const size_t ybytes = npx * 8, sbytes = (per_freq ? (size_t)n_f : npx) * 4;
+    const float2 *ysrc = (const float2 *)y_c64;
+    const float *ssrc = sigma;
+    if (host) {
+        int rc = ensure(c, &c->stage_y, &c->stage_y_cap, ybytes);
+        if (rc) return rc;
+        rc = ensure(c, &c->stage_s, &c->stage_s_cap, sbytes);
+        if (rc) return rc;
+        CUDA_TRY(c, cudaMemcpyAsync(c->stage_y, y_c64, ybytes, cudaMemcpyHostToDevice, c->stream));
+        CUDA_TRY(c, cudaMemcpyAsync(c->stage_s, sigma, sbytes, cudaMemcpyHostToDevice, c->stream));
+        ysrc = (const float2 *)c->stage_y;
+        ssrc = (const float *)c->stage_s;
+    }
+    const size_t wbytes = per_freq ? (size_t)d.ldw * 4 : (size_t)n_t * d.ldw * 4;
+    CUDA_TRY(c, cudaMemsetAsync(m->w_buf, 0, wbytes, c->stream));
+    CUDA_TRY(c, cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
+    const uint64_t total = (uint64_t)n_t * d.ldr;
+    const int blocks = (int)std::min<uint64_t>((total + 255) / 256, (uint64_t)c->num_sms * 8);
+    if (fp16)
+        pack_fp16_kernel<<<blocks, 256, 0, c->stream>>>(ysrc, ssrc, per_freq ? 1 : 0, n_t, n_f, d.ldr, d.ldw,
+                                                         (uint32_t *)m->rec_buf, (float *)m->w_buf, c->d_err);
+    else
+        pack_kernel<<<blocks, 256, 0, c->stream>>>(ysrc, ssrc, per_freq ? 1 : 0, n_t, n_f, d.ldr, d.ldw, d.paper,
+                                                    (uint2 *)m->rec_buf, (float *)m->w_buf, c->d_err);
+    CUDA_TRY(c, cudaGetLastError());
+    int fl = 0;
+    int rc = read_err_flags(c, &fl);
+    if (rc) return rc;
+    if (fl & ERR_BADINPUT) return set_err(c, STK_EINVAL, "y has a non-finite value or sigma is <= 0 or non-finite");
+    if (fl & ERR_FP16_RANGE) return set_err(c, STK_EINVAL, "FP16 storage: |y| / sigma exceeds 65504");
+    if (paper) {
+        d.wmode = WMODE_CONST;
+        d.w_const = 1.0f;
+    } else if (!(fl & FLAG_SIGMA_VARIES)) {
+        d.wmode = WMODE_CONST;
+        float w0 = 0.f;
+        CUDA_TRY(c, cudaMemcpy(&w0, m->w_buf, sizeof(float), cudaMemcpyDeviceToHost));
+        d.w_const = w0;
+    } else {
+        d.wmode = per_freq ? WMODE_FREQ : WMODE_PIXEL;
+    }
+    // constant weight: FP32 records hold |y| w0 (SNR = S / sqrt(n_t w0)); FP16 records hold
+    // |y| / sigma0 (SNR = S r0 / sqrt(n_t r0^2) = S / sqrt(n_t)); paper form: S / n_t
+    if (paper) d.norm = 1.0 / (double)n_t;
+    else if (d.wmode == WMODE_CONST) d.norm = fp16 ? 1.0 / std::sqrt((double)n_t)
+                                                   : 1.0 / std::sqrt((double)n_t * (double)d.w_const);
+    else d.norm = 0.0;
+    d.rec = m->rec_buf;
+    d.w = d.wmode == WMODE_CONST ? nullptr : (const float *)m->w_buf;
+    return STK_OK;
+}
+
 int stk_load_map(stk_ctx *c, const void *y_c64, const float *sigma, int n_t, int n_f, double f_min_hz,
                  double df_hz, unsigned flags, stk_map **out)
 {
@@ -310,14 +373,12 @@ int stk_load_map(stk_ctx *c, const void *y_c64, const float *sigma, int n_t, int
     if (flags & ~(STK_HOST_PTR | STK_SIGMA_PER_FREQ | STK_NORM_PAPER | STK_FP16))
         return set_err(c, STK_EINVAL, "unknown flags 0x%x", flags);
     CUDA_TRY(c, cudaSetDevice(c->device));
-    const bool host = flags & STK_HOST_PTR, per_freq = flags & STK_SIGMA_PER_FREQ, paper = flags & STK_NORM_PAPER;
+    const bool per_freq = flags & STK_SIGMA_PER_FREQ, paper = flags & STK_NORM_PAPER;
     const bool fp16 = flags & STK_FP16;
-    const size_t npx = (size_t)n_t * n_f;
-    const size_t ybytes = npx * 8, sbytes = (per_freq ? (size_t)n_f : npx) * 4;
 
     stk_map *m = new stk_map();
     m->ctx = c;
-    m->flags = flags;
+    m->flags = flags & ~STK_HOST_PTR;
     MapDev &d = m->dev;
     d.n_t = n_t;
     d.n_f = n_f;
@@ -332,76 +393,37 @@ int stk_load_map(stk_ctx *c, const void *y_c64, const float *sigma, int n_t, int
     const uint64_t n_max = (uint64_t)d.M * d.M * (2ull * (uint64_t)n_f - 1);
     d.fast32 = find_magic(d.d, n_max, d.magic, d.shift) ? 1 : 0;
 
-    void *ytmp = nullptr, *stmp = nullptr;
-    auto fail = [&](int code) {
+    cudaError_t e;
+    const size_t recbytes = (size_t)n_t * d.ldr * (fp16 ? 4 : 8);
+    const size_t wbytes = per_freq ? (size_t)d.ldw * 4 : (size_t)n_t * d.ldw * 4;
+    if ((e = cudaMalloc(&m->rec_buf, recbytes)) != cudaSuccess || (e = cudaMalloc(&m->w_buf, wbytes)) != cudaSuccess) {
+        cudaFree(m->rec_buf);
+        delete m;
+        return set_err(c, STK_ENOMEM, "map allocation (%zu bytes): %s", recbytes + wbytes, cudaGetErrorString(e));
+    }
+    int rc = pack_into(c, m, y_c64, sigma, flags);
+    if (rc) {
         cudaStreamSynchronize(c->stream);
-        cudaFree(ytmp);
-        cudaFree(stmp);
         cudaFree(m->rec_buf);
         cudaFree(m->w_buf);
         delete m;
-        return code;
-    };
-    cudaError_t e;
-    const float2 *ysrc = (const float2 *)y_c64;
-    const float *ssrc = sigma;
-    if (host) {
-        if ((e = cudaMalloc(&ytmp, ybytes)) != cudaSuccess || (e = cudaMalloc(&stmp, sbytes)) != cudaSuccess)
-            return fail(set_err(c, STK_ENOMEM, "staging allocation: %s", cudaGetErrorString(e)));
-        if ((e = cudaMemcpyAsync(ytmp, y_c64, ybytes, cudaMemcpyHostToDevice, c->stream)) != cudaSuccess ||
-            (e = cudaMemcpyAsync(stmp, sigma, sbytes, cudaMemcpyHostToDevice, c->stream)) != cudaSuccess)
-            return fail(set_err(c, STK_ECUDA, "host-to-device copy: %s", cudaGetErrorString(e)));
-        ysrc = (const float2 *)ytmp;
-        ssrc = (const float *)stmp;
+        return rc;
     }
-    const size_t recbytes = (size_t)n_t * d.ldr * (fp16 ? 4 : 8);
-    if ((e = cudaMalloc(&m->rec_buf, recbytes)) != cudaSuccess)
-        return fail(set_err(c, STK_ENOMEM, "map allocation (%zu bytes): %s", recbytes, cudaGetErrorString(e)));
-    const size_t wbytes = per_freq ? (size_t)d.ldw * 4 : (size_t)n_t * d.ldw * 4;
-    if ((e = cudaMalloc(&m->w_buf, wbytes)) != cudaSuccess)
-        return fail(set_err(c, STK_ENOMEM, "weight allocation: %s", cudaGetErrorString(e)));
-    if ((e = cudaMemsetAsync(m->w_buf, 0, wbytes, c->stream)) != cudaSuccess ||
-        (e = cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream)) != cudaSuccess)
-        return fail(set_err(c, STK_ECUDA, "memset: %s", cudaGetErrorString(e)));
-    const uint64_t total = (uint64_t)n_t * d.ldr;
-    const int blocks = (int)std::min<uint64_t>((total + 255) / 256, (uint64_t)c->num_sms * 8);
-    if (fp16)
-        pack_fp16_kernel<<<blocks, 256, 0, c->stream>>>(ysrc, ssrc, per_freq ? 1 : 0, n_t, n_f, d.ldr, d.ldw,
-                                                         (uint32_t *)m->rec_buf, (float *)m->w_buf, c->d_err);
-    else
-        pack_kernel<<<blocks, 256, 0, c->stream>>>(ysrc, ssrc, per_freq ? 1 : 0, n_t, n_f, d.ldr, d.ldw, d.paper,
-                                                    (uint2 *)m->rec_buf, (float *)m->w_buf, c->d_err);
-    if ((e = cudaGetLastError()) != cudaSuccess)
-        return fail(set_err(c, STK_ECUDA, "pack kernel launch: %s", cudaGetErrorString(e)));
-    int fl = 0;
-    if (read_err_flags(c, &fl) != STK_OK) return fail(STK_ECUDA);
-    if (fl & ERR_BADINPUT) return fail(set_err(c, STK_EINVAL, "y has a non-finite value or sigma is <= 0 or non-finite"));
-    if (fl & ERR_FP16_RANGE) return fail(set_err(c, STK_EINVAL, "FP16 storage: |y| / sigma exceeds 65504"));
-    cudaFree(ytmp);
-    cudaFree(stmp);
-    ytmp = stmp = nullptr;
-    if (paper) {
-        d.wmode = WMODE_CONST;
-        d.w_const = 1.0f;
-    } else if (!(fl & FLAG_SIGMA_VARIES)) {
-        d.wmode = WMODE_CONST;
-        float w0 = 0.f;
-        if ((e = cudaMemcpy(&w0, m->w_buf, sizeof(float), cudaMemcpyDeviceToHost)) != cudaSuccess)
-            return fail(set_err(c, STK_ECUDA, "weight read-back: %s", cudaGetErrorString(e)));
-        d.w_const = w0;
-    } else {
-        d.wmode = per_freq ? WMODE_FREQ : WMODE_PIXEL;
-    }
-    // constant weight: FP32 records hold |y| w0 (SNR = S / sqrt(n_t w0)); FP16 records hold
-    // |y| / sigma0 (SNR = S r0 / sqrt(n_t r0^2) = S / sqrt(n_t)); paper form: S / n_t
-    if (paper) d.norm = 1.0 / (double)n_t;
-    else if (d.wmode == WMODE_CONST) d.norm = fp16 ? 1.0 / std::sqrt((double)n_t)
-                                                   : 1.0 / std::sqrt((double)n_t * (double)d.w_const);
-    else d.norm = 0.0;
-    d.rec = m->rec_buf;
-    d.w = d.wmode == WMODE_CONST ? nullptr : (const float *)m->w_buf;
     *out = m;
     return STK_OK;
+}
+
+int stk_update_map(stk_ctx *c, stk_map *m, const void *y_c64, const float *sigma, unsigned flags)
+{
+    if (!c) return STK_EINVAL;
+    if (!m || m->ctx != c) return set_err(c, STK_EINVAL, "map is NULL or belongs to another context");
+    if (!y_c64 || !sigma) return set_err(c, STK_EINVAL, "y or sigma is NULL");
+    if (flags & ~(STK_HOST_PTR | STK_SIGMA_PER_FREQ | STK_NORM_PAPER | STK_FP16))
+        return set_err(c, STK_EINVAL, "unknown flags 0x%x", flags);
+    if ((flags & ~STK_HOST_PTR) != m->flags)
+        return set_err(c, STK_EINVAL, "flags 0x%x do not match the map's (0x%x, host flag aside)", flags, m->flags);
+    CUDA_TRY(c, cudaSetDevice(c->device));
+    return pack_into(c, m, y_c64, sigma, flags);
 }
 
 void stk_free_map(stk_map *m)

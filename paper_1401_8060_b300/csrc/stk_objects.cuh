@@ -29,6 +29,10 @@ struct stk_ctx {
     size_t small_cap = 0;
     double *tauq_dev = nullptr;    // delay prior quantiles
     size_t tauq_cap = 0;
+    void *stage_y = nullptr;       // host-pointer map uploads: y and sigma staged here
+    size_t stage_y_cap = 0;
+    void *stage_s = nullptr;
+    size_t stage_s_cap = 0;
     Tuning tune{};
     ScorePlan plan{};
     bool profiling = false;

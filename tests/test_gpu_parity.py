@@ -292,6 +292,34 @@ def test_host_and_device_maps_identical(ctx):
     np.testing.assert_array_equal(ctx.score_all(mh).cpu().numpy(), ctx.score_all(md).cpu().numpy())
 
 
+@pytest.mark.parametrize("fp16", [False, True])
+@pytest.mark.parametrize("host", [False, True])
+def test_update_map_equals_fresh_load(ctx, fp16, host):
+    """stk_update_map re-packs into the map's buffers: scores equal a fresh load's
+    bit for bit, also when the new sigma changes the weighting (per-frequency
+    varying -> constant -> varying), and the oracle agrees."""
+    n_t, n_f = 64, 150
+    ya, sa = rand_map(61, n_t, n_f, "freq")
+    dev = (lambda a: a) if host else (lambda a: torch.from_numpy(a).cuda())
+    m = ctx.load_map(dev(ya), dev(sa), 40.0, 0.5, fp16=fp16)
+    ctx.set_tracks(4000, 3, 0, 0.01)
+    for seed, mode in [(62, "const"), (63, "freq"), (64, "const")]:
+        yb, sb = rand_map(seed, n_t, n_f, mode)
+        ctx.update_map(m, dev(yb), dev(sb))
+        fresh = ctx.load_map(dev(yb), dev(sb), 40.0, 0.5, fp16=fp16)
+        a, b = ctx.score_all(m).cpu().numpy(), ctx.score_all(fresh).cpu().numpy()
+        np.testing.assert_array_equal(a, b)
+        fresh.close()
+        if not fp16:
+            om = oracle.OracleMap(yb, sb, 40.0, 0.5, True)
+            f3, tau = oracle_params(3, 0, 300, n_f, 0.01)
+            o, ex = om.score_explicit(f3, tau, extras=True)
+            assert_snr_close(a[:300], o, ex, False, n_t, what=f"update {mode}")
+    with pytest.raises(ValueError):            # a different shape is rejected before any copy
+        ctx.update_map(m, dev(np.ones((n_t, n_f + 1), np.complex64)), dev(np.ones(n_f + 1, np.float32)))
+    m.close()
+
+
 def test_invalid_inputs_rejected(ctx):
     L = _lib
     y = np.ones((10, 8), np.complex64)
