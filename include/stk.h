@@ -233,8 +233,9 @@ STK_API int stk_set_profiling(stk_ctx *ctx, int enable);
 
 /* Per-kernel device time of the last stk_score / stk_score_all call, in ms:
  * out[0] scoring kernel, out[1] selection (all top-k kernels), out[2] launch
- * count of that call.  Requires profiling on; synchronises the stream. */
-STK_API int stk_last_timings(stk_ctx *ctx, double out[3]);
+ * count of that call, out[3] coherent-order pre-pass (0 when not used).
+ * Requires profiling on; synchronises the stream. */
+STK_API int stk_last_timings(stk_ctx *ctx, double out[4]);
 
 /* ---- many maps in one launch --------------------------------------------
  * A search records the loudest SNR of every map (Sec. V: year-long runs cut
@@ -327,14 +328,20 @@ STK_API int stk_score_noalloc(const stk_map *map, uint64_t n_tracks, uint64_t se
 #define STK_OPT_WITHHOLD_SLAB 7 /* test of the bounded waits: the first CTA never issues the copy of its
                                    slab number value (-1 = off, the default); the call then ends with
                                    STK_ETIMEOUT after the wait limit and the context stays usable */
+#define STK_OPT_ORDER    8 /* slab kernel: 1 (default) scores templates in a coherent order -- a bucket
+                              sort of the template indices by a Z-order key of (f0, f1, f2) -- so a warp's
+                              pixel gathers fall in a narrow band of bins and shared-memory banks
+                              rarely collide; 0 scores in index order.  Results are identical; the
+                              order costs 8 bytes per template plus 8 MiB of context scratch */
 
 /* Set a tuning option for later scoring calls.  Errors: STK_EINVAL. */
 STK_API int stk_set_option(stk_ctx *ctx, int option, int64_t value);
 
-/* Launch shape of the last scoring call: out[0] kernel (1 simple, 2 slab),
- * [1] templates per thread, [2] threads per block, [3] grid, [4] time columns
- * per slab, [5] slab buffers, [6] template batches, [7] dynamic shared bytes. */
-STK_API int stk_last_plan(const stk_ctx *ctx, int64_t out[8]);
+/* Launch shape of the last scoring call: out[0] kernel (1 simple, 2 slab,
+ * 3 general templates), [1] templates per thread, [2] threads per block,
+ * [3] grid, [4] time columns per slab, [5] slab buffers, [6] template batches,
+ * [7] dynamic shared bytes, [8] 1 if templates were scored in coherent order. */
+STK_API int stk_last_plan(const stk_ctx *ctx, int64_t out[9]);
 
 /* Message for the last error on ctx (never NULL; "" when none). */
 STK_API const char *stk_last_error(const stk_ctx *ctx);

@@ -286,18 +286,18 @@ class Context:
         self._check(lib().stk_set_option(self._h, int(option), int(value)))
 
     def last_plan(self) -> dict:
-        a = (C.c_int64 * 8)()
+        a = (C.c_int64 * 9)()
         self._check(lib().stk_last_plan(self._h, a))
-        keys = ["kernel", "R", "threads", "grid", "S", "nstage", "nbatches", "smem"]
+        keys = ["kernel", "R", "threads", "grid", "S", "nstage", "nbatches", "smem", "order"]
         return dict(zip(keys, [int(v) for v in a]))
 
     def set_profiling(self, on: bool):
         self._check(lib().stk_set_profiling(self._h, 1 if on else 0))
 
     def last_timings(self) -> dict:
-        a = (C.c_double * 3)()
+        a = (C.c_double * 4)()
         self._check(lib().stk_last_timings(self._h, a))
-        return dict(score_ms=a[0], select_ms=a[1], launches=int(a[2]))
+        return dict(score_ms=a[0], select_ms=a[1], launches=int(a[2]), order_ms=a[3])
 
 
 class Batch:

@@ -235,6 +235,7 @@ void stk_destroy(stk_ctx *c)
     cudaFree(c->tauq_dev);
     cudaFree(c->stage_y);
     cudaFree(c->stage_s);
+    cudaFree(c->order_buf);
     for (auto &ev : c->ev)
         if (ev) cudaEventDestroy(ev);
     delete c;
@@ -275,6 +276,10 @@ int stk_set_option(stk_ctx *c, int option, int64_t value)
         if (value < 0 || value > 60000) return set_err(c, STK_EINVAL, "wait limit must be in [0, 60000] ms");
         c->tune.wait_ms = (int)value;
         return STK_OK;
+    case STK_OPT_ORDER:
+        if (value < 0 || value > 1) return set_err(c, STK_EINVAL, "order option must be 0 or 1");
+        c->tune.order = (int)value;
+        return STK_OK;
     case STK_OPT_WITHHOLD_SLAB:
         if (value < -1 || value > (1 << 30)) return set_err(c, STK_EINVAL, "slab index out of range");
         c->tune.withhold_slab = (int)value;
@@ -283,12 +288,13 @@ int stk_set_option(stk_ctx *c, int option, int64_t value)
     }
 }
 
-int stk_last_plan(const stk_ctx *c, int64_t out[8])
+int stk_last_plan(const stk_ctx *c, int64_t out[9])
 {
     if (!c || !out) return STK_EINVAL;
     const ScorePlan &p = c->plan;
     out[0] = p.kernel; out[1] = p.R; out[2] = p.threads; out[3] = p.grid;
     out[4] = p.S; out[5] = p.nstage; out[6] = (int64_t)p.nbatches; out[7] = (int64_t)p.smem;
+    out[8] = p.order;
     return STK_OK;
 }
 
@@ -464,9 +470,15 @@ int stk_set_tracks(stk_ctx *c, uint64_t n_tracks, uint64_t seed, uint64_t counte
 static int score_into(stk_ctx *c, const stk_map *m, double *out)
 {
     CUDA_TRY(c, cudaSetDevice(c->device));
+    void *order = nullptr;
+    if (score_wants_order(m->dev, c->ts, c->tune)) {
+        int rc = ensure(c, &c->order_buf, &c->order_cap, order_scratch_bytes(c->ts.n, m->dev.n_f));
+        if (rc) return rc;
+        order = c->order_buf;
+    }
     if (c->profiling) CUDA_TRY(c, cudaEventRecord(c->ev[0], c->stream));
     cudaError_t e = launch_score_generated(m->dev, c->ts, out, c->d_err, c->tune, c->num_sms, c->smem_optin,
-                                           c->stream, &c->plan);
+                                           c->stream, &c->plan, order, c->profiling ? c->ev[3] : nullptr);
     if (e != cudaSuccess) return set_err(c, STK_ECUDA, "scoring kernel launch: %s", cudaGetErrorString(e));
     if (c->profiling) CUDA_TRY(c, cudaEventRecord(c->ev[1], c->stream));
     return STK_OK;
@@ -481,7 +493,7 @@ int stk_score_all(stk_ctx *c, const stk_map *m, double *out_snr_dev)
     rc = score_into(c, m, out_snr_dev);
     if (rc) return rc;
     c->timed = c->profiling;
-    c->last_launches = 1;
+    c->last_launches = 1 + (c->plan.order ? c->plan.order_launches : 0);
     if (c->profiling) CUDA_TRY(c, cudaEventRecord(c->ev[2], c->stream));
     return STK_OK;
 }
@@ -505,7 +517,7 @@ int stk_score(stk_ctx *c, const stk_map *m, int k, stk_hit *out, unsigned flags)
     int nl = 0;
     cudaError_t e = launch_select_topk(c->snr_buf, c->ts.n, k, c->ts, m->dev, c->sel_buf, dst, c->stream, &nl);
     if (e != cudaSuccess) return set_err(c, STK_ECUDA, "selection launch: %s", cudaGetErrorString(e));
-    c->last_launches = 1 + nl;
+    c->last_launches = 1 + nl + (c->plan.order ? c->plan.order_launches : 0);
     c->timed = c->profiling;
     if (c->profiling) CUDA_TRY(c, cudaEventRecord(c->ev[2], c->stream));
     if (flags & STK_OUT_HOST) {
@@ -657,17 +669,19 @@ int stk_set_profiling(stk_ctx *c, int enable)
     return STK_OK;
 }
 
-int stk_last_timings(stk_ctx *c, double out[3])
+int stk_last_timings(stk_ctx *c, double out[4])
 {
     if (!c || !out) return STK_EINVAL;
     if (!c->timed) return set_err(c, STK_ESTATE, "no profiled call yet (stk_set_profiling)");
     CUDA_TRY(c, cudaEventSynchronize(c->ev[2]));
-    float a = 0.f, b = 0.f;
-    CUDA_TRY(c, cudaEventElapsedTime(&a, c->ev[0], c->ev[1]));
+    float a = 0.f, b = 0.f, o = 0.f;
+    CUDA_TRY(c, cudaEventElapsedTime(&o, c->ev[0], c->ev[3]));
+    CUDA_TRY(c, cudaEventElapsedTime(&a, c->ev[3], c->ev[1]));
     CUDA_TRY(c, cudaEventElapsedTime(&b, c->ev[1], c->ev[2]));
     out[0] = a;
     out[1] = b;
     out[2] = c->last_launches;
+    out[3] = o;
     return STK_OK;
 }
 

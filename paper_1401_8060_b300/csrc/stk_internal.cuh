@@ -461,6 +461,8 @@ struct ScorePlan {
     uint64_t batch;   // templates per batch (staged)
     uint64_t nbatches;
     size_t smem;
+    int order;           // 1: templates scored in coherent (Z-order) order, 0: index order
+    int order_launches;  // launches of the ordering pre-pass
 };
 
 struct Tuning {
@@ -471,11 +473,22 @@ struct Tuning {
     int smem_kb = 0;     // 0 auto
     int wait_ms = 0;     // slab wait limit, 0: 2000 ms
     int withhold_slab = -1;  // test of the bounded waits: CTA 0 withholds this slab copy (-1: off)
+    int order = 1;       // slab kernel: score templates in coherent order (1) or index order (0)
 };
 
 // Launch the scoring kernel for generated templates; writes n SNRs to out.
+// order_scratch (order_scratch_bytes(n, n_f) bytes, or NULL for index order)
+// holds the coherent-order pre-pass of the slab kernel; order_done, if given,
+// is recorded between that pre-pass and the scoring kernel.
 cudaError_t launch_score_generated(const MapDev &m, const TrackSet &ts, double *out, int *err, const Tuning &tu,
-                                   int num_sms, size_t smem_optin, cudaStream_t st, ScorePlan *plan_out);
+                                   int num_sms, size_t smem_optin, cudaStream_t st, ScorePlan *plan_out,
+                                   void *order_scratch = nullptr, cudaEvent_t order_done = nullptr);
+// Whether launch_score_generated would use order scratch for this call.
+bool score_wants_order(const MapDev &m, const TrackSet &ts, const Tuning &tu);
+size_t order_scratch_bytes(uint64_t n, int n_f);
+// Coherent-order pre-pass (stk_order.cu): *perm_out = the scoring order inside scratch.
+cudaError_t launch_order(const MapDev &m, const TrackSet &ts, void *scratch, int num_sms, cudaStream_t st,
+                         const uint32_t **perm_out, int *launches);
 // Explicit templates f3[n][3], tau[n].
 cudaError_t launch_score_explicit(const MapDev &m, const uint32_t *f3, const double *tau, uint64_t n, double *out,
                                   int *err, cudaStream_t st);

@@ -33,10 +33,12 @@ struct stk_ctx {
     size_t stage_y_cap = 0;
     void *stage_s = nullptr;
     size_t stage_s_cap = 0;
+    void *order_buf = nullptr;     // coherent-order pre-pass of the slab kernel
+    size_t order_cap = 0;
     Tuning tune{};
     ScorePlan plan{};
     bool profiling = false;
-    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};  // start, scoring done, selection done, order done
     bool timed = false;
     int last_launches = 0;
     std::string err;

@@ -170,6 +170,7 @@ struct StagedArgs {
     uint32_t wtab_floats;  // n_f rounded to 4 (WMODE_FREQ)
     uint64_t wait_ns;      // limit of each slab wait
     uint64_t withhold_q;   // test of the bounded waits: CTA 0 never issues its slab number withhold_q
+    const uint32_t *perm;  // scoring order: position p holds template offset + perm[p] (NULL: index order)
 };
 
 template <int R, int WMODE, int PREC>
@@ -238,9 +239,10 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
         for (int r = 0; r < R; ++r) {
             uint64_t i = (uint64_t)tid + (uint64_t)r * nthr;
             if (i >= tn) i = tn - 1;  // idle slot: repeat a valid template, result discarded
+            const uint64_t rel = a.perm ? (uint64_t)__ldg(a.perm + t0 + i) : t0 + i;
             uint32_t f[3];
             double tau;
-            draw_track_ts(ts, ts.offset + t0 + i, (uint32_t)m.n_f, f, tau);
+            draw_track_ts(ts, ts.offset + rel, (uint32_t)m.n_f, f, tau);
             const Raster32 rs = raster_init(f[0], f[1], f[2], m.M);
             N[r] = rs.N; D[r] = rs.D; D2[r] = rs.D2;
             ph[r] = phase_consts(m.f_min, m.df, tau);
@@ -282,7 +284,10 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             const uint64_t i = (uint64_t)tid + (uint64_t)r * nthr;
-            if (i < tn) out[t0 + i] = finalize_snr<WMODE>(acc[r], W[r], m);
+            if (i < tn) {
+                const uint64_t rel = a.perm ? (uint64_t)__ldg(a.perm + t0 + i) : t0 + i;
+                out[rel] = finalize_snr<WMODE>(acc[r], W[r], m);
+            }
         }
     }
     if (failed && tid == 0) {
@@ -405,8 +410,15 @@ __global__ void track_params_kernel(MapDev m, TrackSet ts, uint64_t g, uint32_t 
 
 }  // namespace
 
+bool score_wants_order(const MapDev &m, const TrackSet &ts, const Tuning &tu)
+{
+    if (!tu.order || ts.general || !m.fast32 || tu.kernel == 1) return false;
+    return tu.kernel == 2 || ts.n * (uint64_t)m.n_t >= (1ull << 24);
+}
+
 cudaError_t launch_score_generated(const MapDev &m, const TrackSet &ts, double *out, int *err, const Tuning &tu,
-                                   int num_sms, size_t smem_optin, cudaStream_t st, ScorePlan *plan)
+                                   int num_sms, size_t smem_optin, cudaStream_t st, ScorePlan *plan,
+                                   void *order_scratch, cudaEvent_t order_done)
 {
     ScorePlan p{};
     const uint64_t n = ts.n;
@@ -415,6 +427,7 @@ cudaError_t launch_score_generated(const MapDev &m, const TrackSet &ts, double *
         p.threads = 256;
         p.grid = (int)std::min<uint64_t>((n + 255) / 256, 0x7fffffffull);
         if (plan) *plan = p;
+        if (order_done && cudaEventRecord(order_done, st) != cudaSuccess) return cudaGetLastError();
         return launch_general<false>(m, ts, nullptr, nullptr, nullptr, n, out, err, st);
     }
     const uint64_t work = n * (uint64_t)m.n_t;
@@ -479,6 +492,16 @@ cudaError_t launch_score_generated(const MapDev &m, const TrackSet &ts, double *
             sa.wtab_floats = m.wmode == WMODE_FREQ ? (uint32_t)((m.n_f + 3) / 4 * 4) : 0u;
             sa.wait_ns = tu.wait_ms > 0 ? (uint64_t)tu.wait_ms * 1000000ull : kWaitLimitNs;
             sa.withhold_q = tu.withhold_slab >= 0 ? (uint64_t)tu.withhold_slab : ~0ull;
+            sa.perm = nullptr;
+            if (order_scratch && score_wants_order(m, ts, tu)) {
+                cudaError_t e = launch_order(m, ts, order_scratch, num_sms, st, &sa.perm, &p.order_launches);
+                if (e != cudaSuccess) return e;
+                p.order = 1;
+            }
+            if (order_done) {
+                cudaError_t e = cudaEventRecord(order_done, st);
+                if (e != cudaSuccess) return e;
+            }
             if (plan) *plan = p;
             if (m.prec == PREC_FP16)
                 return launch_staged_P<PREC_FP16>(R, m, ts, sa, p.grid, threads, p.smem, out, err, st);
@@ -489,6 +512,10 @@ cudaError_t launch_score_generated(const MapDev &m, const TrackSet &ts, double *
     p.threads = 256;
     p.grid = (int)std::min<uint64_t>((n + 255) / 256, 0x7fffffffull);
     if (plan) *plan = p;
+    if (order_done) {
+        cudaError_t e = cudaEventRecord(order_done, st);
+        if (e != cudaSuccess) return e;
+    }
     return launch_simple<false>(m, ts, nullptr, nullptr, n, out, err, st);
 }
 

@@ -147,6 +147,44 @@ def test_kernels_agree_bitwise(ctx):
         np.testing.assert_array_equal(r, res[0])
 
 
+@pytest.mark.parametrize("n_t,n_f,T,prior", [(40, 1, 5000, False), (33, 2, 7001, False), (50, 7, 20000, True),
+                                              (64, 128, 30000, False), (64, 129, 30001, True),
+                                              (20, 8192, 100003, False), (500, 1600, 200000, False)])
+def test_coherent_order_identical(ctx, n_t, n_f, T, prior):
+    """The slab kernel scores templates in coherent (Z-order) order by default;
+    every template's SNR is bit for bit the one of index order and of the
+    one-thread-per-template kernel, and lands at its own index."""
+    y, sig = rand_map(23, n_t, n_f, "freq")
+    m, om = load_both(ctx, y, sig, 40.0, 0.5)
+    if prior:
+        ctx.set_tau_prior(np.linspace(-0.004, 0.009, 17))
+    ctx.set_tracks(T, 5, 123, 0.01)
+    res = {}
+    try:
+        for kernel, order in [(2, 1), (2, 0), (1, 1)]:
+            ctx.set_option(_lib.STK_OPT_KERNEL, kernel)
+            ctx.set_option(_lib.STK_OPT_ORDER, order)
+            res[(kernel, order)] = ctx.score_all(m).cpu().numpy()
+            assert ctx.last_plan()["order"] == (1 if kernel == 2 and order else 0)
+    finally:
+        ctx.set_option(_lib.STK_OPT_KERNEL, 0)
+        ctx.set_option(_lib.STK_OPT_ORDER, 1)
+        if prior:
+            ctx.set_tau_prior(None)
+    np.testing.assert_array_equal(res[(2, 1)], res[(2, 0)])
+    np.testing.assert_array_equal(res[(2, 1)], res[(1, 1)])
+    # and the values are the oracle's for a sample of indices
+    idx = np.random.default_rng(3).choice(T, 200, replace=False)
+    if prior:
+        pr = [oracle.track_params_prior(5, 123 + int(i), n_f, np.linspace(-0.004, 0.009, 17)) for i in idx]
+    else:
+        pr = [oracle.track_params(5, 123 + int(i), n_f, 0.01) for i in idx]
+    f3 = np.array([p[0] for p in pr], dtype=np.uint32)
+    tau = np.array([p[1] for p in pr])
+    o, ex = om.score_explicit(f3, tau, extras=True)
+    assert_snr_close(res[(2, 1)][idx], o, ex, False, n_t, what="coherent order")
+
+
 @pytest.mark.parametrize("threads,max_r,stages", [(64, 1, 2), (96, 3, 3), (1024, 4, 4), (512, 2, 2), (992, 5, 2)])
 def test_launch_shapes_agree(ctx, threads, max_r, stages):
     n_t, n_f, T = 45, 300, 30001
