@@ -341,18 +341,16 @@ __host__ __device__ __forceinline__ Phase phase_consts(double f_min, double df, 
     const uint64_t b = frac_prod_q64(f_min, tau);
     p.a_lo = (uint32_t)a;
     p.a_hi = (uint32_t)(a >> 32);
-    p.b = (uint32_t)((b + 0x80000000ull) >> 32) + 0x100u;
+    p.b = (uint32_t)((b + 0x80000000ull) >> 32);
     return p;
 }
 
-// Angle (turns, unsigned Q0.32) -> cos(2 pi turn).  The top 23 bits of the
-// turn, with the sign bit flipped, form the mantissa of a float in [1, 2); minus
-// 1.5 that is the turn mapped to [-0.5, 0.5).  __cosf is accurate to about
-// 2^-21 absolute on [-pi, pi].
+// Angle (turns, Q0.32 read as signed, i.e. in [-1/2, 1/2)) -> cos(2 pi turn).
+// The integer-to-float conversion rounds to 24 significant bits (error at most
+// 2^-25 turn); __cosf is accurate to about 2^-21 absolute on [-pi, pi].
 __device__ __forceinline__ float cos_turn(uint32_t t)
 {
-    const float x = __uint_as_float((t >> 9) ^ 0x3fc00000u) - 1.5f;
-    return __cosf(x * 6.28318530717958647692f);
+    return __cosf((float)(int32_t)t * 1.46291807926715968e-9f);  // 2 pi / 2^32
 }
 
 __device__ __forceinline__ uint32_t pixel_turn(uint32_t bin, const Phase &p, uint32_t arg)
@@ -408,6 +406,13 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t by
 {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
                  : "memory");
+}
+
+// Order this thread's earlier shared-memory accesses (generic proxy) before
+// later bulk copies into shared memory (async proxy).
+__device__ __forceinline__ void fence_proxy_async_smem()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
 // One-dimensional bulk copy global -> shared, completing `bytes` on `bar`.

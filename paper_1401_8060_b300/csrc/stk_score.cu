@@ -162,6 +162,12 @@ cudaError_t launch_general(const MapDev &m, const TrackSet &ts, const uint32_t *
 }
 
 // ------------------------------------------------------------------ staged kernel
+constexpr int kMaxStages = 4;
+// shared bytes after the slabs and weight table: full barriers, last issued
+// slab and finished-warp count per buffer, abort flag
+constexpr size_t kStagedBookkeeping = 128;
+static_assert(kMaxStages * (8 + 8 + 4) + 4 <= kStagedBookkeeping, "bookkeeping block too small");
+
 struct StagedArgs {
     int S, nstage, nslabs;
     uint64_t batch, nbatches;
@@ -173,28 +179,41 @@ struct StagedArgs {
     const uint32_t *perm;  // scoring order: position p holds template offset + perm[p] (NULL: index order)
 };
 
+// Slab pipeline without block-wide barriers: a slab buffer is refilled by the
+// warp that finishes it last (a shared counter per buffer elects it), so a warp
+// waits only for the slab it needs next and warps may drift by up to nstage - 1
+// slabs.  Every wait is bounded; a warp that gives up raises a shared flag and
+// the others stop at their next slab.
 template <int R, int WMODE, int PREC>
 __global__ void __launch_bounds__(kMaxThreads, 1)
     score_staged_kernel(MapDev m, TrackSet ts, StagedArgs a, double *__restrict__ out, int *err)
 {
     using Rec = typename Pix<PREC>::Rec;
     extern __shared__ __align__(128) unsigned char smem[];
-    Rec *srec = reinterpret_cast<Rec *>(smem);
+    // bookkeeping first (fixed offsets), then the slab buffers and weight table
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem);               // full barrier per buffer
+    uint64_t *issued = bars + kMaxStages;                               // last slab issued into each buffer
+    uint32_t *done = reinterpret_cast<uint32_t *>(issued + kMaxStages);  // warps finished with each buffer
+    int *abort_flag = reinterpret_cast<int *>(done + kMaxStages);
+    Rec *srec = reinterpret_cast<Rec *>(smem + kStagedBookkeeping);
     float *sw = reinterpret_cast<float *>(srec + (size_t)a.nstage * a.slab_recs);  // WMODE_PIXEL slabs
     float *swt = sw + (WMODE == WMODE_PIXEL ? (size_t)a.nstage * a.slab_ws : 0);    // WMODE_FREQ table
-    uint64_t *bars = reinterpret_cast<uint64_t *>(swt + (WMODE == WMODE_FREQ ? a.wtab_floats : 0));
 
     const int tid = threadIdx.x;
     const int nthr = blockDim.x;
+    const int lane = tid & 31;
     if (blockIdx.x >= a.nbatches) return;
     const uint64_t my_nb = (a.nbatches - blockIdx.x + gridDim.x - 1) / gridDim.x;
     const uint64_t total = my_nb * (uint64_t)a.nslabs;  // slabs this CTA consumes, over all its batches
-    const uint32_t row_bytes = (uint32_t)m.ldr * (uint32_t)sizeof(Rec);
-    const uint32_t wrow_bytes = (uint32_t)m.ldw * 4u;
     const Rec *grec = reinterpret_cast<const Rec *>(m.rec);
 
     if (tid == 0) {
-        for (int s = 0; s < a.nstage; ++s) mbar_init(&bars[s], 1);
+        for (int s = 0; s < a.nstage; ++s) {
+            mbar_init(&bars[s], 1);
+            issued[s] = ~0ull;
+            done[s] = 0u;
+        }
+        *abort_flag = 0;
         fence_mbar_init();
     }
     if (WMODE == WMODE_FREQ) {
@@ -202,15 +221,16 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
     }
     __syncthreads();
 
-    // Producer: slab q of this CTA's sequence goes to buffer q % nstage.
-    auto issue = [&](uint64_t q) {
+    // Producer: slab q of this CTA's sequence (slab index sl of a batch) goes to buffer `slot`.
+    auto issue = [&](uint64_t q, int slot, int sl) {
         if (blockIdx.x == 0 && q == a.withhold_q) return;  // a copy that never comes: the wait must give up
-        const int slot = (int)(q % (uint64_t)a.nstage);
-        const int slab = (int)(q % (uint64_t)a.nslabs);
-        const int row0 = slab * a.S;
+        const int row0 = sl * a.S;
         const int rows = min(a.S, m.n_t - row0);
+        const uint32_t row_bytes = (uint32_t)m.ldr * (uint32_t)sizeof(Rec);
+        const uint32_t wrow_bytes = (uint32_t)m.ldw * 4u;
         uint32_t bytes = (uint32_t)rows * row_bytes;
         if (WMODE == WMODE_PIXEL) bytes += (uint32_t)rows * wrow_bytes;
+        issued[slot] = q;
         mbar_arrive_expect_tx(&bars[slot], bytes);
         bulk_g2s(srec + (size_t)slot * a.slab_recs, grec + (size_t)row0 * m.ldr, (uint32_t)rows * row_bytes,
                  &bars[slot]);
@@ -219,13 +239,15 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
                      &bars[slot]);
     };
     if (tid == 0) {
-        const uint64_t pre = total < (uint64_t)a.nstage ? total : (uint64_t)a.nstage;
-        for (uint64_t q = 0; q < pre; ++q) issue(q);
+        const int pre = (int)(total < (uint64_t)a.nstage ? total : (uint64_t)a.nstage);
+        for (int q0 = 0; q0 < pre; ++q0) issue((uint64_t)q0, q0, q0 % a.nslabs);
     }
 
     const uint32_t magic = m.magic;
     const int shift = m.shift;
-    uint64_t q = 0;
+    uint64_t q = 0;      // slab sequence number
+    int slot = 0;        // q % nstage
+    uint32_t parity = 0; // (q / nstage) & 1
     bool failed = false;
     for (uint64_t ib = 0; ib < my_nb && !failed; ++ib) {
         const uint64_t b = blockIdx.x + ib * gridDim.x;
@@ -251,9 +273,13 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
         }
 
         for (int s = 0; s < a.nslabs; ++s, ++q) {
-            const int slot = (int)(q % (uint64_t)a.nstage);
-            const uint32_t parity = (uint32_t)((q / (uint64_t)a.nstage) & 1ull);
-            const bool ok = mbar_wait(&bars[slot], parity, a.wait_ns);
+            const bool ok = __all_sync(0xffffffffu, mbar_wait(&bars[slot], parity, a.wait_ns)) &&
+                            !*(volatile int *)abort_flag;
+            if (!ok) {
+                if (lane == 0) atomicOr(abort_flag, 1);
+                failed = true;
+                break;
+            }
             const int rows = min(a.S, m.n_t - s * a.S);
             const Rec *row = srec + (size_t)slot * a.slab_recs;
             const float *wrow = sw + (size_t)slot * a.slab_ws;
@@ -273,12 +299,25 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
                 row += m.ldr;
                 if (WMODE == WMODE_PIXEL) wrow += m.ldw;
             }
-            // Everyone is done with this buffer; refill it with slab q + nstage.
-            if (__syncthreads_or(!ok)) {
-                failed = true;
-                break;
+            // This warp is done with the buffer; the last warp to finish refills it.
+            __syncwarp();
+            if (lane == 0) {
+                __threadfence_block();
+                if (atomicAdd(&done[slot], 1u) == (uint32_t)(nthr >> 5) - 1u) {
+                    done[slot] = 0u;
+                    __threadfence_block();
+                    fence_proxy_async_smem();
+                    if (q + a.nstage < total) {
+                        int sl = s + a.nstage;
+                        while (sl >= a.nslabs) sl -= a.nslabs;
+                        issue(q + a.nstage, slot, sl);
+                    }
+                }
             }
-            if (tid == 0 && q + a.nstage < total) issue(q + a.nstage);
+            if (++slot == a.nstage) {
+                slot = 0;
+                parity ^= 1u;
+            }
         }
         if (failed) break;
 #pragma unroll
@@ -290,12 +329,13 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
             }
         }
     }
-    if (failed && tid == 0) {
-        atomicOr(err, ERR_TIMEOUT);
-        // Let copies already issued (slab q and up to nstage - 1 after it) land before
-        // the CTA's shared memory goes away; each wait is bounded too.
-        for (uint64_t qq = q; qq < q + (uint64_t)a.nstage && qq < total; ++qq)
-            mbar_wait(&bars[qq % a.nstage], (uint32_t)((qq / a.nstage) & 1ull), a.wait_ns);
+    // Copies already issued must land before the CTA's shared memory goes away
+    // (after a timeout some may still be in flight); each wait is bounded.
+    __syncthreads();
+    if (tid == 0) {
+        if (*(volatile int *)abort_flag) atomicOr(err, ERR_TIMEOUT);
+        for (int s = 0; s < a.nstage; ++s)
+            if (issued[s] != ~0ull) mbar_wait(&bars[s], (uint32_t)((issued[s] / a.nstage) & 1ull), a.wait_ns);
     }
 }
 
@@ -442,7 +482,7 @@ cudaError_t launch_score_generated(const MapDev &m, const TrackSet &ts, double *
         size_t budget = smem_optin;
         if (tu.smem_kb > 0) budget = std::min(budget, (size_t)tu.smem_kb * 1024);
         const int nstage = std::max(2, std::min(tu.nstage, 4));
-        const size_t fixed = wtab_bytes + 64;
+        const size_t fixed = wtab_bytes + kStagedBookkeeping;
         long S = budget > fixed ? (long)((budget - fixed) / (nstage * (row_bytes + wrow_bytes))) : 0;
         S = std::min<long>(S, m.n_t);
         if (S < 1) {
@@ -480,7 +520,7 @@ cudaError_t launch_score_generated(const MapDev &m, const TrackSet &ts, double *
             p.nslabs = (int)((m.n_t + S - 1) / S);
             p.batch = batch;
             p.nbatches = nb;
-            p.smem = (size_t)nstage * S * (row_bytes + wrow_bytes) + wtab_bytes + (size_t)nstage * 8;
+            p.smem = (size_t)nstage * S * (row_bytes + wrow_bytes) + wtab_bytes + kStagedBookkeeping;
             StagedArgs sa;
             sa.S = (int)S;
             sa.nstage = nstage;
