@@ -97,6 +97,10 @@ STK_API int stk_set_stream(stk_ctx *ctx, void *cuda_stream);
  * Statistic selected (Eq. 7 and the footnote to Eq. 5 allowing other weights):
  *   default         SNR = sum_j Re[e^{2 pi i f_j tau} y_j sigma_j^-2] / sqrt(sum_j sigma_j^-2)
  *   STK_NORM_PAPER  SNR = (1/n_t) sum_j Re[e^{2 pi i f_j tau} y_j / sigma_j]
+ * Arithmetic: pixel magnitude and phase stored FP32 and Q0.32 turns (FP16 and
+ * Q0.16 with STK_FP16), sums FP32, normalisation FP64.  The delay phase
+ * f tau mod 1 is exact in 64-bit fixed point per template; per pixel it is a
+ * 32-bit turn, within 3e-6 rad for n_f <= 8192 (2^-32 turn beyond).
  * The library keeps its own packed copy; the caller may free y and sigma when
  * the call returns (it synchronises the stream).  Errors: STK_EINVAL (sizes,
  * NULL pointers, a non-finite y, sigma <= 0 or non-finite, f_min/df
@@ -255,7 +259,9 @@ typedef struct stk_batch stk_batch; /* opaque */
  * offsets[i] + n_tracks[i] - 1 drawn with seeds[i] (n_tracks[i] in 1 .. 2^32-1),
  * all with delays uniform in (-tau_max_s, tau_max_s).  All maps must share the
  * statistic (weighted or STK_NORM_PAPER), the storage precision and the
- * weighting pattern, and satisfy (n_t - 1)^2 (2 n_f - 1) < 2^32.
+ * weighting pattern, and satisfy (n_t - 1)^2 (2 n_f - 1) < 2^32 and n_f <= 8192
+ * (the pixel phase is then kept as a 32-bit turn per bin, exact at the centre
+ * bin and within 3e-6 rad elsewhere).
  * Errors: STK_EINVAL, STK_ENOMEM, STK_ECUDA. */
 STK_API int stk_batch_create(stk_ctx *ctx, const stk_map *const *maps, int n_maps, const uint64_t *n_tracks,
                              const uint64_t *seeds, const uint64_t *offsets, double tau_max_s, stk_batch **out);
@@ -321,7 +327,8 @@ STK_API int stk_score_noalloc(const stk_map *map, uint64_t n_tracks, uint64_t se
 /* ---- tuning (kernel choice and launch shape; results do not depend on them) */
 #define STK_OPT_KERNEL   1 /* 0 automatic, 1 one-thread-per-template kernel, 2 shared-memory slab kernel */
 #define STK_OPT_THREADS  2 /* slab kernel block size, 0 = automatic, else 32 .. 1024 */
-#define STK_OPT_MAX_R    3 /* slab kernel: most templates held per thread, 1 .. 6 (default 6; at most 5 with a varying weight) */
+#define STK_OPT_MAX_R    3 /* slab kernel: most templates held per thread, 1 .. 12 (default 6; at most 5 with a
+                              varying weight; 7 .. 12 limit the block to 512 threads) */
 #define STK_OPT_STAGES   4 /* slab kernel: shared-memory slab buffers, 2 .. 4 (default 2) */
 #define STK_OPT_SMEM_KB  5 /* slab kernel: shared-memory budget in KiB, 0 = the device maximum */
 #define STK_OPT_WAIT_MS  6 /* slab kernel: limit of each in-kernel wait for a slab copy, ms (0 = 2000) */

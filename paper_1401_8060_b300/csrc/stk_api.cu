@@ -261,7 +261,7 @@ int stk_set_option(stk_ctx *c, int option, int64_t value)
         c->tune.threads = (int)value;
         return STK_OK;
     case STK_OPT_MAX_R:
-        if (value < 1 || value > 6) return set_err(c, STK_EINVAL, "templates per thread must be in [1, 6]");
+        if (value < 1 || value > 12) return set_err(c, STK_EINVAL, "templates per thread must be in [1, 12]");
         c->tune.max_R = (int)value;
         return STK_OK;
     case STK_OPT_STAGES:

@@ -4,7 +4,7 @@
 // own template set, recording every map's loudest SNR (Sec. V, Eqs. 9-10: time
 // windows and n_ts unphysical time shifts per window).  A batch runs them all
 // in one kernel:
-//   - the work is a list of tiles (map, block of R * blockDim templates) in
+//   - the work is a list of tiles (map, block of R * blockDim positions) in
 //     schedule order, largest maps first; CTAs take tiles from a global work
 //     counter, so ragged maps balance across the GPU;
 //   - each tile streams its map through shared memory in slabs (bulk copies on
@@ -14,8 +14,10 @@
 // Before taking a tile a CTA reads a cancel flag in host-mapped memory.  The
 // launch sequence is captured once in a CUDA graph and replayed.  Every
 // template's SNR is computed with the same per-pixel arithmetic as the
-// single-map kernels (the division by 2 M^2 uses the multiply-shift with one
-// correction step, exact for all numerators below 2^32).
+// single-map kernels.  The division by 2 M^2 is the map's exact multiply-shift
+// when it has one, else a multiply-shift with one correction step (exact for all
+// numerators below 2^32).  Each map's templates are scored in coherent
+// order (a bucket sort over all maps, run inside the graph before the tiles).
 #include <algorithm>
 #include <cmath>
 #include <vector>
@@ -32,17 +34,22 @@ constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s per slab wait
 constexpr int kMaxWarps = 32;
 constexpr int kRankChunk = 64;
 constexpr int kRankTile = 1024;
+constexpr int kBatchStages = 4;            // most slab buffers
+constexpr size_t kBatchBookkeeping = 128;  // barriers, last issued slab, finished warps, abort flag
+static_assert(kBatchStages * (8 + 8 + 4) + 4 <= kBatchBookkeeping, "bookkeeping block too small");
 
 struct BatchMap {
     MapDev m;
     TrackSet ts;
-    uint32_t magic;   // ceil(2^(32+shift) / d) < 2^32, used with one correction step
+    uint32_t magic;   // exact multiply-shift (fast), else ceil(2^(32+shift) / d) with one correction
     int shift;
+    int fast;
     uint32_t d32;     // 2 M^2
     int S;            // time columns per slab
     int nslabs;
     uint32_t ntiles;  // template blocks of this map
     uint32_t tile0;   // first candidate block of this map (map-major order)
+    uint32_t pos0;    // first position of this map in the scoring order
 };
 
 struct BatchArgs {
@@ -59,32 +66,70 @@ struct BatchArgs {
     unsigned long long *cand_key;  // [all tiles][K]
     unsigned int *cand_idx;
     int *err;
+    const uint32_t *perm;   // coherent order: position pos0 + p of map i holds its template perm[.] (NULL: index order)
 };
+
+// One slab of one tile: rows time columns for the R templates of this thread.
+template <int R, int WMODE, int PREC, bool FAST>
+__device__ __forceinline__ void batch_slab(const typename Pix<PREC>::Rec *row, const float *wrow, const float *swt,
+                                           int rows, int ldr, int ldw, uint32_t magic, int shift, uint32_t d32,
+                                           uint32_t (&N)[R], uint32_t (&D)[R], const uint32_t (&D2)[R],
+                                           const uint32_t (&pa)[R], const uint32_t (&pc)[R], float (&acc)[R],
+                                           float (&W)[R])
+{
+    using Rec = typename Pix<PREC>::Rec;
+#pragma unroll 2
+    for (int jj = 0; jj < rows; ++jj) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const uint32_t bin = FAST ? __umulhi(N[r], magic) >> shift : div_corrected(N[r], magic, shift, d32);
+            const Rec v = row[bin];
+            float wv = 0.f;
+            if (WMODE == WMODE_FREQ) wv = swt[bin];
+            if (WMODE == WMODE_PIXEL) wv = wrow[bin];
+            accumulate_turn<PREC, WMODE>(v, pixel_turn_narrow(bin, pa[r], pc[r], Pix<PREC>::arg(v)), wv, acc[r],
+                                         W[r]);
+            N[r] += D[r];
+            D[r] += D2[r];
+        }
+        row += ldr;
+        if (WMODE == WMODE_PIXEL) wrow += ldw;
+    }
+}
 
 template <int R, int WMODE, int PREC>
 __global__ void __launch_bounds__(1024, 1) score_batch_kernel(BatchArgs a)
 {
     using Rec = typename Pix<PREC>::Rec;
     extern __shared__ __align__(128) unsigned char smem[];
-    unsigned char *slabs = smem;
-    float *swt = reinterpret_cast<float *>(smem + (size_t)a.nstage * a.slot_bytes);
-    uint64_t *bars = reinterpret_cast<uint64_t *>(swt + a.wtab_floats);
-    unsigned long long *ck = reinterpret_cast<unsigned long long *>(bars + a.nstage);
+    // bookkeeping first (fixed offsets), then slab buffers, weight table, tile candidates
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem);                // full barrier per buffer
+    uint64_t *issued = bars + kBatchStages;                              // last slab issued into each buffer
+    uint32_t *done = reinterpret_cast<uint32_t *>(issued + kBatchStages);  // warps finished with each buffer
+    int *abort_flag = reinterpret_cast<int *>(done + kBatchStages);
+    unsigned char *slabs = smem + kBatchBookkeeping;
+    float *swt = reinterpret_cast<float *>(slabs + (size_t)a.nstage * a.slot_bytes);
+    unsigned long long *ck = reinterpret_cast<unsigned long long *>(swt + a.wtab_floats);
     unsigned int *ci = reinterpret_cast<unsigned int *>(ck + kMaxWarps * a.K);
     __shared__ unsigned int sh_tile;
 
     const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31, warp = tid >> 5, nwarps = nthr >> 5;
     const int K = a.K;
     if (tid == 0) {
-        for (int s = 0; s < a.nstage; ++s) mbar_init(&bars[s], 1);
+        for (int s = 0; s < a.nstage; ++s) {
+            mbar_init(&bars[s], 1);
+            issued[s] = ~0ull;
+            done[s] = 0u;
+        }
+        *abort_flag = 0;
         fence_mbar_init();
     }
     __syncthreads();
 
-    uint64_t q = 0;  // slabs consumed so far: buffer q % nstage, phase q / nstage
+    uint64_t q = 0;       // slab sequence number over all tiles of this CTA
+    int slot = 0;         // q % nstage
+    uint32_t parity = 0;  // (q / nstage) & 1
     int cur_map = -1;
-    bool failed = false;
-    uint64_t q_issued_end = 0;  // one past the last slab issued
     while (true) {
         if (tid == 0) {
             unsigned int t = atomicAdd(a.counter, 1u);
@@ -103,6 +148,7 @@ __global__ void __launch_bounds__(1024, 1) score_batch_kernel(BatchArgs a)
         const int n_t = bm->m.n_t, ldr = bm->m.ldr, ldw = bm->m.ldw;
         const uint32_t magic = bm->magic, d32 = bm->d32;
         const int shift = bm->shift, S = bm->S, nslabs = bm->nslabs;
+        const bool fast = bm->fast != 0;
         if (WMODE == WMODE_FREQ && (int)tb.x != cur_map) {
             const int n_f = bm->m.n_f;
             const float *w = bm->m.w;
@@ -113,80 +159,89 @@ __global__ void __launch_bounds__(1024, 1) score_batch_kernel(BatchArgs a)
         const uint64_t t0 = (uint64_t)tb.y * a.tile;
         const uint64_t nt_map = bm->ts.n;
         const uint64_t tn = (nt_map - t0) < a.tile ? (nt_map - t0) : a.tile;
-        const uint32_t row_bytes = (uint32_t)ldr * (uint32_t)sizeof(Rec);
-        const uint32_t wrow_bytes = (uint32_t)ldw * 4u;
 
-        auto issue = [&](uint64_t qq, int slab) {
-            const int slot = (int)(qq % (uint64_t)a.nstage);
-            const int row0 = slab * S;
+        // slab sl of this tile (sequence number qq) into buffer bslot
+        auto issue = [&](uint64_t qq, int bslot, int sl) {
+            const uint32_t row_bytes = (uint32_t)ldr * (uint32_t)sizeof(Rec);
+            const uint32_t wrow_bytes = (uint32_t)ldw * 4u;
+            const int row0 = sl * S;
             const int rows = min(S, n_t - row0);
-            unsigned char *dst = slabs + (size_t)slot * a.slot_bytes;
+            unsigned char *dst = slabs + (size_t)bslot * a.slot_bytes;
             uint32_t bytes = (uint32_t)rows * row_bytes;
             if (WMODE == WMODE_PIXEL) bytes += (uint32_t)rows * wrow_bytes;
-            mbar_arrive_expect_tx(&bars[slot], bytes);
+            issued[bslot] = qq;
+            mbar_arrive_expect_tx(&bars[bslot], bytes);
             const Rec *grec = reinterpret_cast<const Rec *>(bm->m.rec);
-            bulk_g2s(dst, grec + (size_t)row0 * ldr, (uint32_t)rows * row_bytes, &bars[slot]);
+            bulk_g2s(dst, grec + (size_t)row0 * ldr, (uint32_t)rows * row_bytes, &bars[bslot]);
             if (WMODE == WMODE_PIXEL)
                 bulk_g2s(dst + (size_t)S * row_bytes, bm->m.w + (size_t)row0 * ldw, (uint32_t)rows * wrow_bytes,
-                         &bars[slot]);
+                         &bars[bslot]);
         };
-        const uint64_t qbase = q;
-        const int pre = min(a.nstage, nslabs);
-        if (tid == 0)
-            for (int s = 0; s < pre; ++s) issue(qbase + s, s);
-        q_issued_end = qbase + pre;
+        if (tid == 0) {
+            const int pre = min(a.nstage, nslabs);
+            int bs = slot;
+            for (int s = 0; s < pre; ++s) {
+                issue(q + s, bs, s);
+                if (++bs == a.nstage) bs = 0;
+            }
+        }
 
         uint32_t N[R], D[R], D2[R];
-        Phase ph[R];
+        uint32_t pa[R], pc[R];  // narrow phase form (n_f <= kPhaseNarrowNf)
         float acc[R], W[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             uint64_t i = (uint64_t)tid + (uint64_t)r * nthr;
             if (i >= tn) i = tn - 1;  // idle slot: repeat a valid template, result discarded
+            const uint64_t rel = a.perm ? (uint64_t)__ldg(a.perm + bm->pos0 + t0 + i) : t0 + i;
             uint32_t f[3];
             double tau;
-            draw_track(bm->ts.seed, bm->ts.offset + t0 + i, (uint32_t)bm->m.n_f, bm->ts.tau_max, f, tau);
+            draw_track(bm->ts.seed, bm->ts.offset + rel, (uint32_t)bm->m.n_f, bm->ts.tau_max, f, tau);
             const Raster32 rs = raster_init(f[0], f[1], f[2], (uint32_t)(n_t - 1));
             N[r] = rs.N; D[r] = rs.D; D2[r] = rs.D2;
-            ph[r] = phase_consts(bm->m.f_min, bm->m.df, tau);
+            const Phase ph = phase_consts(bm->m.f_min, bm->m.df, tau, bm->m.n_f);
+            pa[r] = ph.a;
+            pc[r] = ph.c;
             acc[r] = 0.f;
             W[r] = 0.f;
         }
 
         for (int s = 0; s < nslabs; ++s, ++q) {
-            const int slot = (int)(q % (uint64_t)a.nstage);
-            const uint32_t parity = (uint32_t)((q / (uint64_t)a.nstage) & 1ull);
-            const bool ok = mbar_wait(&bars[slot], parity, kWaitLimitNs);
+            const bool ok = __all_sync(0xffffffffu, mbar_wait(&bars[slot], parity, kWaitLimitNs)) &&
+                            !*(volatile int *)abort_flag;
+            if (!ok) {
+                if (lane == 0) atomicOr(abort_flag, 1);
+                break;
+            }
             const int rows = min(S, n_t - s * S);
+            const uint32_t row_bytes = (uint32_t)ldr * (uint32_t)sizeof(Rec);
             const Rec *row = reinterpret_cast<const Rec *>(slabs + (size_t)slot * a.slot_bytes);
             const float *wrow = reinterpret_cast<const float *>(slabs + (size_t)slot * a.slot_bytes +
                                                                 (size_t)S * row_bytes);
-#pragma unroll 2
-            for (int jj = 0; jj < rows; ++jj) {
-#pragma unroll
-                for (int r = 0; r < R; ++r) {
-                    const uint32_t bin = div_corrected(N[r], magic, shift, d32);
-                    const Rec v = row[bin];
-                    float wv = 0.f;
-                    if (WMODE == WMODE_FREQ) wv = swt[bin];
-                    if (WMODE == WMODE_PIXEL) wv = wrow[bin];
-                    accumulate<PREC, WMODE>(v, bin, ph[r], wv, acc[r], W[r]);
-                    N[r] += D[r];
-                    D[r] += D2[r];
+            if (fast)
+                batch_slab<R, WMODE, PREC, true>(row, wrow, swt, rows, ldr, ldw, magic, shift, d32, N, D, D2, pa, pc,
+                                                 acc, W);
+            else
+                batch_slab<R, WMODE, PREC, false>(row, wrow, swt, rows, ldr, ldw, magic, shift, d32, N, D, D2, pa,
+                                                  pc, acc, W);
+            // This warp is done with the buffer; the last warp to finish refills it.
+            __syncwarp();
+            if (lane == 0) {
+                __threadfence_block();
+                if (atomicAdd(&done[slot], 1u) == (uint32_t)nwarps - 1u) {
+                    done[slot] = 0u;
+                    __threadfence_block();
+                    fence_proxy_async_smem();
+                    if (s + a.nstage < nslabs) issue(q + a.nstage, slot, s + a.nstage);
                 }
-                row += ldr;
-                if (WMODE == WMODE_PIXEL) wrow += ldw;
             }
-            if (__syncthreads_or(!ok)) {
-                failed = true;
-                break;
-            }
-            if (s + a.nstage < nslabs) {
-                if (tid == 0) issue(q + a.nstage, s + a.nstage);
-                q_issued_end = q + a.nstage + 1;
+            if (++slot == a.nstage) {
+                slot = 0;
+                parity ^= 1u;
             }
         }
-        if (failed) break;
+        __syncthreads();
+        if (*(volatile int *)abort_flag) break;  // read after the barrier: the same for every thread
 
         // this tile's K loudest: repeated arg-max, per warp and then over the warps
         unsigned long long key[R];
@@ -195,8 +250,9 @@ __global__ void __launch_bounds__(1024, 1) score_batch_kernel(BatchArgs a)
         for (int r = 0; r < R; ++r) {
             const uint64_t i = (uint64_t)tid + (uint64_t)r * nthr;
             const bool valid = i < tn;
+            const uint64_t rel = valid ? (a.perm ? (uint64_t)__ldg(a.perm + bm->pos0 + t0 + i) : t0 + i) : 0ull;
             key[r] = valid ? order_key(finalize_snr<WMODE>(acc[r], W[r], bm->m)) : 0ull;
-            idx[r] = valid ? (unsigned int)(t0 + i) : 0xffffffffu;
+            idx[r] = valid ? (unsigned int)rel : 0xffffffffu;
         }
         for (int it = 0; it < K; ++it) {
             unsigned long long bk = 0ull;
@@ -254,11 +310,14 @@ __global__ void __launch_bounds__(1024, 1) score_batch_kernel(BatchArgs a)
         }
         // the next tile's fetch barrier orders the reuse of ck / ci and the slab buffers
     }
-    if (failed && tid == 0) {
-        atomicOr(a.err, ERR_TIMEOUT);
-        // let the copies this CTA issued and has not consumed land (bounded waits)
-        for (uint64_t qq = q; qq < q_issued_end; ++qq)
-            mbar_wait(&bars[qq % a.nstage], (uint32_t)((qq / a.nstage) & 1ull), kWaitLimitNs);
+    // Copies already issued must land before the CTA's shared memory goes away
+    // (after a timeout some may still be in flight); each wait is bounded.
+    __syncthreads();
+    if (tid == 0) {
+        if (*(volatile int *)abort_flag) atomicOr(a.err, ERR_TIMEOUT);
+        for (int s = 0; s < a.nstage; ++s)
+            if (issued[s] != ~0ull)
+                mbar_wait(&bars[s], (uint32_t)((issued[s] / (uint64_t)a.nstage) & 1ull), kWaitLimitNs);
     }
 }
 
@@ -319,8 +378,7 @@ __global__ void __launch_bounds__(256) batch_rank_kernel(const BatchMap *__restr
 template <int R, int WMODE, int PREC>
 cudaError_t launch_batch_R(const BatchArgs &a, int grid, int threads, size_t smem, bool set_attr, cudaStream_t st)
 {
-    auto k = score_batch_kernel<R, WMODE, PREC>;
-    if (set_attr) {
+    auto k = score_batch_kernel<R, WMODE, PREC>;    if (set_attr) {
         cudaFuncAttributes fa;
         cudaError_t e = cudaFuncGetAttributes(&fa, k);
         if (e != cudaSuccess) return e;
@@ -404,6 +462,12 @@ struct stk_batch {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
     int graph_k = 0;
+    // coherent order (one bucket sort over all maps, run in every scoring call)
+    bool use_order = false;
+    OrderMap *d_omaps = nullptr;
+    void *order_buf = nullptr;
+    uint64_t total_n = 0, total_buckets = 0, max_n = 0;
+    const uint32_t *d_perm = nullptr;
 };
 
 namespace {
@@ -426,7 +490,7 @@ int configure(stk_batch *b, int threads, int R, int nstage)
     for (auto *m : b->maps) max_nf = std::max<uint32_t>(max_nf, (uint32_t)m->dev.n_f);
     const uint32_t wtab = b->wmode == WMODE_FREQ ? (max_nf + 3) / 4 * 4 : 0;
     // room for the kernel's own static shared memory (the tile index, aligned) and slack
-    const size_t fixed = (size_t)wtab * 4 + (size_t)nstage * 8 + (size_t)kMaxWarps * STK_BATCH_MAX_K * 12 + 1024;
+    const size_t fixed = kBatchBookkeeping + (size_t)wtab * 4 + (size_t)kMaxWarps * STK_BATCH_MAX_K * 12 + 1024;
     if (c->smem_optin <= fixed) return set_err(c, STK_EINVAL, "shared memory too small for the batch");
     const uint32_t slot = (uint32_t)((c->smem_optin - fixed) / nstage / 16 * 16);
     const uint32_t tile = (uint32_t)(R * threads);
@@ -485,17 +549,25 @@ int configure(stk_batch *b, int threads, int R, int nstage)
     b->tile = tile;
     b->slot_bytes = slot;
     b->wtab_floats = wtab;
-    b->smem = (size_t)nstage * slot + (size_t)wtab * 4 + (size_t)nstage * 8 + (size_t)kMaxWarps * STK_BATCH_MAX_K * 12;
+    b->smem = kBatchBookkeeping + (size_t)nstage * slot + (size_t)wtab * 4 + (size_t)kMaxWarps * STK_BATCH_MAX_K * 12;
     b->ntiles_total = tile0;
     b->max_ntiles = max_ntiles;
     drop_graph(b);
     return STK_OK;
 }
 
-// The launch sequence: zero the work counter, run the tiles, merge per map.
-cudaError_t enqueue(stk_batch *b, int k, uint32_t ntiles, bool merge, bool set_attr, cudaStream_t st)
+// The launch sequence: the coherent order (if `order`), zero the work counter,
+// run the tiles, merge per map.
+cudaError_t enqueue(stk_batch *b, int k, uint32_t ntiles, bool merge, bool set_attr, cudaStream_t st,
+                    bool order = true)
 {
+    if (b->use_order && order) {
+        cudaError_t e = launch_order_batch(b->d_omaps, b->n_maps, b->max_n, b->total_n, b->total_buckets,
+                                           b->order_buf, b->ctx->num_sms, st, &b->d_perm, nullptr);
+        if (e != cudaSuccess) return e;
+    }
     BatchArgs a;
+    a.perm = b->use_order ? b->d_perm : nullptr;
     a.maps = b->d_maps;
     a.sched = b->d_sched;
     a.ntiles = ntiles;
@@ -524,7 +596,7 @@ int ensure_graph(stk_batch *b, int k)
     if (b->gexec && b->graph_k == k) return STK_OK;
     drop_graph(b);
     // kernel attributes are set outside the capture
-    cudaError_t e = enqueue(b, k, 0, false, true, b->cap_stream);
+    cudaError_t e = enqueue(b, k, 0, false, true, b->cap_stream, false);
     if (e != cudaSuccess) return set_err(c, STK_ECUDA, "batch warm launch: %s", cudaGetErrorString(e));
     CUDA_TRY(c, cudaStreamSynchronize(b->cap_stream));
     CUDA_TRY(c, cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
@@ -578,6 +650,11 @@ int stk_batch_create(stk_ctx *c, const stk_map *const *maps, int n_maps, const u
             delete b;
             return set_err(c, STK_EINVAL, "n_tracks[%d] must be in [1, 2^32)", i);
         }
+        if (m->dev.n_f > kPhaseNarrowNf) {
+            delete b;
+            return set_err(c, STK_EINVAL, "map %d: n_f = %d exceeds %d (batched scoring)", i, m->dev.n_f,
+                           kPhaseNarrowNf);
+        }
         const uint64_t M = m->dev.M;
         if ((unsigned __int128)M * M * (2 * (uint64_t)m->dev.n_f - 1) >= ((unsigned __int128)1 << 32)) {
             delete b;
@@ -587,7 +664,25 @@ int stk_batch_create(stk_ctx *c, const stk_map *const *maps, int n_maps, const u
         x.m = m->dev;
         x.ts = TrackSet{n_tracks[i], seeds[i], offsets[i], tau_max_s};
         x.d32 = (uint32_t)m->dev.d;
-        corrected_magic(m->dev.d, x.magic, x.shift);
+        x.pos0 = (uint32_t)b->total_n;
+        b->total_n += n_tracks[i];
+        b->max_n = std::max<uint64_t>(b->max_n, n_tracks[i]);
+        if (b->total_n > 0xffffffffull) {
+            delete b;
+            return set_err(c, STK_EINVAL, "the batch's templates must number below 2^32 in all");
+        }
+    }
+    // the division by 2 M^2: a map's exact multiply-shift when it has one, else the
+    // corrected form
+    for (int i = 0; i < n_maps; ++i) {
+        BatchMap &x = b->hmaps[i];
+        x.fast = maps[i]->dev.fast32 ? 1 : 0;
+        if (x.fast) {
+            x.magic = maps[i]->dev.magic;
+            x.shift = maps[i]->dev.shift;
+        } else {
+            corrected_magic(maps[i]->dev.d, x.magic, x.shift);
+        }
     }
     cudaError_t e;
     if ((e = cudaMalloc(&b->d_counter, sizeof(unsigned int))) != cudaSuccess ||
@@ -599,6 +694,30 @@ int stk_batch_create(stk_ctx *c, const stk_map *const *maps, int n_maps, const u
         return set_err(c, STK_ENOMEM, "batch allocation: %s", cudaGetErrorString(e));
     }
     *b->h_cancel = 0;
+    if (c->tune.order) {
+        // buckets: at most 2^26 over all maps, so the key keeps fewer bits per map in large batches
+        int max_bits = 7;
+        while (max_bits > 1 && ((uint64_t)n_maps << (3 * max_bits)) > (1ull << 26)) --max_bits;
+        std::vector<OrderMap> om(n_maps);
+        for (int i = 0; i < n_maps; ++i) {
+            int bits;
+            om[i].ts = b->hmaps[i].ts;
+            om[i].n_f = (uint32_t)b->hmaps[i].m.n_f;
+            order_shape(b->hmaps[i].m.n_f, max_bits, om[i].shift, bits);
+            om[i].bucket0 = (uint32_t)b->total_buckets;
+            om[i].pos0 = b->hmaps[i].pos0;
+            b->total_buckets += 1ull << (3 * bits);
+        }
+        const size_t bytes = order_scratch_bytes_total(b->total_n, b->total_buckets);
+        if ((e = cudaMalloc(&b->d_omaps, sizeof(OrderMap) * n_maps)) != cudaSuccess ||
+            (e = cudaMalloc(&b->order_buf, bytes)) != cudaSuccess ||
+            (e = cudaMemcpy(b->d_omaps, om.data(), sizeof(OrderMap) * n_maps, cudaMemcpyHostToDevice)) !=
+                cudaSuccess) {
+            stk_batch_destroy(b);
+            return set_err(c, STK_ENOMEM, "batch order scratch (%zu bytes): %s", bytes, cudaGetErrorString(e));
+        }
+        b->use_order = true;
+    }
     int rc = configure(b, 1024, 5, 2);
     if (rc) {
         stk_batch_destroy(b);
@@ -620,6 +739,8 @@ void stk_batch_destroy(stk_batch *b)
     cudaFree(b->d_ckey);
     cudaFree(b->d_cidx);
     cudaFree(b->d_hits);
+    cudaFree(b->d_omaps);
+    cudaFree(b->order_buf);
     if (b->h_cancel) cudaFreeHost(b->h_cancel);
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
     delete b;
@@ -685,9 +806,9 @@ int stk_batch_tune(stk_batch *b, int k, int64_t out[4])
             const uint64_t t0 = (uint64_t)sp.y * b->tile;
             px += (double)std::min<uint64_t>(b->tile, x.ts.n - t0) * x.m.n_t;
         }
-        if (e == cudaSuccess) e = enqueue(b, k, nt, false, true, c->stream);  // warm-up
+        if (e == cudaSuccess) e = enqueue(b, k, nt, false, true, c->stream, ci == 0);  // warm-up (+ order once)
         if (e == cudaSuccess) e = cudaEventRecord(e0, c->stream);
-        if (e == cudaSuccess) e = enqueue(b, k, nt, false, false, c->stream);
+        if (e == cudaSuccess) e = enqueue(b, k, nt, false, false, c->stream, false);
         if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
         if (e == cudaSuccess) e = cudaEventSynchronize(e1);
         if (e != cudaSuccess) {

@@ -121,9 +121,15 @@ __host__ __device__ __forceinline__ void draw_track(uint64_t seed, uint64_t g, u
         mul64_hilo(u[k], (uint64_t)n_f, hi, lo);
         f[k] = (uint32_t)hi;
     }
-    const uint64_t v = u[3] >> 12;
-    const double unit = (double)(2 * v + 1) * 0x1p-52 - 1.0;
-    tau = tau_max * unit;
+    // tau = tau_max ((2 v + 1) 2^-52 - 1), v = u3 >> 12.  The bracket is exactly
+    // m 2^-52 with m = 2 v + 1 - 2^52 (|m| < 2^52), so tau = m (tau_max 2^-52) rounds
+    // the same real number once: one conversion and one multiply.
+    const int64_t m = (int64_t)(2 * (u[3] >> 12) + 1) - (int64_t)(1ull << 52);
+    const double scaled = tau_max * 0x1p-52;
+    if (scaled >= 0x1p-1000 || scaled == 0.0)
+        tau = (double)m * scaled;
+    else  // tau_max so small that tau_max 2^-52 would lose bits
+        tau = tau_max * ((double)m * 0x1p-52);
 }
 
 // Delay from the prior's quantile table: q = (u >> 11) 2^-53 (n_q - 1), then linear
@@ -293,13 +299,19 @@ __device__ __forceinline__ int32_t gen_pixel(const GenCurve &c, const GenFilter 
 }
 
 // ---------------------------------------------------------------- phase in turns
-// theta_j / 2 pi = (f_min + bin_j df) tau = b + bin_j a  (mod 1), with
-// a = frac(df tau) kept as unsigned Q0.64 (a_hi:a_lo) and b = frac(f_min tau)
-// as Q0.32.  Per pixel, turn = umulhi(bin, a_lo) + bin a_hi + b + arg (mod 2^32)
-// is the angle to 2^-32 turns for bins below 2^32.  b carries +2^8 so that the
-// 23-bit float built from turn >> 9 is rounded to nearest rather than truncated.
+// theta_j / 2 pi = (f_min + bin_j df) tau = B + bin_j A  (mod 1), with A =
+// frac(df tau) and B = frac(f_min tau) exact 64-bit fractions (Q0.64).  A pixel
+// needs its turn as Q0.32.  Two forms, both turn = bin a + hi32(bin a_lo) + c + arg
+// (mod 2^32):
+//   narrow maps (n_f <= kPhaseNarrowNf): a = A rounded to 32 bits, a_lo = 0 and c
+//     chosen so the turn is exact at the centre bin n_f / 2; the error is at most
+//     |bin - n_f/2| 2^-33 + 2^-33 turn (<= 4.8e-7 turn = 3.0e-6 rad at n_f = 8192);
+//   wider maps: a:a_lo = A (64 bits), c = B rounded; error below 2^-32 turn.
+// The slab and batched kernels take the narrow form without the hi32 term.
+constexpr int kPhaseNarrowNf = 8192;
+
 struct Phase {
-    uint32_t a_lo, a_hi, b;
+    uint32_t a, c, a_lo;
 };
 
 // frac(x * y) * 2^64 (unsigned, value - floor(value)), from the exact product of
@@ -334,14 +346,22 @@ __host__ __device__ __forceinline__ uint64_t frac_prod_q64(double x, double y)
     return q;
 }
 
-__host__ __device__ __forceinline__ Phase phase_consts(double f_min, double df, double tau)
+__host__ __device__ __forceinline__ Phase phase_consts(double f_min, double df, double tau, int n_f)
 {
     Phase p;
-    const uint64_t a = frac_prod_q64(df, tau);
-    const uint64_t b = frac_prod_q64(f_min, tau);
-    p.a_lo = (uint32_t)a;
-    p.a_hi = (uint32_t)(a >> 32);
-    p.b = (uint32_t)((b + 0x80000000ull) >> 32);
+    const uint64_t A = frac_prod_q64(df, tau);
+    const uint64_t B = frac_prod_q64(f_min, tau);
+    if (n_f <= kPhaseNarrowNf) {
+        const uint32_t bc = (uint32_t)(n_f / 2);
+        p.a = (uint32_t)((A + 0x80000000ull) >> 32);                       // mod 2^32: A near 1 wraps to 0
+        const uint32_t t_c = (uint32_t)(((uint64_t)bc * A + B + 0x80000000ull) >> 32);  // exact turn at bc
+        p.c = t_c - bc * p.a;
+        p.a_lo = 0u;
+    } else {
+        p.a = (uint32_t)(A >> 32);
+        p.a_lo = (uint32_t)A;
+        p.c = (uint32_t)((B + 0x80000000ull) >> 32);
+    }
     return p;
 }
 
@@ -355,7 +375,13 @@ __device__ __forceinline__ float cos_turn(uint32_t t)
 
 __device__ __forceinline__ uint32_t pixel_turn(uint32_t bin, const Phase &p, uint32_t arg)
 {
-    return __umulhi(bin, p.a_lo) + bin * p.a_hi + p.b + arg;
+    return bin * p.a + __umulhi(bin, p.a_lo) + p.c + arg;
+}
+
+// The narrow form (a_lo = 0): slab and batched kernels, n_f <= kPhaseNarrowNf.
+__device__ __forceinline__ uint32_t pixel_turn_narrow(uint32_t bin, uint32_t a, uint32_t c, uint32_t arg)
+{
+    return bin * a + c + arg;
 }
 
 // ---------------------------------------------------------------- rasteriser state
@@ -490,10 +516,27 @@ cudaError_t launch_score_generated(const MapDev &m, const TrackSet &ts, double *
                                    void *order_scratch = nullptr, cudaEvent_t order_done = nullptr);
 // Whether launch_score_generated would use order scratch for this call.
 bool score_wants_order(const MapDev &m, const TrackSet &ts, const Tuning &tu);
+
+// Coherent-order pre-pass (stk_order.cu).  One map: buckets of 7-bit control
+// bins; *perm_out = the scoring order inside scratch (perm[p] = template index
+// relative to the range's offset).
 size_t order_scratch_bytes(uint64_t n, int n_f);
-// Coherent-order pre-pass (stk_order.cu): *perm_out = the scoring order inside scratch.
 cudaError_t launch_order(const MapDev &m, const TrackSet &ts, void *scratch, int num_sms, cudaStream_t st,
                          const uint32_t **perm_out, int *launches);
+// Many maps: map i's templates take buckets bucket0 .. bucket0 + 2^(3 bits) - 1
+// and positions pos0 .. pos0 + n - 1 of perm (values relative to its offset).
+struct OrderMap {
+    TrackSet ts;
+    uint32_t n_f;
+    int shift;         // control bins >> shift (bits bits each) form the key
+    uint32_t bucket0;
+    uint32_t pos0;
+};
+void order_shape(int n_f, int max_bits, int &shift, int &bits);
+size_t order_scratch_bytes_total(uint64_t total_n, uint64_t total_buckets);
+cudaError_t launch_order_batch(const OrderMap *d_maps, int n_maps, uint64_t max_n, uint64_t total_n,
+                               uint64_t total_buckets, void *scratch, int num_sms, cudaStream_t st,
+                               const uint32_t **perm_out, int *launches);
 // Explicit templates f3[n][3], tau[n].
 cudaError_t launch_score_explicit(const MapDev &m, const uint32_t *f3, const double *tau, uint64_t n, double *out,
                                   int *err, cudaStream_t st);

@@ -13,13 +13,18 @@
 // banks.
 //
 // The order is a bucket sort of the template indices by a Morton (Z-order) key
-// of the three control bins, each reduced to its 7 leading bits:
-//   keys:    key[i] of template offset + i, histogram of the keys (atomics)
+// of the three control bins, each reduced to its leading bits (7 for one map;
+// fewer per map in a batch, where map i owns its own range of buckets and of
+// positions):
+//   keys:    bucket of each template, histogram of the buckets (atomics)
 //   tiles:   per tile of 4096 buckets, the number of templates
+//   bases:   exclusive prefix of the tile counts (one block)
 //   scan:    exclusive prefix over buckets (tile base + in-tile scan)
-//   scatter: perm[pos] = i, pos taken from the bucket's running offset
+//   scatter: perm[pos] = i (index within its map), pos from the bucket's offset
 // Within a bucket the order is whatever the atomics give; no result depends on
 // it (each template's sums run over its own columns in column order).
+#include <algorithm>
+
 #include "stk_internal.cuh"
 
 namespace stk {
@@ -28,6 +33,17 @@ namespace {
 
 constexpr int kTile = 4096;        // buckets per scan tile
 constexpr int kScanThreads = 256;  // 16 buckets per thread
+constexpr int kBaseThreads = 1024; // one block scans the tile counts
+
+struct OrderArgs {
+    const OrderMap *maps;  // device array (grid.y = map), or NULL: `single`
+    OrderMap single;
+};
+
+__device__ __forceinline__ const OrderMap &order_map(const OrderArgs &a)
+{
+    return a.maps ? a.maps[blockIdx.y] : a.single;
+}
 
 // bits 0..9 of x spread to bits 0, 3, 6, ..., 27 (Morton interleave)
 __device__ __forceinline__ uint32_t spread3(uint32_t x)
@@ -40,17 +56,20 @@ __device__ __forceinline__ uint32_t spread3(uint32_t x)
     return x;
 }
 
-__global__ void order_keys_kernel(TrackSet ts, uint32_t n_f, int shift, uint32_t *__restrict__ keys,
-                                  uint32_t *__restrict__ hist)
+__global__ void order_keys_kernel(OrderArgs a, uint32_t *__restrict__ keys, uint32_t *__restrict__ hist)
 {
+    const OrderMap &om = order_map(a);
+    const TrackSet ts = om.ts;
+    const uint32_t n_f = om.n_f, bucket0 = om.bucket0, pos0 = om.pos0;
+    const int shift = om.shift;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < ts.n; i += stride) {
         uint32_t f[3];
         double tau;
         draw_track_ts(ts, ts.offset + i, n_f, f, tau);
-        const uint32_t key =
-            spread3(f[0] >> shift) | (spread3(f[1] >> shift) << 1) | (spread3(f[2] >> shift) << 2);
-        keys[i] = key;
+        const uint32_t key = bucket0 + (spread3(f[0] >> shift) | (spread3(f[1] >> shift) << 1) |
+                                        (spread3(f[2] >> shift) << 2));
+        keys[pos0 + i] = key;
         atomicAdd(&hist[key], 1u);
     }
 }
@@ -67,6 +86,22 @@ __device__ __forceinline__ uint32_t block_sum(uint32_t v, uint32_t *red)
     return t;
 }
 
+// Exclusive scan of each thread's `run` over the block (warp scans, then warp bases).
+__device__ __forceinline__ uint32_t block_exclusive(uint32_t run, uint32_t *wsum)
+{
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    uint32_t inc = run;
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (l >= o) inc += y;
+    }
+    if (l == 31) wsum[w] = inc;
+    __syncthreads();
+    uint32_t wb = 0;
+    for (int k = 0; k < w; ++k) wb += wsum[k];
+    return wb + inc - run;
+}
+
 __global__ void __launch_bounds__(kScanThreads) order_tiles_kernel(const uint32_t *__restrict__ hist, uint32_t nb,
                                                                    uint32_t *__restrict__ tilesum)
 {
@@ -78,16 +113,27 @@ __global__ void __launch_bounds__(kScanThreads) order_tiles_kernel(const uint32_
     if (threadIdx.x == 0) tilesum[blockIdx.x] = t;
 }
 
+// tilesum[] (counts) becomes the exclusive prefix over tiles; one block.
+__global__ void __launch_bounds__(kBaseThreads) order_bases_kernel(uint32_t *__restrict__ tilesum, uint32_t ntiles)
+{
+    __shared__ uint32_t wsum[kBaseThreads / 32];
+    const uint32_t per = (ntiles + kBaseThreads - 1) / kBaseThreads;
+    const uint32_t b0 = threadIdx.x * per;
+    uint32_t run = 0;
+    for (uint32_t q = 0; q < per && b0 + q < ntiles; ++q) run += tilesum[b0 + q];
+    uint32_t acc = block_exclusive(run, wsum);
+    for (uint32_t q = 0; q < per && b0 + q < ntiles; ++q) {
+        const uint32_t c = tilesum[b0 + q];
+        tilesum[b0 + q] = acc;
+        acc += c;
+    }
+}
+
 // hist[] (counts) becomes the exclusive prefix over all buckets.
 __global__ void __launch_bounds__(kScanThreads) order_scan_kernel(uint32_t *__restrict__ hist, uint32_t nb,
-                                                                  const uint32_t *__restrict__ tilesum)
+                                                                  const uint32_t *__restrict__ tilebase)
 {
-    __shared__ uint32_t red[kScanThreads / 32];
     __shared__ uint32_t wsum[kScanThreads / 32];
-    uint32_t pre = 0;
-    for (uint32_t k = threadIdx.x; k < blockIdx.x; k += kScanThreads) pre += tilesum[k];
-    const uint32_t base = block_sum(pre, red);
-
     constexpr int per = kTile / kScanThreads;
     const uint32_t b0 = blockIdx.x * kTile + threadIdx.x * per;
     uint32_t c[per], run = 0;
@@ -96,18 +142,7 @@ __global__ void __launch_bounds__(kScanThreads) order_scan_kernel(uint32_t *__re
         c[q] = (b0 + q < nb) ? hist[b0 + q] : 0u;
         run += c[q];
     }
-    // exclusive scan of the threads' totals: warp inclusive scan, then warp bases
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    uint32_t inc = run;
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
-        if (l >= o) inc += y;
-    }
-    if (l == 31) wsum[w] = inc;
-    __syncthreads();
-    uint32_t wb = 0;
-    for (int k = 0; k < w; ++k) wb += wsum[k];
-    uint32_t acc = base + wb + inc - run;
+    uint32_t acc = tilebase[blockIdx.x] + block_exclusive(run, wsum);
 #pragma unroll
     for (int q = 0; q < per; ++q) {
         if (b0 + q < nb) hist[b0 + q] = acc;
@@ -115,12 +150,15 @@ __global__ void __launch_bounds__(kScanThreads) order_scan_kernel(uint32_t *__re
     }
 }
 
-__global__ void order_scatter_kernel(const uint32_t *__restrict__ keys, uint64_t n, uint32_t *__restrict__ offs,
+__global__ void order_scatter_kernel(OrderArgs a, const uint32_t *__restrict__ keys, uint32_t *__restrict__ offs,
                                      uint32_t *__restrict__ perm)
 {
+    const OrderMap &om = order_map(a);
+    const uint64_t n = om.ts.n;
+    const uint32_t pos0 = om.pos0;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        const uint32_t pos = atomicAdd(&offs[keys[i]], 1u);
+        const uint32_t pos = atomicAdd(&offs[keys[pos0 + i]], 1u);
         perm[pos] = (uint32_t)i;
     }
 }
@@ -135,49 +173,74 @@ int bit_length(uint32_t x)
     return b;
 }
 
-void order_shape(int n_f, int &shift, uint32_t &nb)
+cudaError_t run_order(const OrderArgs &oa, int n_maps, uint64_t max_n, uint64_t total_n, uint64_t nb,
+                      void *scratch, int num_sms, cudaStream_t st, const uint32_t **perm_out, int *launches)
 {
-    const int bits = bit_length((uint32_t)(n_f > 1 ? n_f - 1 : 0));
-    const int keep = bits < 7 ? bits : 7;
-    shift = bits - keep;
-    nb = 1u << (3 * keep);
+    const uint32_t ntiles = (uint32_t)((nb + kTile - 1) / kTile);
+    uint32_t *keys = reinterpret_cast<uint32_t *>(scratch);
+    uint32_t *perm = keys + total_n;
+    uint32_t *hist = perm + total_n;
+    uint32_t *tilesum = hist + nb;
+    cudaError_t e = cudaMemsetAsync(hist, 0, (size_t)nb * sizeof(uint32_t), st);
+    if (e != cudaSuccess) return e;
+    const int threads = 256;
+    // about 8 blocks per SM over all maps
+    const uint64_t want = std::max<uint64_t>(1, std::min<uint64_t>((max_n + threads - 1) / threads,
+                                                                    (uint64_t)num_sms * 8 / (uint64_t)n_maps + 1));
+    const dim3 grid((unsigned)want, (unsigned)n_maps);
+    order_keys_kernel<<<grid, threads, 0, st>>>(oa, keys, hist);
+    order_tiles_kernel<<<ntiles, kScanThreads, 0, st>>>(hist, (uint32_t)nb, tilesum);
+    order_bases_kernel<<<1, kBaseThreads, 0, st>>>(tilesum, ntiles);
+    order_scan_kernel<<<ntiles, kScanThreads, 0, st>>>(hist, (uint32_t)nb, tilesum);
+    order_scatter_kernel<<<grid, threads, 0, st>>>(oa, keys, hist, perm);
+    *perm_out = perm;
+    if (launches) *launches = 6;
+    return cudaGetLastError();
 }
 
 }  // namespace
 
+void order_shape(int n_f, int max_bits, int &shift, int &bits)
+{
+    const int b = bit_length((uint32_t)(n_f > 1 ? n_f - 1 : 0));
+    bits = b < max_bits ? b : max_bits;
+    shift = b - bits;
+}
+
+size_t order_scratch_bytes_total(uint64_t total_n, uint64_t total_buckets)
+{
+    const uint64_t ntiles = (total_buckets + kTile - 1) / kTile;
+    return (size_t)(2 * total_n + total_buckets + ntiles) * sizeof(uint32_t) + 256;
+}
+
 size_t order_scratch_bytes(uint64_t n, int n_f)
 {
-    int shift;
-    uint32_t nb;
-    order_shape(n_f, shift, nb);
-    const uint64_t ntiles = (nb + kTile - 1) / kTile;
-    return (size_t)(2 * n + nb + ntiles) * sizeof(uint32_t) + 256;
+    int shift, bits;
+    order_shape(n_f, 7, shift, bits);
+    return order_scratch_bytes_total(n, 1ull << (3 * bits));
 }
 
 cudaError_t launch_order(const MapDev &m, const TrackSet &ts, void *scratch, int num_sms, cudaStream_t st,
                          const uint32_t **perm_out, int *launches)
 {
-    int shift;
-    uint32_t nb;
-    order_shape(m.n_f, shift, nb);
-    const uint32_t ntiles = (nb + kTile - 1) / kTile;
-    const uint64_t n = ts.n;
-    uint32_t *keys = reinterpret_cast<uint32_t *>(scratch);
-    uint32_t *perm = keys + n;
-    uint32_t *hist = perm + n;
-    uint32_t *tilesum = hist + nb;
-    cudaError_t e = cudaMemsetAsync(hist, 0, (size_t)nb * sizeof(uint32_t), st);
-    if (e != cudaSuccess) return e;
-    const int threads = 256;
-    const uint64_t want = (n + threads - 1) / threads;
-    const int grid = (int)std::min<uint64_t>(want, (uint64_t)num_sms * 8);
-    order_keys_kernel<<<grid, threads, 0, st>>>(ts, (uint32_t)m.n_f, shift, keys, hist);
-    order_tiles_kernel<<<ntiles, kScanThreads, 0, st>>>(hist, nb, tilesum);
-    order_scan_kernel<<<ntiles, kScanThreads, 0, st>>>(hist, nb, tilesum);
-    order_scatter_kernel<<<grid, threads, 0, st>>>(keys, n, hist, perm);
-    *perm_out = perm;
-    if (launches) *launches = 5;
-    return cudaGetLastError();
+    OrderArgs oa{};
+    oa.maps = nullptr;
+    oa.single.ts = ts;
+    oa.single.n_f = (uint32_t)m.n_f;
+    int bits;
+    order_shape(m.n_f, 7, oa.single.shift, bits);
+    oa.single.bucket0 = 0;
+    oa.single.pos0 = 0;
+    return run_order(oa, 1, ts.n, ts.n, 1ull << (3 * bits), scratch, num_sms, st, perm_out, launches);
+}
+
+cudaError_t launch_order_batch(const OrderMap *d_maps, int n_maps, uint64_t max_n, uint64_t total_n,
+                               uint64_t total_buckets, void *scratch, int num_sms, cudaStream_t st,
+                               const uint32_t **perm_out, int *launches)
+{
+    OrderArgs oa{};
+    oa.maps = d_maps;
+    return run_order(oa, n_maps, max_n, total_n, total_buckets, scratch, num_sms, st, perm_out, launches);
 }
 
 }  // namespace stk

@@ -39,14 +39,21 @@ struct Pix<PREC_FP16> {  // low half: FP16 |y|/sigma; high half: arg in Q0.16 tu
 // FP32 records carry |z| and wv = sigma^-2; FP16 records carry |y|/sigma and
 // wv = 1/sigma, so |z| = mag wv and the weight is wv^2.
 template <int PREC, int WMODE>
-__device__ __forceinline__ void accumulate(typename Pix<PREC>::Rec v, uint32_t bin, const Phase &ph, float wv,
-                                           float &acc, float &W)
+__device__ __forceinline__ void accumulate_turn(typename Pix<PREC>::Rec v, uint32_t turn, float wv, float &acc,
+                                                float &W)
 {
-    const float c = cos_turn(pixel_turn(bin, ph, Pix<PREC>::arg(v)));
+    const float c = cos_turn(turn);
     float mg = Pix<PREC>::mag(v);
     if (PREC == PREC_FP16 && WMODE != WMODE_CONST) mg *= wv;
     acc = fmaf(mg, c, acc);
     if (WMODE != WMODE_CONST) W = (PREC == PREC_FP16) ? fmaf(wv, wv, W) : W + wv;
+}
+
+template <int PREC, int WMODE>
+__device__ __forceinline__ void accumulate(typename Pix<PREC>::Rec v, uint32_t bin, const Phase &ph, float wv,
+                                           float &acc, float &W)
+{
+    accumulate_turn<PREC, WMODE>(v, pixel_turn(bin, ph, Pix<PREC>::arg(v)), wv, acc, W);
 }
 
 // Normalisation (Eq. 7 with the weighting of the footnote to Eq. 5), FP64 on the

@@ -52,7 +52,7 @@ __global__ void __launch_bounds__(256) score_simple_kernel(MapDev m, TrackSet ts
     } else {
         draw_track_ts(ts, ts.offset + i, (uint32_t)m.n_f, f, tau);
     }
-    const Phase ph = phase_consts(m.f_min, m.df, tau);
+    const Phase ph = phase_consts(m.f_min, m.df, tau, m.n_f);
     float acc = 0.f, W = 0.f;
     Raster32 r;
     if (FAST32) r = raster_init(f[0], f[1], f[2], m.M);
@@ -119,7 +119,7 @@ __global__ void __launch_bounds__(256) score_general_kernel(MapDev m, TrackSet t
         draw_track_ts(ts, ts.offset + i, (uint32_t)m.n_f, f, tau);
         draw_times(ts.seed, ts.offset + i, (uint32_t)m.n_t, (uint32_t)ts.t_min, t);
     }
-    const Phase ph = phase_consts(m.f_min, m.df, tau);
+    const Phase ph = phase_consts(m.f_min, m.df, tau, m.n_f);
     const GenCurve c = gen_curve(t, f);
     const GenFilter gf = gen_filter(c);
     float acc = 0.f, W = 0.f;
@@ -184,8 +184,12 @@ struct StagedArgs {
 // waits only for the slab it needs next and warps may drift by up to nstage - 1
 // slabs.  Every wait is bounded; a warp that gives up raises a shared flag and
 // the others stop at their next slab.
+// Up to 6 templates per thread fit 64 registers (1024 threads); 7 to 12 need up
+// to 128 (512 threads).
+constexpr int staged_max_threads(int R) { return R <= 6 ? kMaxThreads : 512; }
+
 template <int R, int WMODE, int PREC>
-__global__ void __launch_bounds__(kMaxThreads, 1)
+__global__ void __launch_bounds__(staged_max_threads(R), 1)
     score_staged_kernel(MapDev m, TrackSet ts, StagedArgs a, double *__restrict__ out, int *err)
 {
     using Rec = typename Pix<PREC>::Rec;
@@ -255,7 +259,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
         const uint64_t tn = (ts.n - t0) < a.batch ? (ts.n - t0) : a.batch;
 
         uint32_t N[R], D[R], D2[R];
-        Phase ph[R];
+        uint32_t pa[R], pc[R];  // narrow phase form (n_f <= kPhaseNarrowNf)
         float acc[R], W[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) {
@@ -267,7 +271,9 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
             draw_track_ts(ts, ts.offset + rel, (uint32_t)m.n_f, f, tau);
             const Raster32 rs = raster_init(f[0], f[1], f[2], m.M);
             N[r] = rs.N; D[r] = rs.D; D2[r] = rs.D2;
-            ph[r] = phase_consts(m.f_min, m.df, tau);
+            const Phase ph = phase_consts(m.f_min, m.df, tau, m.n_f);
+            pa[r] = ph.a;
+            pc[r] = ph.c;
             acc[r] = 0.f;
             W[r] = 0.f;
         }
@@ -292,7 +298,8 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
                     float wv = 0.f;
                     if (WMODE == WMODE_FREQ) wv = swt[bin];
                     if (WMODE == WMODE_PIXEL) wv = wrow[bin];
-                    accumulate<PREC, WMODE>(v, bin, ph[r], wv, acc[r], W[r]);
+                    accumulate_turn<PREC, WMODE>(v, pixel_turn_narrow(bin, pa[r], pc[r], Pix<PREC>::arg(v)), wv,
+                                                 acc[r], W[r]);
                     N[r] += D[r];
                     D[r] += D2[r];
                 }
@@ -364,6 +371,12 @@ cudaError_t launch_staged_W(int R, const MapDev &m, const TrackSet &ts, const St
         if (WMODE == WMODE_CONST)
             return launch_staged_R<6, WMODE_CONST, PREC>(m, ts, sa, grid, threads, smem, out, err, st);
         return cudaErrorInvalidValue;
+    case 7: return launch_staged_R<7, WMODE, PREC>(m, ts, sa, grid, threads, smem, out, err, st);
+    case 8: return launch_staged_R<8, WMODE, PREC>(m, ts, sa, grid, threads, smem, out, err, st);
+    case 9: return launch_staged_R<9, WMODE, PREC>(m, ts, sa, grid, threads, smem, out, err, st);
+    case 10: return launch_staged_R<10, WMODE, PREC>(m, ts, sa, grid, threads, smem, out, err, st);
+    case 11: return launch_staged_R<11, WMODE, PREC>(m, ts, sa, grid, threads, smem, out, err, st);
+    case 12: return launch_staged_R<12, WMODE, PREC>(m, ts, sa, grid, threads, smem, out, err, st);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -452,7 +465,7 @@ __global__ void track_params_kernel(MapDev m, TrackSet ts, uint64_t g, uint32_t 
 
 bool score_wants_order(const MapDev &m, const TrackSet &ts, const Tuning &tu)
 {
-    if (!tu.order || ts.general || !m.fast32 || tu.kernel == 1) return false;
+    if (!tu.order || ts.general || !m.fast32 || tu.kernel == 1 || m.n_f > kPhaseNarrowNf) return false;
     return tu.kernel == 2 || ts.n * (uint64_t)m.n_t >= (1ull << 24);
 }
 
@@ -473,7 +486,7 @@ cudaError_t launch_score_generated(const MapDev &m, const TrackSet &ts, double *
     const uint64_t work = n * (uint64_t)m.n_t;
     int kernel = tu.kernel;
     if (kernel == 0) kernel = (!m.fast32 || work < (1ull << 24)) ? 1 : 2;
-    if (kernel == 2 && !m.fast32) kernel = 1;
+    if (kernel == 2 && (!m.fast32 || m.n_f > kPhaseNarrowNf)) kernel = 1;  // slab kernel: narrow phase form
 
     if (kernel == 2) {
         const size_t row_bytes = (size_t)m.ldr * (m.prec == PREC_FP16 ? 4 : 8);
@@ -488,9 +501,12 @@ cudaError_t launch_score_generated(const MapDev &m, const TrackSet &ts, double *
         if (S < 1) {
             kernel = 1;  // a single map row does not fit in shared memory
         } else {
-            // templates held per thread: 6 fit 64 registers without a weight sum, 5 with one
-            const int maxR = std::max(1, std::min(tu.max_R, m.wmode == WMODE_CONST ? 6 : 5));
-            const uint64_t cap = (uint64_t)maxR * kMaxThreads;
+            // templates held per thread: 6 fit 64 registers without a weight sum, 5 with
+            // one (1024 threads); 7 to 12 only when asked for, with at most 512 threads
+            const int maxR = tu.max_R > 6 ? std::min(tu.max_R, 12)
+                                          : std::max(1, std::min(tu.max_R, m.wmode == WMODE_CONST ? 6 : 5));
+            const int tmax = maxR > 6 ? 512 : kMaxThreads;
+            const uint64_t cap = (uint64_t)maxR * tmax;
             const uint64_t G = (uint64_t)std::max(1, num_sms);
             const uint64_t per_cta = (n + G - 1) / G;
             const uint64_t nb_per_cta = std::max<uint64_t>(1, (per_cta + cap - 1) / cap);
@@ -500,7 +516,7 @@ cudaError_t launch_score_generated(const MapDev &m, const TrackSet &ts, double *
             nb = (n + batch - 1) / batch;
             int R, threads;
             if (tu.threads > 0) {
-                threads = std::min(kMaxThreads, (tu.threads + 31) / 32 * 32);
+                threads = std::min(tmax, (tu.threads + 31) / 32 * 32);
                 R = (int)((batch + threads - 1) / threads);
                 if (R > maxR) {  // requested block too small for the batch: shrink the batch
                     R = maxR;
@@ -508,7 +524,7 @@ cudaError_t launch_score_generated(const MapDev &m, const TrackSet &ts, double *
                     nb = (n + batch - 1) / batch;
                 }
             } else {
-                R = (int)std::min<uint64_t>((batch + kMaxThreads - 1) / kMaxThreads, (uint64_t)maxR);
+                R = (int)std::min<uint64_t>((batch + tmax - 1) / tmax, (uint64_t)maxR);
                 threads = (int)(((batch + R - 1) / R + 31) / 32 * 32);
             }
             p.kernel = 2;

@@ -68,6 +68,48 @@ def test_batch_equals_single_map_scoring(ctx, mode, paper, fp16):
     b.close()
 
 
+def test_batch_order_on_and_off_identical(ctx):
+    """The batch scores each map's templates in coherent order by default (a
+    bucket sort over all maps inside the captured graph); a batch created with
+    index order returns the same hits bit for bit, also for many maps (fewer
+    key bits per map) and ragged template counts."""
+    maps, _, nt, sd, of = ragged(ctx, 15, 70, "freq")
+    k = 5
+    b1 = stk.Batch(ctx, maps, nt, sd, of, 0.01)
+    h1 = b1.score(k)
+    np.testing.assert_array_equal(b1.score(k), h1)
+    ctx.set_option(_lib.STK_OPT_ORDER, 0)
+    try:
+        b0 = stk.Batch(ctx, maps, nt, sd, of, 0.01)
+    finally:
+        ctx.set_option(_lib.STK_OPT_ORDER, 1)
+    np.testing.assert_array_equal(b0.score(k), h1)
+    b0.close()
+    b1.close()
+
+
+def test_batch_map_without_exact_32bit_division(ctx):
+    """An 885 x 2000 map has no exact 32-bit multiply-shift for its division by
+    2 M^2 (the single-map path then uses the one-thread-per-template kernel);
+    in a batch it takes the corrected division while the others keep theirs."""
+    maps, hosts, nt, sd, of = ragged(ctx, 16, 3, "freq")
+    sig = synth.sigma_powerlaw(40.0 + 0.5 * np.arange(2000), 1.0)
+    y = synth.noise_map(885, 2000, sig, 17)
+    maps.insert(1, ctx.load_map(torch.from_numpy(y).cuda(), torch.from_numpy(sig).cuda(), 40.0, 0.5))
+    nt.insert(1, 3000)
+    sd.insert(1, 77)
+    of.insert(1, 5)
+    k = 6
+    b = stk.Batch(ctx, maps, nt, sd, of, 0.01)
+    hits = b.score(k)
+    for i, m in enumerate(maps):
+        ctx.set_tracks(nt[i], sd[i], of[i], 0.01)
+        np.testing.assert_array_equal(hits[i], ctx.score(m, k), err_msg=f"map {i}")
+    om = oracle.OracleMap(y, sig, 40.0, 0.5, True)
+    assert_topk_matches(hits[1], om.score_range(77, 5, 3000, 0.01), 5, k, what="885 x 2000 map")
+    b.close()
+
+
 def test_batch_vs_oracle(ctx):
     maps, hosts, nt, sd, of = ragged(ctx, 6, 5, "freq")
     k = 16

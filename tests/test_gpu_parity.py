@@ -185,6 +185,41 @@ def test_coherent_order_identical(ctx, n_t, n_f, T, prior):
     assert_snr_close(res[(2, 1)][idx], o, ex, False, n_t, what="coherent order")
 
 
+@pytest.mark.parametrize("n_f", [8191, 8192, 8193, 20000])
+def test_phase_forms_at_the_narrow_limit(ctx, n_f):
+    """Up to 8192 bins the per-pixel phase is a 32-bit turn exact at the centre
+    bin; wider maps keep 64 bits (one-thread-per-template kernel).  Both stay
+    within the parity bound at the extreme bins, where the narrow form's error
+    is largest, with the largest delay."""
+    n_t = 24
+    y, sig = rand_map(24, n_t, n_f, "freq")
+    m, om = load_both(ctx, y, sig, 40.0, 0.5)
+    rng = np.random.default_rng(25)
+    ends = np.array([0, n_f - 1], dtype=np.uint32)
+    f3 = ends[rng.integers(0, 2, (400, 3))]
+    f3[:200, 1] = rng.integers(0, n_f, 200)
+    tau = rng.choice([-1.0, 1.0], 400) * (0.01 - rng.uniform(0, 1e-6, 400))
+    got = ctx.score_explicit(m, torch.from_numpy(f3.astype(np.int32)), torch.from_numpy(tau)).cpu().numpy()
+    o, ex = om.score_explicit(f3, tau, extras=True)
+    assert_snr_close(got, o, ex, False, n_t, what=f"phase n_f={n_f}")
+    ctx.set_tracks(20000, 6, 0, 0.01)
+    ctx.set_option(_lib.STK_OPT_KERNEL, 2)
+    try:
+        a = ctx.score_all(m).cpu().numpy()
+        assert ctx.last_plan()["kernel"] == (2 if n_f <= 8192 else 1)
+    finally:
+        ctx.set_option(_lib.STK_OPT_KERNEL, 0)
+    ctx.set_option(_lib.STK_OPT_KERNEL, 1)
+    try:
+        b = ctx.score_all(m).cpu().numpy()
+    finally:
+        ctx.set_option(_lib.STK_OPT_KERNEL, 0)
+    np.testing.assert_array_equal(a, b)
+    f3, tau = oracle_params(6, 0, 300, n_f, 0.01)
+    o, ex = om.score_explicit(f3, tau, extras=True)
+    assert_snr_close(a[:300], o, ex, False, n_t, what=f"generated n_f={n_f}")
+
+
 @pytest.mark.parametrize("threads,max_r,stages", [(64, 1, 2), (96, 3, 3), (1024, 4, 4), (512, 2, 2), (992, 5, 2)])
 def test_launch_shapes_agree(ctx, threads, max_r, stages):
     n_t, n_f, T = 45, 300, 30001
