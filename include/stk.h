@@ -327,8 +327,9 @@ STK_API int stk_score_noalloc(const stk_map *map, uint64_t n_tracks, uint64_t se
 /* ---- tuning (kernel choice and launch shape; results do not depend on them) */
 #define STK_OPT_KERNEL   1 /* 0 automatic, 1 one-thread-per-template kernel, 2 shared-memory slab kernel */
 #define STK_OPT_THREADS  2 /* slab kernel block size, 0 = automatic, else 32 .. 1024 */
-#define STK_OPT_MAX_R    3 /* slab kernel: most templates held per thread, 1 .. 12 (default 6; at most 5 with a
-                              varying weight; 7 .. 12 limit the block to 512 threads) */
+#define STK_OPT_MAX_R    3 /* slab kernel: most templates held per thread, 1 .. 12 (default 12); 7 .. 12 limit
+                              the block to 512 threads and a varying weight to 11, 1 .. 6 allow 1024 threads
+                              (up to 5 with a varying weight) */
 #define STK_OPT_STAGES   4 /* slab kernel: shared-memory slab buffers, 2 .. 4 (default 2) */
 #define STK_OPT_SMEM_KB  5 /* slab kernel: shared-memory budget in KiB, 0 = the device maximum */
 #define STK_OPT_WAIT_MS  6 /* slab kernel: limit of each in-kernel wait for a slab copy, ms (0 = 2000) */

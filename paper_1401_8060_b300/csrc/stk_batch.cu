@@ -81,7 +81,24 @@ __device__ __forceinline__ void batch_slab(const typename Pix<PREC>::Rec *row, c
 #pragma unroll 2
     for (int jj = 0; jj < rows; ++jj) {
 #pragma unroll
-        for (int r = 0; r < R; ++r) {
+        for (int r = 0; r + 1 < R; r += 2) {  // templates in pairs: packed FP32 arithmetic
+            const uint32_t b0 = FAST ? __umulhi(N[r], magic) >> shift : div_corrected(N[r], magic, shift, d32);
+            const uint32_t b1 =
+                FAST ? __umulhi(N[r + 1], magic) >> shift : div_corrected(N[r + 1], magic, shift, d32);
+            const Rec v0 = row[b0], v1 = row[b1];
+            float w0 = 0.f, w1 = 0.f;
+            if (WMODE == WMODE_FREQ) { w0 = swt[b0]; w1 = swt[b1]; }
+            if (WMODE == WMODE_PIXEL) { w0 = wrow[b0]; w1 = wrow[b1]; }
+            accumulate_turn2<PREC, WMODE>(v0, v1, pixel_turn_narrow(b0, pa[r], pc[r], Pix<PREC>::arg(v0)),
+                                          pixel_turn_narrow(b1, pa[r + 1], pc[r + 1], Pix<PREC>::arg(v1)), w0, w1,
+                                          acc[r], acc[r + 1], W[r], W[r + 1]);
+            N[r] += D[r];
+            D[r] += D2[r];
+            N[r + 1] += D[r + 1];
+            D[r + 1] += D2[r + 1];
+        }
+        if (R & 1) {
+            constexpr int r = R - 1;
             const uint32_t bin = FAST ? __umulhi(N[r], magic) >> shift : div_corrected(N[r], magic, shift, d32);
             const Rec v = row[bin];
             float wv = 0.f;

@@ -368,9 +368,11 @@ __host__ __device__ __forceinline__ Phase phase_consts(double f_min, double df, 
 // Angle (turns, Q0.32 read as signed, i.e. in [-1/2, 1/2)) -> cos(2 pi turn).
 // The integer-to-float conversion rounds to 24 significant bits (error at most
 // 2^-25 turn); __cosf is accurate to about 2^-21 absolute on [-pi, pi].
+constexpr float kTurnToRad = 1.46291807926715968e-9f;  // 2 pi / 2^32
+
 __device__ __forceinline__ float cos_turn(uint32_t t)
 {
-    return __cosf((float)(int32_t)t * 1.46291807926715968e-9f);  // 2 pi / 2^32
+    return __cosf((float)(int32_t)t * kTurnToRad);
 }
 
 __device__ __forceinline__ uint32_t pixel_turn(uint32_t bin, const Phase &p, uint32_t arg)
@@ -499,7 +501,7 @@ struct ScorePlan {
 struct Tuning {
     int kernel = 0;      // 0 auto
     int threads = 0;     // 0 auto
-    int max_R = 6;       // capped per weight mode by the launcher
+    int max_R = 12;      // capped per weight mode by the launcher
     int nstage = 2;
     int smem_kb = 0;     // 0 auto
     int wait_ms = 0;     // slab wait limit, 0: 2000 ms

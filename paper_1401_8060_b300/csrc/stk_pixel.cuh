@@ -49,6 +49,50 @@ __device__ __forceinline__ void accumulate_turn(typename Pix<PREC>::Rec v, uint3
     if (WMODE != WMODE_CONST) W = (PREC == PREC_FP16) ? fmaf(wv, wv, W) : W + wv;
 }
 
+// Packed pairs of FP32 operations (Blackwell .f32x2): each lane rounds to
+// nearest exactly as the scalar operation does, two results per instruction.
+__device__ __forceinline__ void fma2(float &d0, float &d1, float a0, float a1, float b0, float b1)
+{
+    asm("{ .reg .b64 ra, rb, rc; mov.b64 ra, {%2, %3}; mov.b64 rb, {%4, %5}; mov.b64 rc, {%0, %1};"
+        " fma.rn.f32x2 rc, ra, rb, rc; mov.b64 {%0, %1}, rc; }"
+        : "+f"(d0), "+f"(d1)
+        : "f"(a0), "f"(a1), "f"(b0), "f"(b1));
+}
+
+__device__ __forceinline__ void add2(float &d0, float &d1, float a0, float a1)
+{
+    asm("{ .reg .b64 ra, rc; mov.b64 ra, {%2, %3}; mov.b64 rc, {%0, %1};"
+        " add.rn.f32x2 rc, rc, ra; mov.b64 {%0, %1}, rc; }"
+        : "+f"(d0), "+f"(d1)
+        : "f"(a0), "f"(a1));
+}
+
+__device__ __forceinline__ void mul2(float &d0, float &d1, float a0, float a1)
+{
+    asm("{ .reg .b64 ra, rc; mov.b64 ra, {%2, %3}; mov.b64 rc, {%0, %1};"
+        " mul.rn.f32x2 rc, rc, ra; mov.b64 {%0, %1}, rc; }"
+        : "+f"(d0), "+f"(d1)
+        : "f"(a0), "f"(a1));
+}
+
+// accumulate_turn for two templates' pixels at once, bit for bit the same.
+template <int PREC, int WMODE>
+__device__ __forceinline__ void accumulate_turn2(typename Pix<PREC>::Rec v0, typename Pix<PREC>::Rec v1,
+                                                 uint32_t t0, uint32_t t1, float w0, float w1, float &acc0,
+                                                 float &acc1, float &W0, float &W1)
+{
+    float x0 = (float)(int32_t)t0, x1 = (float)(int32_t)t1;
+    mul2(x0, x1, kTurnToRad, kTurnToRad);
+    const float c0 = __cosf(x0), c1 = __cosf(x1);
+    float m0 = Pix<PREC>::mag(v0), m1 = Pix<PREC>::mag(v1);
+    if (PREC == PREC_FP16 && WMODE != WMODE_CONST) mul2(m0, m1, w0, w1);
+    fma2(acc0, acc1, m0, m1, c0, c1);
+    if (WMODE != WMODE_CONST) {
+        if (PREC == PREC_FP16) fma2(W0, W1, w0, w1, w0, w1);
+        else add2(W0, W1, w0, w1);
+    }
+}
+
 template <int PREC, int WMODE>
 __device__ __forceinline__ void accumulate(typename Pix<PREC>::Rec v, uint32_t bin, const Phase &ph, float wv,
                                            float &acc, float &W)

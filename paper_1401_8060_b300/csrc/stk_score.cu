@@ -184,12 +184,15 @@ struct StagedArgs {
 // waits only for the slab it needs next and warps may drift by up to nstage - 1
 // slabs.  Every wait is bounded; a warp that gives up raises a shared flag and
 // the others stop at their next slab.
-// Up to 6 templates per thread fit 64 registers (1024 threads); 7 to 12 need up
-// to 128 (512 threads).
-constexpr int staged_max_threads(int R) { return R <= 6 ? kMaxThreads : 512; }
+// Up to 5 templates per thread (6 without a weight sum) fit 64 registers (1024
+// threads); more need up to 128 (512 threads).
+constexpr int staged_max_threads(int R, int WMODE)
+{
+    return (R <= 5 || (R == 6 && WMODE == WMODE_CONST)) ? kMaxThreads : 512;
+}
 
 template <int R, int WMODE, int PREC>
-__global__ void __launch_bounds__(staged_max_threads(R), 1)
+__global__ void __launch_bounds__(staged_max_threads(R, WMODE), 1)
     score_staged_kernel(MapDev m, TrackSet ts, StagedArgs a, double *__restrict__ out, int *err)
 {
     using Rec = typename Pix<PREC>::Rec;
@@ -292,7 +295,23 @@ __global__ void __launch_bounds__(staged_max_threads(R), 1)
 #pragma unroll 2
             for (int jj = 0; jj < rows; ++jj) {
 #pragma unroll
-                for (int r = 0; r < R; ++r) {
+                for (int r = 0; r + 1 < R; r += 2) {  // templates in pairs: packed FP32 arithmetic
+                    const uint32_t b0 = __umulhi(N[r], magic) >> shift;
+                    const uint32_t b1 = __umulhi(N[r + 1], magic) >> shift;
+                    const Rec v0 = row[b0], v1 = row[b1];
+                    float w0 = 0.f, w1 = 0.f;
+                    if (WMODE == WMODE_FREQ) { w0 = swt[b0]; w1 = swt[b1]; }
+                    if (WMODE == WMODE_PIXEL) { w0 = wrow[b0]; w1 = wrow[b1]; }
+                    accumulate_turn2<PREC, WMODE>(v0, v1, pixel_turn_narrow(b0, pa[r], pc[r], Pix<PREC>::arg(v0)),
+                                                  pixel_turn_narrow(b1, pa[r + 1], pc[r + 1], Pix<PREC>::arg(v1)),
+                                                  w0, w1, acc[r], acc[r + 1], W[r], W[r + 1]);
+                    N[r] += D[r];
+                    D[r] += D2[r];
+                    N[r + 1] += D[r + 1];
+                    D[r + 1] += D2[r + 1];
+                }
+                if (R & 1) {
+                    constexpr int r = R - 1;
                     const uint32_t bin = __umulhi(N[r], magic) >> shift;
                     const Rec v = row[bin];
                     float wv = 0.f;
@@ -351,6 +370,7 @@ cudaError_t launch_staged_R(const MapDev &m, const TrackSet &ts, const StagedArg
                             size_t smem, double *out, int *err, cudaStream_t st)
 {
     auto k = score_staged_kernel<R, WMODE, PREC>;
+    if (threads > staged_max_threads(R, WMODE)) return cudaErrorInvalidConfiguration;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k<<<grid, threads, smem, st>>>(m, ts, sa, out, err);
@@ -367,16 +387,16 @@ cudaError_t launch_staged_W(int R, const MapDev &m, const TrackSet &ts, const St
     case 3: return launch_staged_R<3, WMODE, PREC>(m, ts, sa, grid, threads, smem, out, err, st);
     case 4: return launch_staged_R<4, WMODE, PREC>(m, ts, sa, grid, threads, smem, out, err, st);
     case 5: return launch_staged_R<5, WMODE, PREC>(m, ts, sa, grid, threads, smem, out, err, st);
-    case 6:
-        if (WMODE == WMODE_CONST)
-            return launch_staged_R<6, WMODE_CONST, PREC>(m, ts, sa, grid, threads, smem, out, err, st);
-        return cudaErrorInvalidValue;
+    case 6: return launch_staged_R<6, WMODE, PREC>(m, ts, sa, grid, threads, smem, out, err, st);
     case 7: return launch_staged_R<7, WMODE, PREC>(m, ts, sa, grid, threads, smem, out, err, st);
     case 8: return launch_staged_R<8, WMODE, PREC>(m, ts, sa, grid, threads, smem, out, err, st);
     case 9: return launch_staged_R<9, WMODE, PREC>(m, ts, sa, grid, threads, smem, out, err, st);
     case 10: return launch_staged_R<10, WMODE, PREC>(m, ts, sa, grid, threads, smem, out, err, st);
     case 11: return launch_staged_R<11, WMODE, PREC>(m, ts, sa, grid, threads, smem, out, err, st);
-    case 12: return launch_staged_R<12, WMODE, PREC>(m, ts, sa, grid, threads, smem, out, err, st);
+    case 12:
+        if (WMODE == WMODE_CONST)
+            return launch_staged_R<12, WMODE_CONST, PREC>(m, ts, sa, grid, threads, smem, out, err, st);
+        return cudaErrorInvalidValue;
     default: return cudaErrorInvalidValue;
     }
 }
@@ -501,9 +521,10 @@ cudaError_t launch_score_generated(const MapDev &m, const TrackSet &ts, double *
         if (S < 1) {
             kernel = 1;  // a single map row does not fit in shared memory
         } else {
-            // templates held per thread: 6 fit 64 registers without a weight sum, 5 with
-            // one (1024 threads); 7 to 12 only when asked for, with at most 512 threads
-            const int maxR = tu.max_R > 6 ? std::min(tu.max_R, 12)
+            // templates held per thread: up to 6 fit 64 registers without a weight sum,
+            // 5 with one (1024 threads); 7 to 12 (11 with a weight sum) fit 128 registers
+            // (512 threads) and run a few per cent faster, the default
+            const int maxR = tu.max_R > 6 ? std::min(tu.max_R, m.wmode == WMODE_CONST ? 12 : 11)
                                           : std::max(1, std::min(tu.max_R, m.wmode == WMODE_CONST ? 6 : 5));
             const int tmax = maxR > 6 ? 512 : kMaxThreads;
             const uint64_t cap = (uint64_t)maxR * tmax;

@@ -220,7 +220,8 @@ def test_phase_forms_at_the_narrow_limit(ctx, n_f):
     assert_snr_close(a[:300], o, ex, False, n_t, what=f"generated n_f={n_f}")
 
 
-@pytest.mark.parametrize("threads,max_r,stages", [(64, 1, 2), (96, 3, 3), (1024, 4, 4), (512, 2, 2), (992, 5, 2)])
+@pytest.mark.parametrize("threads,max_r,stages", [(64, 1, 2), (96, 3, 3), (1024, 4, 4), (512, 2, 2), (992, 5, 2),
+                                                  (512, 11, 2), (448, 12, 3), (160, 7, 4), (480, 6, 2)])
 def test_launch_shapes_agree(ctx, threads, max_r, stages):
     n_t, n_f, T = 45, 300, 30001
     y, sig = rand_map(22, n_t, n_f, "pixel")
@@ -238,7 +239,7 @@ def test_launch_shapes_agree(ctx, threads, max_r, stages):
         plan = ctx.last_plan()
         assert plan["kernel"] == 2 and plan["threads"] == threads and plan["R"] <= max_r
     finally:
-        for o, v in [(_lib.STK_OPT_KERNEL, 0), (_lib.STK_OPT_THREADS, 0), (_lib.STK_OPT_MAX_R, 6),
+        for o, v in [(_lib.STK_OPT_KERNEL, 0), (_lib.STK_OPT_THREADS, 0), (_lib.STK_OPT_MAX_R, 12),
                      (_lib.STK_OPT_STAGES, 2), (_lib.STK_OPT_SMEM_KB, 0)]:
             ctx.set_option(o, v)
     np.testing.assert_array_equal(got, ref)
