@@ -112,9 +112,17 @@ STK_API int stk_load_map(stk_ctx *ctx, const void *y_c64, const float *sigma, in
  * precision (flags must equal the map's, STK_HOST_PTR aside), packing into the
  * map's existing device buffers: nothing is allocated except, on the first
  * host-pointer update of a context, its staging buffers.  For streams of
- * same-sized maps (time windows, time shifts).  Synchronous.  Errors:
- * STK_EINVAL (as stk_load_map, or flags differing from the map's), STK_ECUDA;
- * after an error the map's contents are undefined until an update succeeds. */
+ * same-sized maps (time windows, time shifts).  A map with varying weights or
+ * STK_NORM_PAPER keeps its weighting and the call does not wait: host data is
+ * copied on the context's stream (pageable buffers before the call returns;
+ * pinned ones when the stream gets there, so leave them unchanged until the
+ * next stk_sync or STK_OUT_HOST call), and invalid data (non-finite y, sigma
+ * <= 0, FP16 overflow) is reported as STK_EINVAL by the next stk_sync or
+ * STK_OUT_HOST scoring call.  A constant-weight map is re-examined, as by
+ * stk_load_map, and the call synchronises.  Errors: STK_EINVAL (sizes, NULL
+ * pointers, flags differing from the map's; invalid data of a constant-weight
+ * map), STK_ECUDA; after an error the map's contents are undefined until an
+ * update succeeds. */
 STK_API int stk_update_map(stk_ctx *ctx, stk_map *map, const void *y_c64, const float *sigma, unsigned flags);
 
 /* Free a packed map (waits for the context's stream).  NULL is a no-op. */

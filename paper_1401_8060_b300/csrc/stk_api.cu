@@ -44,13 +44,17 @@ int flags_to_status(stk_ctx *c, int f)
     if (f & ERR_TIMEOUT) return set_err(c, STK_ETIMEOUT, "a bounded in-kernel wait for a map slab gave up");
     if (f & ERR_CANCELED) return set_err(c, STK_ECANCELED, "batch cancelled through stk_batch_cancel");
     if (f & ERR_BADTRACK) return set_err(c, STK_EINVAL, "explicit template with a control bin outside [0, n_f)");
+    if (f & ERR_BADINPUT)
+        return set_err(c, STK_EINVAL, "stk_update_map data: y non-finite or sigma <= 0 or non-finite");
+    if (f & ERR_FP16_RANGE) return set_err(c, STK_EINVAL, "stk_update_map data: |y| / sigma exceeds 65504 (FP16)");
     return STK_OK;
 }
 
 namespace {
 
 // Pack y, sigma into polar records z = |z| e^{2 pi i arg} with
-// z = y sigma^-2 (weighted) or y / sigma (paper form), and the weights.
+// z = y sigma^-2 (weighted) or y / sigma (paper form), and the weights.  FP32
+// arithmetic (|z| to about 2 ulp, the angle to about 1e-7 rad).
 __global__ void pack_kernel(const float2 *__restrict__ y, const float *__restrict__ sigma, int per_freq, int n_t,
                             int n_f, int ldr, int ldw, int paper, uint2 *__restrict__ rec, float *__restrict__ wout,
                             int *err)
@@ -70,24 +74,14 @@ __global__ void pack_kernel(const float2 *__restrict__ y, const float *__restric
         const float s = per_freq ? sigma[k] : sigma[q];
         if (!isfinite(v.x) || !isfinite(v.y) || !(s > 0.f) || !isfinite(s)) flags |= ERR_BADINPUT;
         if (s != s0) flags |= FLAG_SIGMA_VARIES;
-        const double sd = (double)s;
-        double zr, zi, w;
-        if (paper) {
-            zr = (double)v.x / sd;
-            zi = (double)v.y / sd;
-            w = 1.0;
-        } else {
-            w = 1.0 / (sd * sd);
-            zr = (double)v.x * w;
-            zi = (double)v.y * w;
-        }
-        const double mag = hypot(zr, zi);
-        const double turns = atan2(zi, zr) / 6.283185307179586476925;  // (-1/2, 1/2]
-        const long long fix = llrint(turns * 4294967296.0);
-        rec[p] = make_uint2(__float_as_uint((float)mag), (uint32_t)fix);
+        const float w = paper ? 1.f : 1.f / (s * s);
+        const float h = hypotf(v.x, v.y);
+        const float mag = paper ? h / s : h * w;
+        const float turns = atan2f(v.y, v.x) * 0.159154943091895336f;  // [-1/2, 1/2]; a positive scale keeps it
+        rec[p] = make_uint2(__float_as_uint(mag), (uint32_t)llrintf(turns * 4294967296.0f));
         if (wout) {
-            if (!per_freq) wout[(size_t)t * ldw + k] = (float)w;
-            else if (t == 0) wout[k] = (float)w;
+            if (!per_freq) wout[(size_t)t * ldw + k] = w;
+            else if (t == 0) wout[k] = w;
         }
     }
     if (flags) atomicOr(err, flags);
@@ -113,14 +107,14 @@ __global__ void pack_fp16_kernel(const float2 *__restrict__ y, const float *__re
         const float s = per_freq ? sigma[k] : sigma[q];
         if (!isfinite(v.x) || !isfinite(v.y) || !(s > 0.f) || !isfinite(s)) flags |= ERR_BADINPUT;
         if (s != s0) flags |= FLAG_SIGMA_VARIES;
-        const double h = hypot((double)v.x, (double)v.y) / (double)s;
-        if (!(h <= 65504.0)) flags |= ERR_FP16_RANGE;
-        const double turns = atan2((double)v.y, (double)v.x) / 6.283185307179586476925;  // (-1/2, 1/2]
-        const uint32_t a16 = (uint32_t)llrint(turns * 65536.0) & 0xffffu;
-        const unsigned short hb = __half_as_ushort(__double2half(h));
+        const float h = hypotf(v.x, v.y) / s;
+        if (!(h <= 65504.f)) flags |= ERR_FP16_RANGE;
+        const float turns = atan2f(v.y, v.x) * 0.159154943091895336f;  // [-1/2, 1/2]
+        const uint32_t a16 = (uint32_t)llrintf(turns * 65536.f) & 0xffffu;
+        const unsigned short hb = __half_as_ushort(__float2half_rn(h));
         rec[p] = (a16 << 16) | (uint32_t)hb;
         if (rout) {
-            const float r = (float)(1.0 / (double)s);
+            const float r = 1.f / s;
             if (!per_freq) rout[(size_t)t * ldw + k] = r;
             else if (t == 0) rout[k] = r;
         }
@@ -299,8 +293,12 @@ int stk_last_plan(const stk_ctx *c, int64_t out[9])
 }
 
 // Copy (host pointers: through the context's staging buffers) and pack y, sigma
-// into the map's buffers; set the weighting mode and normalisation.  Synchronises.
-static int pack_into(stk_ctx *c, stk_map *m, const void *y_c64, const float *sigma, unsigned flags)
+// into the map's buffers; set the weighting mode and normalisation.  Synchronises,
+// unless `deferred`: then the map keeps its weighting mode (per-pixel or
+// per-frequency weights, or the paper form, which hold for any sigma), nothing
+// waits, and invalid data is reported by the next reader of the deferred errors.
+static int pack_into(stk_ctx *c, stk_map *m, const void *y_c64, const float *sigma, unsigned flags,
+                     bool deferred = false)
 {
     MapDev &d = m->dev;
     const int n_t = d.n_t, n_f = d.n_f;
@@ -322,7 +320,7 @@ static int pack_into(stk_ctx *c, stk_map *m, const void *y_c64, const float *sig
     }
     const size_t wbytes = per_freq ? (size_t)d.ldw * 4 : (size_t)n_t * d.ldw * 4;
     CUDA_TRY(c, cudaMemsetAsync(m->w_buf, 0, wbytes, c->stream));
-    CUDA_TRY(c, cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
+    if (!deferred) CUDA_TRY(c, cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
     const uint64_t total = (uint64_t)n_t * d.ldr;
     const int blocks = (int)std::min<uint64_t>((total + 255) / 256, (uint64_t)c->num_sms * 8);
     if (fp16)
@@ -332,6 +330,7 @@ static int pack_into(stk_ctx *c, stk_map *m, const void *y_c64, const float *sig
         pack_kernel<<<blocks, 256, 0, c->stream>>>(ysrc, ssrc, per_freq ? 1 : 0, n_t, n_f, d.ldr, d.ldw, d.paper,
                                                     (uint2 *)m->rec_buf, (float *)m->w_buf, c->d_err);
     CUDA_TRY(c, cudaGetLastError());
+    if (deferred) return STK_OK;
     int fl = 0;
     int rc = read_err_flags(c, &fl);
     if (rc) return rc;
@@ -429,7 +428,9 @@ int stk_update_map(stk_ctx *c, stk_map *m, const void *y_c64, const float *sigma
     if ((flags & ~STK_HOST_PTR) != m->flags)
         return set_err(c, STK_EINVAL, "flags 0x%x do not match the map's (0x%x, host flag aside)", flags, m->flags);
     CUDA_TRY(c, cudaSetDevice(c->device));
-    return pack_into(c, m, y_c64, sigma, flags);
+    // varying weights or the paper form stay valid for any new sigma: no wait
+    const bool deferred = m->dev.paper || m->dev.wmode != WMODE_CONST;
+    return pack_into(c, m, y_c64, sigma, flags, deferred);
 }
 
 void stk_free_map(stk_map *m)
