@@ -179,11 +179,11 @@ class ClockSampler:
 
 
 def kernel_source_hash():
+    """Hash of the sources that define the slab scoring kernel."""
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_1401_8060_b300", "csrc")
-    for f in sorted(os.listdir(d)):
-        if f.endswith((".cu", ".cuh")):
-            h.update(open(os.path.join(d, f), "rb").read())
+    for f in ("stk_internal.cuh", "stk_pixel.cuh", "stk_score.cu"):
+        h.update(open(os.path.join(d, f), "rb").read())
     return h.hexdigest()[:16]
 
 
