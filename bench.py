@@ -190,13 +190,18 @@ def kernel_source_hash():
 def profiled_traffic():
     """DRAM bytes per launch of the scoring kernel from the committed ncu summary,
     or None when the kernel sources changed since it was taken."""
-    p = os.path.join(ROOT, "profiles", "score_staged_realistic.json")
+    p = os.path.join(ROOT, "profiles", "score_staged_realistic_traffic.txt")
     if not os.path.exists(p):
         return None, None
-    d = json.load(open(p))
-    if d.get("kernel_source_hash") != kernel_source_hash():
-        return None, d.get("kernel_source_hash")
-    return d.get("dram_bytes_per_launch"), d.get("kernel_source_hash")
+    kv = {}
+    for line in open(p):
+        line = line.split("#", 1)[0].strip()
+        if "=" in line:
+            k, v = (t.strip() for t in line.split("=", 1))
+            kv[k] = v
+    if kv.get("kernel_source_hash") != kernel_source_hash():
+        return None, kv.get("kernel_source_hash")
+    return int(kv["dram_bytes_per_launch"]), kv.get("kernel_source_hash")
 
 
 def cpu_baseline(fm, w, chunk, seconds=10.0):
