@@ -41,6 +41,9 @@ def lib():
         L.orc_score_range.argtypes = [C.c_void_p, C.c_uint64, C.c_uint64, C.c_uint64, C.c_double,
                                       C.c_int, dp]
         L.orc_score_range.restype = C.c_int
+        L.orc_score_range_scale.argtypes = [C.c_void_p, C.c_uint64, C.c_uint64, C.c_uint64, C.c_double,
+                                            C.c_int, dp, dp]
+        L.orc_score_range_scale.restype = C.c_int
         L.orc_interp_explicit.argtypes = [C.c_void_p, dp, dp, C.c_uint64, dp, dp]
         L.orc_track_times.argtypes = [C.c_uint64, C.c_uint64, C.c_int, C.c_int, u32p]
         L.orc_track_params_prior.argtypes = [C.c_uint64, C.c_uint64, C.c_int, dp, C.c_int, u32p, dp]
@@ -190,6 +193,19 @@ class OracleMap:
         if rc != 0:
             raise RuntimeError("oracle score_range_ext failed (%d)" % rc)
         return out
+
+    def score_range_scale(self, seed: int, offset: int, n_tracks: int, tau_max: float,
+                          nthreads: int | None = None):
+        """score_range, plus each template's comparison scale sum_j |z_j| / norm."""
+        if nthreads is None:
+            nthreads = os.cpu_count() or 1
+        out = np.zeros(n_tracks)
+        sc = np.zeros(n_tracks)
+        rc = lib().orc_score_range_scale(self._h, seed, offset, n_tracks, tau_max, int(nthreads),
+                                         _ptr(out, C.c_double), _ptr(sc, C.c_double))
+        if rc != 0:
+            raise RuntimeError("oracle score_range_scale failed (%d)" % rc)
+        return out, sc
 
     def score_range(self, seed: int, offset: int, n_tracks: int, tau_max: float,
                     nthreads: int | None = None) -> np.ndarray:

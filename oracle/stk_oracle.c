@@ -193,6 +193,7 @@ typedef struct {
     uint64_t seed, g0, n;
     double tau_max;
     double *out;
+    double *scale;   /* optional: sum_j |z_j| / norm, the scale of the comparison bound */
 } orc_job;
 
 static void *orc_range_worker(void *arg)
@@ -200,15 +201,33 @@ static void *orc_range_worker(void *arg)
     orc_job *jb = (orc_job *)arg;
     for (uint64_t i = 0; i < jb->n; ++i) {
         uint32_t f[3];
-        double tau;
+        double tau, W = 0.0, Z = 0.0;
         orc_track_params(jb->seed, jb->g0 + i, jb->m->n_f, jb->tau_max, f, &tau);
-        jb->out[i] = orc_score_track(jb->m, f, tau, NULL, NULL, NULL, NULL);
+        jb->out[i] = orc_score_track(jb->m, f, tau, NULL, &W, NULL, &Z);
+        if (jb->scale) jb->scale[i] = Z / (jb->m->paper_mode ? (double)jb->m->n_t : sqrt(W));
     }
     return NULL;
 }
 
+static int orc_range_run(const orc_map *m, uint64_t seed, uint64_t offset, uint64_t T, double tau_max,
+                         int nthreads, double *snr_out, double *scale_out);
+
 int orc_score_range(const orc_map *m, uint64_t seed, uint64_t offset, uint64_t T,
                     double tau_max, int nthreads, double *snr_out)
+{
+    return orc_range_run(m, seed, offset, T, tau_max, nthreads, snr_out, NULL);
+}
+
+/* As orc_score_range, also writing each template's comparison scale
+ * sum_j |z_j| / norm (norm = sqrt(W), or N in the paper form). */
+int orc_score_range_scale(const orc_map *m, uint64_t seed, uint64_t offset, uint64_t T,
+                          double tau_max, int nthreads, double *snr_out, double *scale_out)
+{
+    return orc_range_run(m, seed, offset, T, tau_max, nthreads, snr_out, scale_out);
+}
+
+static int orc_range_run(const orc_map *m, uint64_t seed, uint64_t offset, uint64_t T, double tau_max,
+                         int nthreads, double *snr_out, double *scale_out)
 {
     if (nthreads < 1) nthreads = 1;
     if ((uint64_t)nthreads > T) nthreads = T ? (int)T : 1;
@@ -220,6 +239,7 @@ int orc_score_range(const orc_map *m, uint64_t seed, uint64_t offset, uint64_t T
         uint64_t n = base + ((uint64_t)t < rem ? 1 : 0);
         jobs[t].m = m; jobs[t].seed = seed; jobs[t].g0 = offset + start; jobs[t].n = n;
         jobs[t].tau_max = tau_max; jobs[t].out = snr_out + start;
+        jobs[t].scale = scale_out ? scale_out + start : NULL;
         start += n;
     }
     int rc = 0, started = 0;

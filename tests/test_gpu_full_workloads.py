@@ -1,0 +1,108 @@
+"""The benchmark's workloads in full, in its launch configuration, against the
+FP64 oracle run over every template:
+
+  realistic (500 x 1600, 5e6 templates, k = 1024), FP32: every SNR within the
+    parity bound 1e-5 max(|SNR|, sum_j |z_j| / norm), the k loudest as the
+    oracle's (values relative 1e-5; indices unless the oracle's own SNRs are
+    closer than that);
+  the same map with FP16 storage: every SNR within the FP16 storage bound
+    3.5e-4 sum_j |z_j| / norm + 1e-5 |SNR| (RMS and maximum printed);
+  the 256 ragged maps of the batched workload (1e6 templates each, k = 16):
+    every map's hits equal its single-map scoring bit for bit, and a subset of
+    maps (largest, smallest, injected, a map without an exact 32-bit division)
+    matches the oracle run over all of its templates.
+"""
+import os
+
+import numpy as np
+import pytest
+
+from _parity import RTOL, assert_topk_matches
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+import oracle  # noqa: E402
+import paper_1401_8060_b300 as stk  # noqa: E402
+from paper_1401_8060_b300 import synth  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_1401_8060_b300 import build
+    build.build()
+    c = stk.Context(0)
+    yield c
+    c.close()
+
+
+@pytest.fixture(scope="module")
+def realistic():
+    """The realistic map and the oracle's SNR and comparison scale of every template."""
+    w = synth.WORKLOADS["realistic"]
+    fm = synth.realistic_map()
+    om = oracle.OracleMap.from_ftmap(fm)
+    o, sc = om.score_range_scale(w["seed"], 0, w["n_tracks"], w["tau_max"], nthreads=os.cpu_count())
+    return w, fm, o, sc
+
+
+def test_realistic_fp32_every_template(ctx, realistic):
+    w, fm, o, sc = realistic
+    m = ctx.load_map(torch.from_numpy(fm.y).cuda(), torch.from_numpy(fm.sigma).cuda(), fm.f_min, fm.df)
+    ctx.set_tracks(w["n_tracks"], w["seed"], 0, w["tau_max"])
+    hits = ctx.score(m, w["k"])
+    plan = ctx.last_plan()
+    assert plan["kernel"] == 2 and plan["order"] == 1
+    g = ctx.score_all(m).cpu().numpy()
+    err = np.abs(g - o)
+    bound = RTOL * np.maximum(np.abs(o), sc)
+    bad = np.nonzero(err > bound)[0]
+    assert bad.size == 0, f"{bad.size} templates out of bound; first {bad[:5]}"
+    print(f"realistic FP32: max |dSNR| / scale = {np.max(err / sc):.3g}, "
+          f"RMS = {np.sqrt(np.mean((err / sc) ** 2)):.3g}")
+    n_diff = assert_topk_matches(hits, o, 0, w["k"], what="realistic top-k")
+    print(f"realistic top-{w['k']}: {n_diff} indices differ from the oracle's (near-ties)")
+    m.close()
+
+
+def test_realistic_fp16_every_template(ctx, realistic):
+    w, fm, o, sc = realistic
+    m = ctx.load_map(torch.from_numpy(fm.y).cuda(), torch.from_numpy(fm.sigma).cuda(), fm.f_min, fm.df,
+                     fp16=True)
+    ctx.set_tracks(w["n_tracks"], w["seed"], 0, w["tau_max"])
+    g = ctx.score_all(m).cpu().numpy()
+    err = np.abs(g - o)
+    assert np.all(err <= 3.5e-4 * sc + 1e-5 * np.abs(o)), np.max(err / sc)
+    print(f"realistic FP16: max |dSNR| / scale = {np.max(err / sc):.3g}, "
+          f"RMS = {np.sqrt(np.mean((err / sc) ** 2)):.3g}")
+    m.close()
+
+
+def test_batched_workload(ctx):
+    bmaps = synth.batched_maps(256)
+    maps = [ctx.load_map(torch.from_numpy(f.y).cuda(), torch.from_numpy(f.sigma).cuda(), f.f_min, f.df)
+            for f in bmaps]
+    n, T, k = len(maps), 1_000_000, 16
+    seeds = [1000 + i for i in range(n)]
+    b = stk.Batch(ctx, maps, [T] * n, seeds, [0] * n, 0.01)
+    hits = b.score(k)
+    for i, m in enumerate(maps):
+        ctx.set_tracks(T, seeds[i], 0, 0.01)
+        np.testing.assert_array_equal(hits[i], ctx.score(m, k), err_msg=f"map {i}")
+    cells = [f.n_t * f.n_f for f in bmaps]
+    subset = {int(np.argmax(cells)), int(np.argmin(cells))}
+    subset |= set([i for i, f in enumerate(bmaps) if f.injections][:2])
+    # the 898 x 1777 map has no exact 32-bit multiply-shift for its division by 2 M^2
+    subset |= {i for i, f in enumerate(bmaps) if (f.n_t, f.n_f) == (898, 1777)}
+    assert len(subset) >= 5
+    for i in sorted(subset):
+        f = bmaps[i]
+        om = oracle.OracleMap.from_ftmap(f)
+        o = om.score_range(seeds[i], 0, T, 0.01, nthreads=os.cpu_count())
+        assert_topk_matches(hits[i], o, 0, k, what=f"batched map {i} ({f.n_t} x {f.n_f})")
+    b.close()
+    for m in maps:
+        m.close()
