@@ -52,6 +52,8 @@ def lib():
         L.orc_score_range_ext.argtypes = [C.c_void_p, C.c_uint64, C.c_uint64, C.c_uint64, C.c_double, C.c_int,
                                           C.c_int, dp, C.c_int, C.c_int, dp]
         L.orc_score_range_ext.restype = C.c_int
+        L.orc_score_range_ext_scale.argtypes = L.orc_score_range_ext.argtypes + [dp]
+        L.orc_score_range_ext_scale.restype = C.c_int
         L.orc_topk.argtypes = [dp, C.c_uint64, C.c_uint64, C.c_int, dp, u64p]
         L.orc_topk.restype = C.c_int
         _lib = L
@@ -181,18 +183,25 @@ class OracleMap:
         return out
 
     def score_range_ext(self, seed: int, offset: int, n_tracks: int, tau_max: float, general: bool = False,
-                        t_min: int = 1, quantiles=None, nthreads: int | None = None) -> np.ndarray:
-        """score_range with general templates and/or a delay prior."""
+                        t_min: int = 1, quantiles=None, nthreads: int | None = None, with_scale: bool = False):
+        """score_range with general templates and/or a delay prior; with_scale also
+        returns each template's comparison scale sum_j |z_j| / norm."""
         if nthreads is None:
             nthreads = os.cpu_count() or 1
         q = np.ascontiguousarray(quantiles if quantiles is not None else np.zeros(1), dtype=np.float64)
         nq = int(q.size) if quantiles is not None else 0
         out = np.zeros(n_tracks)
-        rc = lib().orc_score_range_ext(self._h, seed, offset, n_tracks, tau_max, int(general), int(t_min),
-                                       _ptr(q, C.c_double), nq, int(nthreads), _ptr(out, C.c_double))
+        if with_scale:
+            sc = np.zeros(n_tracks)
+            rc = lib().orc_score_range_ext_scale(self._h, seed, offset, n_tracks, tau_max, int(general), int(t_min),
+                                                 _ptr(q, C.c_double), nq, int(nthreads), _ptr(out, C.c_double),
+                                                 _ptr(sc, C.c_double))
+        else:
+            rc = lib().orc_score_range_ext(self._h, seed, offset, n_tracks, tau_max, int(general), int(t_min),
+                                           _ptr(q, C.c_double), nq, int(nthreads), _ptr(out, C.c_double))
         if rc != 0:
             raise RuntimeError("oracle score_range_ext failed (%d)" % rc)
-        return out
+        return (out, sc) if with_scale else out
 
     def score_range_scale(self, seed: int, offset: int, n_tracks: int, tau_max: float,
                           nthreads: int | None = None):

@@ -437,22 +437,34 @@ void orc_track_bins_general(const uint32_t t[3], const uint32_t f[3], int n_t, i
 }
 
 /* Eq. 7 over a general template's N = t2 - t0 + 1 pixels. */
-double orc_score_general(const orc_map *m, const uint32_t t[3], const uint32_t f[3], double tau)
+/* Eq. 7 over a general template's pixels; *scale_out (optional) receives the
+ * comparison scale sum_j |z_j| / norm. */
+static double orc_score_general_scale(const orc_map *m, const uint32_t t[3], const uint32_t f[3], double tau,
+                                      double *scale_out)
 {
     int32_t *bins = (int32_t *)malloc(sizeof(int32_t) * (size_t)m->n_t);
     orc_track_bins_general(t, f, m->n_t, m->n_f, bins);
-    double S = 0.0, W = 0.0;
+    double S = 0.0, W = 0.0, Z = 0.0;
     int N = 0;
     for (int j = 0; j < m->n_t; ++j) {
         if (bins[j] < 0) continue;
         size_t p = (size_t)j * m->n_f + (size_t)bins[j];
         double th = 2.0 * M_PI * (m->f_min + (double)bins[j] * m->df) * tau;
-        S += cos(th) * m->z[2 * p] - sin(th) * m->z[2 * p + 1];
+        double zr = m->z[2 * p], zi = m->z[2 * p + 1];
+        S += cos(th) * zr - sin(th) * zi;
         W += m->w[p];
+        Z += sqrt(zr * zr + zi * zi);
         ++N;
     }
     free(bins);
-    return m->paper_mode ? S / (double)N : S / sqrt(W);
+    double norm = m->paper_mode ? (double)N : sqrt(W);
+    if (scale_out) *scale_out = Z / norm;
+    return S / norm;
+}
+
+double orc_score_general(const orc_map *m, const uint32_t t[3], const uint32_t f[3], double tau)
+{
+    return orc_score_general_scale(m, t, f, tau, NULL);
 }
 
 void orc_score_explicit_general(const orc_map *m, const uint32_t *t3, const uint32_t *f3, const double *tau,
@@ -470,6 +482,7 @@ typedef struct {
     int general, t_min, n_q;
     const double *tq;
     double *out;
+    double *scale;   /* optional: comparison scale sum_j |z_j| / norm */
 } orc_gjob;
 
 static void *orc_general_worker(void *arg)
@@ -483,16 +496,37 @@ static void *orc_general_worker(void *arg)
         else orc_track_params(jb->seed, g, jb->m->n_f, jb->tau_max, f, &tau);
         if (jb->general) {
             orc_track_times(jb->seed, g, jb->m->n_t, jb->t_min, t);
-            jb->out[i] = orc_score_general(jb->m, t, f, tau);
+            jb->out[i] = orc_score_general_scale(jb->m, t, f, tau, jb->scale ? jb->scale + i : NULL);
         } else {
-            jb->out[i] = orc_score_track(jb->m, f, tau, NULL, NULL, NULL, NULL);
+            double W = 0.0, Z = 0.0;
+            jb->out[i] = orc_score_track(jb->m, f, tau, NULL, &W, NULL, &Z);
+            if (jb->scale) jb->scale[i] = Z / (jb->m->paper_mode ? (double)jb->m->n_t : sqrt(W));
         }
     }
     return NULL;
 }
 
+static int orc_range_ext_run(const orc_map *m, uint64_t seed, uint64_t offset, uint64_t T, double tau_max,
+                             int general, int t_min, const double *tq, int n_q, int nthreads, double *snr_out,
+                             double *scale_out);
+
 int orc_score_range_ext(const orc_map *m, uint64_t seed, uint64_t offset, uint64_t T, double tau_max, int general,
                         int t_min, const double *tq, int n_q, int nthreads, double *snr_out)
+{
+    return orc_range_ext_run(m, seed, offset, T, tau_max, general, t_min, tq, n_q, nthreads, snr_out, NULL);
+}
+
+/* As orc_score_range_ext, also writing each template's comparison scale. */
+int orc_score_range_ext_scale(const orc_map *m, uint64_t seed, uint64_t offset, uint64_t T, double tau_max,
+                              int general, int t_min, const double *tq, int n_q, int nthreads, double *snr_out,
+                              double *scale_out)
+{
+    return orc_range_ext_run(m, seed, offset, T, tau_max, general, t_min, tq, n_q, nthreads, snr_out, scale_out);
+}
+
+static int orc_range_ext_run(const orc_map *m, uint64_t seed, uint64_t offset, uint64_t T, double tau_max,
+                             int general, int t_min, const double *tq, int n_q, int nthreads, double *snr_out,
+                             double *scale_out)
 {
     if (nthreads < 1) nthreads = 1;
     if ((uint64_t)nthreads > T) nthreads = T ? (int)T : 1;
@@ -502,7 +536,8 @@ int orc_score_range_ext(const orc_map *m, uint64_t seed, uint64_t offset, uint64
     uint64_t base = T / (uint64_t)nthreads, rem = T % (uint64_t)nthreads, start = 0;
     for (int t = 0; t < nthreads; ++t) {
         uint64_t n = base + ((uint64_t)t < rem ? 1 : 0);
-        orc_gjob j = {m, seed, offset + start, n, tau_max, general, t_min, n_q, tq, snr_out + start};
+        orc_gjob j = {m, seed, offset + start, n, tau_max, general, t_min, n_q, tq, snr_out + start,
+                      scale_out ? scale_out + start : NULL};
         jobs[t] = j;
         start += n;
     }

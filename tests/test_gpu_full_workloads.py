@@ -7,6 +7,8 @@ FP64 oracle run over every template:
     closer than that);
   the same map with FP16 storage: every SNR within the FP16 storage bound
     3.5e-4 sum_j |z_j| / norm + 1e-5 |SNR| (RMS and maximum printed);
+  general templates (random control times, duration >= 25 columns), 1e6 on the
+    realistic map: every SNR within the parity bound, the k loudest;
   the 256 ragged maps of the batched workload (1e6 templates each, k = 16):
     every map's hits equal its single-map scoring bit for bit, and a subset of
     maps (largest, smallest, injected, a map without an exact 32-bit division)
@@ -106,3 +108,27 @@ def test_batched_workload(ctx):
     b.close()
     for m in maps:
         m.close()
+
+
+def test_general_templates_benchmark_size(ctx, realistic):
+    """The benchmark's general-template variant: 1e6 templates with random
+    control times (duration >= 25 columns) on the realistic map, every SNR
+    against the oracle, and the k loudest."""
+    w, fm, _, _ = realistic
+    T, t_min, k = 1_000_000, 25, 1024
+    m = ctx.load_map(torch.from_numpy(fm.y).cuda(), torch.from_numpy(fm.sigma).cuda(), fm.f_min, fm.df)
+    ctx.set_template_shape(True, t_min)
+    try:
+        ctx.set_tracks(T, w["seed"], 0, w["tau_max"])
+        hits = ctx.score(m, k)
+        g = ctx.score_all(m).cpu().numpy()
+    finally:
+        ctx.set_template_shape(False)
+    om = oracle.OracleMap.from_ftmap(fm)
+    o, sc = om.score_range_ext(w["seed"], 0, T, w["tau_max"], general=True, t_min=t_min,
+                               nthreads=os.cpu_count(), with_scale=True)
+    err = np.abs(g - o)
+    assert np.all(err <= RTOL * np.maximum(np.abs(o), sc)), np.max(err / sc)
+    print(f"general templates: max |dSNR| / scale = {np.max(err / sc):.3g}")
+    assert_topk_matches(hits, o, 0, k, what="general templates top-k")
+    m.close()
