@@ -473,7 +473,7 @@ static int score_into(stk_ctx *c, const stk_map *m, double *out)
     CUDA_TRY(c, cudaSetDevice(c->device));
     void *order = nullptr;
     if (score_wants_order(m->dev, c->ts, c->tune)) {
-        int rc = ensure(c, &c->order_buf, &c->order_cap, order_scratch_bytes(c->ts.n, m->dev.n_f));
+        int rc = ensure(c, &c->order_buf, &c->order_cap, order_scratch_bytes(c->ts.n, m->dev.n_f, c->ts.general != 0));
         if (rc) return rc;
         order = c->order_buf;
     }

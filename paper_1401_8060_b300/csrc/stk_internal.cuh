@@ -522,17 +522,19 @@ bool score_wants_order(const MapDev &m, const TrackSet &ts, const Tuning &tu);
 // Coherent-order pre-pass (stk_order.cu).  One map: buckets of 7-bit control
 // bins; *perm_out = the scoring order inside scratch (perm[p] = template index
 // relative to the range's offset).
-size_t order_scratch_bytes(uint64_t n, int n_f);
+size_t order_scratch_bytes(uint64_t n, int n_f, bool general = false);
 cudaError_t launch_order(const MapDev &m, const TrackSet &ts, void *scratch, int num_sms, cudaStream_t st,
                          const uint32_t **perm_out, int *launches);
 // Many maps: map i's templates take buckets bucket0 .. bucket0 + 2^(3 bits) - 1
 // and positions pos0 .. pos0 + n - 1 of perm (values relative to its offset).
 struct OrderMap {
-    TrackSet ts;
+    TrackSet ts;       // with ts.general: key = (t0, t2, Z-order of the bins), 4 + 4 + 12 bits
     uint32_t n_f;
     int shift;         // control bins >> shift (bits bits each) form the key
     uint32_t bucket0;
     uint32_t pos0;
+    uint32_t n_t;      // general templates: the map's columns
+    int tshift;        // general templates: control times >> tshift (4 bits each)
 };
 void order_shape(int n_f, int max_bits, int &shift, int &bits);
 size_t order_scratch_bytes_total(uint64_t total_n, uint64_t total_buckets);

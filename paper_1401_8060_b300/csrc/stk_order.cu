@@ -15,7 +15,9 @@
 // The order is a bucket sort of the template indices by a Morton (Z-order) key
 // of the three control bins, each reduced to its leading bits (7 for one map;
 // fewer per map in a batch, where map i owns its own range of buckets and of
-// positions):
+// positions).  General templates (random control times) are keyed first by
+// their start and end columns, so a warp's templates also cover the same
+// columns, then by the bins:
 //   keys:    bucket of each template, histogram of the buckets (atomics)
 //   tiles:   per tile of 4096 buckets, the number of templates
 //   bases:   exclusive prefix of the tile counts (one block)
@@ -67,8 +69,13 @@ __global__ void order_keys_kernel(OrderArgs a, uint32_t *__restrict__ keys, uint
         uint32_t f[3];
         double tau;
         draw_track_ts(ts, ts.offset + i, n_f, f, tau);
-        const uint32_t key = bucket0 + (spread3(f[0] >> shift) | (spread3(f[1] >> shift) << 1) |
-                                        (spread3(f[2] >> shift) << 2));
+        uint32_t key = spread3(f[0] >> shift) | (spread3(f[1] >> shift) << 1) | (spread3(f[2] >> shift) << 2);
+        if (ts.general) {  // start and end column first: a warp's templates cover the same columns
+            uint32_t t[3];
+            draw_times(ts.seed, ts.offset + i, om.n_t, (uint32_t)ts.t_min, t);
+            key |= (((t[0] >> om.tshift) << 4) | (t[2] >> om.tshift)) << 12;
+        }
+        key += bucket0;
         keys[pos0 + i] = key;
         atomicAdd(&hist[key], 1u);
     }
@@ -213,11 +220,14 @@ size_t order_scratch_bytes_total(uint64_t total_n, uint64_t total_buckets)
     return (size_t)(2 * total_n + total_buckets + ntiles) * sizeof(uint32_t) + 256;
 }
 
-size_t order_scratch_bytes(uint64_t n, int n_f)
+// Pinned templates: 7 bits per control bin (2^21 buckets).  General templates:
+// 4 bits each of the start and end column, then 4 bits per control bin (2^20).
+size_t order_scratch_bytes(uint64_t n, int n_f, bool general)
 {
     int shift, bits;
     order_shape(n_f, 7, shift, bits);
-    return order_scratch_bytes_total(n, 1ull << (3 * bits));
+    // general keys place the time bits at bit 12 whatever the bin bits in use
+    return order_scratch_bytes_total(n, general ? (1ull << 20) : (1ull << (3 * bits)));
 }
 
 cudaError_t launch_order(const MapDev &m, const TrackSet &ts, void *scratch, int num_sms, cudaStream_t st,
@@ -227,11 +237,15 @@ cudaError_t launch_order(const MapDev &m, const TrackSet &ts, void *scratch, int
     oa.maps = nullptr;
     oa.single.ts = ts;
     oa.single.n_f = (uint32_t)m.n_f;
-    int bits;
-    order_shape(m.n_f, 7, oa.single.shift, bits);
+    int bits, tbits;
+    order_shape(m.n_f, ts.general ? 4 : 7, oa.single.shift, bits);
+    order_shape(m.n_t, 4, oa.single.tshift, tbits);
+    oa.single.n_t = (uint32_t)m.n_t;
     oa.single.bucket0 = 0;
     oa.single.pos0 = 0;
-    return run_order(oa, 1, ts.n, ts.n, 1ull << (3 * bits), scratch, num_sms, st, perm_out, launches);
+    // general keys place the time bits at bit 12 whatever the bin bits in use
+    const uint64_t nb = ts.general ? (1ull << 20) : (1ull << (3 * bits));
+    return run_order(oa, 1, ts.n, ts.n, nb, scratch, num_sms, st, perm_out, launches);
 }
 
 cudaError_t launch_order_batch(const OrderMap *d_maps, int n_maps, uint64_t max_n, uint64_t total_n,

@@ -90,14 +90,18 @@ __device__ __forceinline__ double finalize_general(float acc, float W, const Map
     return (double)acc * (y0 * fma(-0.5, t, 1.5));
 }
 
+// One thread per template, in coherent order when perm is given (a warp's
+// templates then start and end in nearby columns and sit at nearby bins).
 template <int WMODE, int PREC, bool EXPLICIT>
 __global__ void __launch_bounds__(256) score_general_kernel(MapDev m, TrackSet ts, const uint32_t *__restrict__ t3,
                                                             const uint32_t *__restrict__ f3,
                                                             const double *__restrict__ tau_in, uint64_t n,
-                                                            double *__restrict__ out, int *err)
+                                                            double *__restrict__ out, int *err,
+                                                            const uint32_t *__restrict__ perm)
 {
-    const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+    const uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    const uint64_t i = perm ? (uint64_t)__ldg(perm + p) : p;
     uint32_t f[3], t[3];
     double tau;
     if (EXPLICIT) {
@@ -137,19 +141,22 @@ __global__ void __launch_bounds__(256) score_general_kernel(MapDev m, TrackSet t
 
 template <int WMODE, int PREC, bool EXPLICIT>
 cudaError_t launch_general_W(const MapDev &m, const TrackSet &ts, const uint32_t *t3, const uint32_t *f3,
-                             const double *tau, uint64_t n, double *out, int *err, cudaStream_t st)
+                             const double *tau, uint64_t n, double *out, int *err, cudaStream_t st,
+                             const uint32_t *perm)
 {
     const uint64_t blocks = (n + 255) / 256;
     if (blocks > 0x7fffffffull) return cudaErrorInvalidValue;
-    score_general_kernel<WMODE, PREC, EXPLICIT><<<(unsigned)blocks, 256, 0, st>>>(m, ts, t3, f3, tau, n, out, err);
+    score_general_kernel<WMODE, PREC, EXPLICIT>
+        <<<(unsigned)blocks, 256, 0, st>>>(m, ts, t3, f3, tau, n, out, err, perm);
     return cudaGetLastError();
 }
 
 template <bool EXPLICIT>
 cudaError_t launch_general(const MapDev &m, const TrackSet &ts, const uint32_t *t3, const uint32_t *f3,
-                           const double *tau, uint64_t n, double *out, int *err, cudaStream_t st)
+                           const double *tau, uint64_t n, double *out, int *err, cudaStream_t st,
+                           const uint32_t *perm = nullptr)
 {
-#define STK_GEN(W, P) return launch_general_W<W, P, EXPLICIT>(m, ts, t3, f3, tau, n, out, err, st)
+#define STK_GEN(W, P) return launch_general_W<W, P, EXPLICIT>(m, ts, t3, f3, tau, n, out, err, st, perm)
     if (m.prec == PREC_FP16) {
         if (m.wmode == WMODE_CONST) STK_GEN(WMODE_CONST, PREC_FP16);
         if (m.wmode == WMODE_FREQ) STK_GEN(WMODE_FREQ, PREC_FP16);
@@ -485,7 +492,9 @@ __global__ void track_params_kernel(MapDev m, TrackSet ts, uint64_t g, uint32_t 
 
 bool score_wants_order(const MapDev &m, const TrackSet &ts, const Tuning &tu)
 {
-    if (!tu.order || ts.general || !m.fast32 || tu.kernel == 1 || m.n_f > kPhaseNarrowNf) return false;
+    if (!tu.order) return false;
+    if (ts.general) return ts.n * (uint64_t)m.n_t >= (1ull << 22);  // general-template kernel
+    if (!m.fast32 || tu.kernel == 1 || m.n_f > kPhaseNarrowNf) return false;
     return tu.kernel == 2 || ts.n * (uint64_t)m.n_t >= (1ull << 24);
 }
 
@@ -499,9 +508,15 @@ cudaError_t launch_score_generated(const MapDev &m, const TrackSet &ts, double *
         p.kernel = 3;
         p.threads = 256;
         p.grid = (int)std::min<uint64_t>((n + 255) / 256, 0x7fffffffull);
+        const uint32_t *perm = nullptr;
+        if (order_scratch && score_wants_order(m, ts, tu)) {
+            cudaError_t e = launch_order(m, ts, order_scratch, num_sms, st, &perm, &p.order_launches);
+            if (e != cudaSuccess) return e;
+            p.order = 1;
+        }
         if (plan) *plan = p;
         if (order_done && cudaEventRecord(order_done, st) != cudaSuccess) return cudaGetLastError();
-        return launch_general<false>(m, ts, nullptr, nullptr, nullptr, n, out, err, st);
+        return launch_general<false>(m, ts, nullptr, nullptr, nullptr, n, out, err, st, perm);
     }
     const uint64_t work = n * (uint64_t)m.n_t;
     int kernel = tu.kernel;

@@ -111,6 +111,33 @@ def test_general_topk_with_prior_vs_oracle(ctx):
     assert np.all(hits["tau"] >= q[0]) and np.all(hits["tau"] <= q[-1])
 
 
+@pytest.mark.parametrize("n_t,n_f,T,prior", [(300, 700, 40000, False), (120, 5, 50000, True),
+                                              (12, 2000, 400000, False)])
+def test_general_coherent_order_identical(ctx, n_t, n_f, T, prior):
+    """Large general-template jobs run in coherent order (start and end column,
+    then bins); every SNR equals index order bit for bit at its own index."""
+    from paper_1401_8060_b300 import _lib
+    y, sig = _map("freq", n_t, n_f, 31)
+    m = ctx.load_map(torch.from_numpy(y).cuda(), torch.from_numpy(sig).cuda(), 40.0, 0.5)
+    ctx.set_template_shape(True, 3)
+    if prior:
+        ctx.set_tau_prior(np.linspace(-0.006, 0.008, 9))
+    ctx.set_tracks(T, 5, 77, 0.01)
+    try:
+        a = ctx.score_all(m).cpu().numpy()
+        assert ctx.last_plan()["order"] == 1
+        ctx.set_option(_lib.STK_OPT_ORDER, 0)
+        b = ctx.score_all(m).cpu().numpy()
+        assert ctx.last_plan()["order"] == 0
+    finally:
+        ctx.set_option(_lib.STK_OPT_ORDER, 1)
+        ctx.set_template_shape(False)
+        if prior:
+            ctx.set_tau_prior(None)
+    np.testing.assert_array_equal(a, b)
+    m.close()
+
+
 def test_general_rejects_large_maps(ctx):
     y = np.zeros((10, 9000), np.complex64)
     m = ctx.load_map(y, np.ones(9000, np.float32), 40.0, 0.5)
