@@ -291,9 +291,10 @@ STK_API int stk_batch_score(stk_batch *batch, int k, stk_hit *out, unsigned flag
  * The flag stays set until cleared. */
 STK_API int stk_batch_cancel(stk_batch *batch, int on);
 
-/* Autotuner: time every candidate launch shape (threads per block, templates
- * per thread, slab buffers) on a sample of this batch's tiles and keep the
- * fastest for later stk_batch_score calls.  out (may be NULL) receives
+/* Autotuner: time every candidate launch shape (512/768/1024 threads with 2..5
+ * templates per thread, or 512 threads with 6, 8, 10 or 11; 2 or 3 slab
+ * buffers: 32 shapes) on a sample of this batch's tiles and keep the fastest
+ * for later stk_batch_score calls.  out (may be NULL) receives
  * {threads, templates per thread, slab buffers, sample time in ns}.
  * Errors: STK_EINVAL, STK_ECUDA. */
 STK_API int stk_batch_tune(stk_batch *batch, int k, int64_t out[4]);

@@ -114,8 +114,12 @@ __device__ __forceinline__ void batch_slab(const typename Pix<PREC>::Rec *row, c
     }
 }
 
+// Up to 5 templates per thread fit 64 registers (1024 threads); 6 to 11 need up
+// to 128 (512 threads).
+constexpr int batch_max_threads(int R) { return R <= 5 ? 1024 : 512; }
+
 template <int R, int WMODE, int PREC>
-__global__ void __launch_bounds__(1024, 1) score_batch_kernel(BatchArgs a)
+__global__ void __launch_bounds__(batch_max_threads(R), 1) score_batch_kernel(BatchArgs a)
 {
     using Rec = typename Pix<PREC>::Rec;
     extern __shared__ __align__(128) unsigned char smem[];
@@ -395,7 +399,9 @@ __global__ void __launch_bounds__(256) batch_rank_kernel(const BatchMap *__restr
 template <int R, int WMODE, int PREC>
 cudaError_t launch_batch_R(const BatchArgs &a, int grid, int threads, size_t smem, bool set_attr, cudaStream_t st)
 {
-    auto k = score_batch_kernel<R, WMODE, PREC>;    if (set_attr) {
+    auto k = score_batch_kernel<R, WMODE, PREC>;
+    if (threads > batch_max_threads(R)) return cudaErrorInvalidConfiguration;
+    if (set_attr) {
         cudaFuncAttributes fa;
         cudaError_t e = cudaFuncGetAttributes(&fa, k);
         if (e != cudaSuccess) return e;
@@ -420,6 +426,10 @@ cudaError_t launch_batch_W(int R, const BatchArgs &a, int grid, int threads, siz
     case 3: return launch_batch_R<3, WMODE, PREC>(a, grid, threads, smem, sa, st);
     case 4: return launch_batch_R<4, WMODE, PREC>(a, grid, threads, smem, sa, st);
     case 5: return launch_batch_R<5, WMODE, PREC>(a, grid, threads, smem, sa, st);
+    case 6: return launch_batch_R<6, WMODE, PREC>(a, grid, threads, smem, sa, st);
+    case 8: return launch_batch_R<8, WMODE, PREC>(a, grid, threads, smem, sa, st);
+    case 10: return launch_batch_R<10, WMODE, PREC>(a, grid, threads, smem, sa, st);
+    case 11: return launch_batch_R<11, WMODE, PREC>(a, grid, threads, smem, sa, st);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -804,14 +814,23 @@ int stk_batch_tune(stk_batch *b, int k, int64_t out[4])
     cudaEvent_t e0, e1;
     CUDA_TRY(c, cudaEventCreate(&e0));
     CUDA_TRY(c, cudaEventCreate(&e1));
-    const int threads_c[] = {512, 768, 1024};
-    const int nstage_c[] = {2, 3};
+    // candidate launch shapes: 64-register (up to 1024 threads, R <= 5) and
+    // 128-register (512 threads, R 6..11) families, 2 or 3 slab buffers
+    struct Shape {
+        int threads, R, nstage;
+    };
+    std::vector<Shape> shapes;
+    for (int th : {512, 768, 1024})
+        for (int R = 2; R <= 5; ++R)
+            for (int ns : {2, 3}) shapes.push_back({th, R, ns});
+    for (int R : {6, 8, 10, 11})
+        for (int ns : {2, 3}) shapes.push_back({512, R, ns});
     double best_rate = -1.0;
     int bt = b->threads, bR = b->R, bs = b->nstage;
     float best_ms = 0.f;
     int rc = STK_OK;
-    for (int ci = 0; ci < 3 * 4 * 2 && rc == STK_OK; ++ci) {
-        const int th = threads_c[ci / 8], R = 2 + (ci / 2) % 4, ns = nstage_c[ci % 2];
+    for (size_t ci = 0; ci < shapes.size() && rc == STK_OK; ++ci) {
+        const int th = shapes[ci].threads, R = shapes[ci].R, ns = shapes[ci].nstage;
         if ((rc = configure(b, th, R, ns)) != STK_OK) break;
         // sample: the first waves of the schedule (largest maps), about 3 tiles per SM
         const uint32_t nt = std::min<uint32_t>(b->ntiles_total, (uint32_t)c->num_sms * 3);

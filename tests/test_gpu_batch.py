@@ -130,7 +130,8 @@ def test_batch_graph_replay_k_change_and_tune(ctx):
     h3 = b.score(3)                                          # new graph for another k
     np.testing.assert_array_equal(h3, h8[:, :3])
     cfg = b.tune(8)
-    assert cfg["threads"] in (512, 768, 1024) and 2 <= cfg["R"] <= 5 and cfg["nstage"] in (2, 3)
+    assert cfg["threads"] in (512, 768, 1024) and 2 <= cfg["R"] <= 11 and cfg["nstage"] in (2, 3)
+    assert cfg["R"] <= 5 or cfg["threads"] == 512
     np.testing.assert_array_equal(b.score(8), h8)          # any launch shape: same result
     out = torch.zeros(len(maps) * 8 * 40, dtype=torch.uint8, device="cuda")
     b.score(8, out=out)
