@@ -482,6 +482,37 @@ def main():
             "config": "n_t ~ U{100..1000}, n_f ~ U{200..2000}, 0.5 Hz from 40 Hz, sigma0 ~ U(0.5, 2), "
                       "10% injected (SNR 10-30)"}
         batch.close()
+        # the same maps with little work per map (2e4 templates): launch overheads and
+        # per-map fill dominate the sequential calls; one batched launch avoids them
+        Ts = 20_000
+        bsm = stk.Batch(ctx, dm, [Ts] * nb, seeds, [0] * nb, w["tau_max"])
+        bsm.tune(kb)
+        for _ in range(3):
+            bsm.score(kb, out=outb)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        flush.zero_()
+        e0.record(stream)
+        bsm.score(kb, out=outb)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_small = e0.elapsed_time(e1)
+        bsm.close()
+        seq_small = []
+        for rep in range(2):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            flush.zero_()
+            e0.record(stream)
+            for i, m_ in enumerate(dm):
+                ctx.set_tracks(Ts, seeds[i], 0, w["tau_max"])
+                ctx.score(m_, kb, out=outs)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            seq_small.append(e0.elapsed_time(e1))
+        ctx.sync()
+        variants["batched"]["small_work"] = {
+            "templates_per_map": Ts, "ms_per_step": ms_small, "sequential_ms": min(seq_small),
+            "speedup_vs_sequential": min(seq_small) / ms_small,
+            "value": float(sum(f.n_t for f in bmaps)) * Ts / (ms_small / 1e3), "unit": "track-pixels/s"}
         for m_ in dm:
             m_.close()
         ctx.set_tracks(T, w["seed"], offset, w["tau_max"])
