@@ -126,16 +126,47 @@ __global__ void __launch_bounds__(256) score_general_kernel(MapDev m, TrackSet t
     const Phase ph = phase_consts(m.f_min, m.df, tau, m.n_f);
     const GenCurve c = gen_curve(t, f);
     const GenFilter gf = gen_filter(c);
-    float acc = 0.f, W = 0.f;
-    int32_t b = (int32_t)f[0];
-    for (int j = (int)t[0]; j <= (int)t[2]; ++j) {
-        if (j > (int)t[0]) b = gen_pixel(c, gf, j, m.n_f);
+    // Two partial sums: pixels the estimate decides, in column order, and pixels
+    // within its margin of a rounding boundary (about 2 % of them), also in column
+    // order.  Those wait, up to four per lane; the waiting pixels of all lanes then
+    // take the long exact test together, so the warp runs it once for every lane
+    // rather than once per lane.  Each template's sums do not depend on its
+    // neighbours in the warp: when a flush happens changes nothing.
+    float acc = 0.f, W = 0.f, acc_x = 0.f, W_x = 0.f;
+    auto add = [&](int j, int32_t b, float &a_, float &w_) {
         const auto v = Pix<PREC>::load_global(m.rec, (size_t)j * m.ldr + (uint32_t)b);
         float wv = 0.f;
         if (WMODE == WMODE_FREQ) wv = __ldg(m.w + b);
         if (WMODE == WMODE_PIXEL) wv = __ldg(m.w + (size_t)j * m.ldw + b);
-        accumulate<PREC, WMODE>(v, (uint32_t)b, ph, wv, acc, W);
+        accumulate<PREC, WMODE>(v, (uint32_t)b, ph, wv, a_, w_);
+    };
+    int np = 0, pj0 = 0, pj1 = 0, pj2 = 0, pj3 = 0;
+    int32_t pb0 = 0, pb1 = 0, pb2 = 0, pb3 = 0;
+    auto flush = [&]() {
+        for (int q = 0; q < np; ++q) {
+            const int j = q == 0 ? pj0 : q == 1 ? pj1 : q == 2 ? pj2 : pj3;
+            const int32_t b0 = q == 0 ? pb0 : q == 1 ? pb1 : q == 2 ? pb2 : pb3;
+            add(j, gen_step(c, j, b0, m.n_f), acc_x, W_x);
+        }
+        np = 0;
+    };
+    add((int)t[0], (int32_t)f[0], acc, W);
+    for (int j = (int)t[0] + 1; j <= (int)t[2]; ++j) {
+        int32_t b;
+        if (gen_estimate(c, gf, j, m.n_f, b)) {
+            add(j, b, acc, W);
+        } else {
+            if (np == 0) { pj0 = j; pb0 = b; }
+            else if (np == 1) { pj1 = j; pb1 = b; }
+            else if (np == 2) { pj2 = j; pb2 = b; }
+            else { pj3 = j; pb3 = b; }
+            ++np;
+        }
+        if (__any_sync(__activemask(), np == 4)) flush();
     }
+    flush();
+    acc += acc_x;
+    W += W_x;
     out[i] = finalize_general<WMODE, PREC>(acc, W, m, (int)(t[2] - t[0] + 1));
 }
 
