@@ -405,6 +405,43 @@ def test_update_map_equals_fresh_load(ctx, fp16, host):
         m.close()
 
 
+def test_pipelined_updates_on_two_streams(ctx):
+    """Two maps alternate: each step's data is copied in and packed on a copy
+    stream while the other map scores on a compute stream (the end-to-end
+    benchmark's pattern); every step's records equal a plain load-and-score."""
+    n_t, n_f, T, k = 48, 200, 30000, 8
+    ectx = stk.Context(0)                      # follows the current torch stream
+    ectx.set_tracks(T, 4, 0, 0.01)
+    datas = [rand_map(70 + i, n_t, n_f, "freq") for i in range(6)]
+    pins = [(torch.from_numpy(y).pin_memory(), torch.from_numpy(s).pin_memory()) for y, s in datas]
+    maps = [ectx.load_map(pins[0][0], pins[0][1], 40.0, 0.5) for _ in range(2)]
+    copy_s, comp_s = torch.cuda.Stream(), torch.cuda.Stream()
+    outs = [torch.zeros(k * 40, dtype=torch.uint8, device="cuda") for _ in range(len(datas))]
+    scored = [None, None]
+    for i, (yp, sp) in enumerate(pins):
+        j = i % 2
+        if scored[j] is not None:
+            scored[j].synchronize()
+        with torch.cuda.stream(copy_s):
+            ectx.update_map(maps[j], yp, sp)
+            copied = torch.cuda.Event()
+            copied.record(copy_s)
+        with torch.cuda.stream(comp_s):
+            comp_s.wait_event(copied)
+            ectx.score(maps[j], k, out=outs[i])
+            scored[j] = torch.cuda.Event()
+            scored[j].record(comp_s)
+    torch.cuda.synchronize()
+    ectx.sync()
+    for i, (y, s) in enumerate(datas):
+        m = ctx.load_map(y, s, 40.0, 0.5)
+        ctx.set_tracks(T, 4, 0, 0.01)
+        np.testing.assert_array_equal(outs[i].cpu().numpy().view(stk.HIT_DTYPE), ctx.score(m, k),
+                                      err_msg=f"step {i}")
+        m.close()
+    ectx.close()
+
+
 def test_update_map_invalid_data_reported(ctx):
     """A weighted map's update does not wait: bad data surfaces at the next
     host-output scoring call; a constant-weight map's update checks at once."""
