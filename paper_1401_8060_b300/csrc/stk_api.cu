@@ -473,7 +473,8 @@ static int score_into(stk_ctx *c, const stk_map *m, double *out)
     CUDA_TRY(c, cudaSetDevice(c->device));
     void *order = nullptr;
     if (score_wants_order(m->dev, c->ts, c->tune)) {
-        int rc = ensure(c, &c->order_buf, &c->order_cap, order_scratch_bytes(c->ts.n, m->dev.n_f, c->ts.general != 0));
+        int rc = ensure(c, &c->order_buf, &c->order_cap, order_scratch_bytes(c->ts.n, m->dev.n_f, m->dev.n_t,
+                                                                           c->ts.general != 0, c->num_sms));
         if (rc) return rc;
         order = c->order_buf;
     }

@@ -17,7 +17,7 @@
 // single-map kernels.  The division by 2 M^2 is the map's exact multiply-shift
 // when it has one, else a multiply-shift with one correction step (exact for all
 // numerators below 2^32).  Each map's templates are scored in coherent
-// order (a bucket sort over all maps, run inside the graph before the tiles).
+// order (one sort over all maps, run inside the graph before the tiles).
 #include <algorithm>
 #include <cmath>
 #include <vector>
@@ -493,7 +493,8 @@ struct stk_batch {
     bool use_order = false;
     OrderMap *d_omaps = nullptr;
     void *order_buf = nullptr;
-    uint64_t total_n = 0, total_buckets = 0, max_n = 0;
+    uint64_t total_n = 0, max_n = 0;
+    uint32_t order_nc = 0, order_fbits = 0;  // coarse buckets, most fine bits of a map
     const uint32_t *d_perm = nullptr;
 };
 
@@ -589,7 +590,7 @@ cudaError_t enqueue(stk_batch *b, int k, uint32_t ntiles, bool merge, bool set_a
                     bool order = true)
 {
     if (b->use_order && order) {
-        cudaError_t e = launch_order_batch(b->d_omaps, b->n_maps, b->max_n, b->total_n, b->total_buckets,
+        cudaError_t e = launch_order_batch(b->d_omaps, b->n_maps, b->total_n, b->order_nc, b->order_fbits,
                                            b->order_buf, b->ctx->num_sms, st, &b->d_perm, nullptr);
         if (e != cudaSuccess) return e;
     }
@@ -721,25 +722,23 @@ int stk_batch_create(stk_ctx *c, const stk_map *const *maps, int n_maps, const u
         return set_err(c, STK_ENOMEM, "batch allocation: %s", cudaGetErrorString(e));
     }
     *b->h_cancel = 0;
-    if (c->tune.order) {
-        // buckets: at most 2^26 over all maps, so the key keeps fewer bits per map in large batches
-        int max_bits = 7;
-        while (max_bits > 1 && ((uint64_t)n_maps << (3 * max_bits)) > (1ull << 26)) --max_bits;
+    if (c->tune.order && n_maps <= 8192) {
+        // coarse buckets: at most 8192 over all maps, so large batches keep fewer key bits per map
         std::vector<OrderMap> om(n_maps);
         for (int i = 0; i < n_maps; ++i) {
-            int bits;
+            om[i] = OrderMap{};
             om[i].ts = b->hmaps[i].ts;
             om[i].n_f = (uint32_t)b->hmaps[i].m.n_f;
-            order_shape(b->hmaps[i].m.n_f, max_bits, om[i].shift, bits);
-            om[i].bucket0 = (uint32_t)b->total_buckets;
+            om[i].n_t = (uint32_t)b->hmaps[i].m.n_t;
             om[i].pos0 = b->hmaps[i].pos0;
-            b->total_buckets += 1ull << (3 * bits);
         }
-        const size_t bytes = order_scratch_bytes_total(b->total_n, b->total_buckets);
+        order_plan_maps(om.data(), n_maps, b->order_nc, b->order_fbits);
+        const size_t bytes = order_scratch_bytes_maps(b->total_n, b->order_nc, c->num_sms);
         if ((e = cudaMalloc(&b->d_omaps, sizeof(OrderMap) * n_maps)) != cudaSuccess ||
             (e = cudaMalloc(&b->order_buf, bytes)) != cudaSuccess ||
             (e = cudaMemcpy(b->d_omaps, om.data(), sizeof(OrderMap) * n_maps, cudaMemcpyHostToDevice)) !=
-                cudaSuccess) {
+                cudaSuccess ||
+            (e = order_prepare(b->order_nc, b->order_fbits)) != cudaSuccess) {
             stk_batch_destroy(b);
             return set_err(c, STK_ENOMEM, "batch order scratch (%zu bytes): %s", bytes, cudaGetErrorString(e));
         }

@@ -537,28 +537,33 @@ cudaError_t launch_score_generated(const MapDev &m, const TrackSet &ts, double *
 // Whether launch_score_generated would use order scratch for this call.
 bool score_wants_order(const MapDev &m, const TrackSet &ts, const Tuning &tu);
 
-// Coherent-order pre-pass (stk_order.cu).  One map: buckets of 7-bit control
-// bins; *perm_out = the scoring order inside scratch (perm[p] = template index
-// relative to the range's offset).
-size_t order_scratch_bytes(uint64_t n, int n_f, bool general = false);
+// Coherent-order pre-pass (stk_order.cu).  One map: the key is 7 bits per
+// control bin (general templates: 4 bits each of the start and end column and
+// of the bins); *perm_out = the scoring order inside scratch (perm[p] =
+// template index relative to the range's offset).
+size_t order_scratch_bytes(uint64_t n, int n_f, int n_t, bool general, int num_sms);
 cudaError_t launch_order(const MapDev &m, const TrackSet &ts, void *scratch, int num_sms, cudaStream_t st,
                          const uint32_t **perm_out, int *launches);
-// Many maps: map i's templates take buckets bucket0 .. bucket0 + 2^(3 bits) - 1
-// and positions pos0 .. pos0 + n - 1 of perm (values relative to its offset).
+// Many maps: map i's templates take positions pos0 .. pos0 + n - 1 of perm
+// (values relative to its offset) and coarse buckets from coarse0.
 struct OrderMap {
     TrackSet ts;       // with ts.general: key = (t0, t2, Z-order of the bins), 4 + 4 + 12 bits
     uint32_t n_f;
-    int shift;         // control bins >> shift (bits bits each) form the key
-    uint32_t bucket0;
-    uint32_t pos0;
-    uint32_t n_t;      // general templates: the map's columns
+    uint32_t n_t;
+    int shift;         // control bins >> shift form the key
     int tshift;        // general templates: control times >> tshift (4 bits each)
+    int fbits;         // key bits below the coarse bucket
+    uint32_t coarse0;  // first coarse bucket
+    uint32_t pos0;     // first position
 };
 void order_shape(int n_f, int max_bits, int &shift, int &bits);
-size_t order_scratch_bytes_total(uint64_t total_n, uint64_t total_buckets);
-cudaError_t launch_order_batch(const OrderMap *d_maps, int n_maps, uint64_t max_n, uint64_t total_n,
-                               uint64_t total_buckets, void *scratch, int num_sms, cudaStream_t st,
-                               const uint32_t **perm_out, int *launches);
+// Fill shift, tshift, fbits and coarse0 of maps (ts, n_f, n_t, pos0 given); nc = coarse buckets in all.
+void order_plan_maps(OrderMap *maps, int n_maps, uint32_t &nc, uint32_t &max_fbits);
+size_t order_scratch_bytes_maps(uint64_t total_n, uint32_t nc, int num_sms);
+cudaError_t order_prepare(uint32_t nc, uint32_t max_fbits);
+cudaError_t launch_order_batch(const OrderMap *d_maps, int n_maps, uint64_t total_n, uint32_t nc, uint32_t max_fbits,
+                               void *scratch, int num_sms, cudaStream_t st, const uint32_t **perm_out,
+                               int *launches);
 // Explicit templates f3[n][3], tau[n].
 cudaError_t launch_score_explicit(const MapDev &m, const uint32_t *f3, const double *tau, uint64_t n, double *out,
                                   int *err, cudaStream_t st);

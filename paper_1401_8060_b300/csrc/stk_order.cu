@@ -1,31 +1,34 @@
-// Coherent template order: a scheduling pre-pass for the slab kernel.
+// Coherent template order: a scheduling pre-pass for the slab, batched and
+// general-template kernels.
 //
 // Templates are independent draws, and the statistic of each (Eq. 7) does not
-// depend on the order in which templates are scored, so the slab kernel may
-// give a warp any 32 templates.  Given 32 random templates, the lanes' pixel
-// bins in a column are random and their shared-memory gathers collide in banks
-// (about 6 wavefronts per warp for 8-byte records and 3.5 for the 4-byte weight
-// table, against 2 and 1 without conflicts).  Two templates whose control
-// frequencies differ by at most d bins are at most d bins apart in every column
-// (the curve is a convex combination of f0, f1, f2 with Bernstein weights), so
-// scoring templates in an order that keeps neighbours in (f0, f1, f2) together
-// puts each warp's bins in a narrow band, where distinct bins fall in distinct
-// banks.
+// depend on the order in which templates are scored, so a kernel may give a
+// warp any 32 templates.  Given 32 random templates, the lanes' pixel bins in a
+// column are random and their shared-memory gathers collide in banks (about 6
+// wavefronts per warp for 8-byte records and 3.5 for the 4-byte weight table,
+// against 2 and 1 without conflicts).  Two templates whose control frequencies
+// differ by at most d bins are at most d bins apart in every column (the curve
+// is a convex combination of f0, f1, f2 with Bernstein weights), so scoring
+// templates in an order that keeps neighbours in (f0, f1, f2) together puts
+// each warp's bins in a narrow band, where distinct bins fall in distinct banks.
 //
-// The order is a bucket sort of the template indices by a Morton (Z-order) key
-// of the three control bins, each reduced to its leading bits (7 for one map;
-// fewer per map in a batch, where map i owns its own range of buckets and of
-// positions).  General templates (random control times) are keyed first by
-// their start and end columns, so a warp's templates also cover the same
-// columns, then by the bins:
-//   keys:    bucket of each template, histogram of the buckets (atomics)
-//   tiles:   per tile of 4096 buckets, the number of templates
-//   bases:   exclusive prefix of the tile counts (one block)
-//   scan:    exclusive prefix over buckets (tile base + in-tile scan)
-//   scatter: perm[pos] = i (index within its map), pos from the bucket's offset
-// Within a bucket the order is whatever the atomics give; no result depends on
-// it (each template's sums run over its own columns in column order).
+// The order sorts template positions by a key: the Morton (Z-order) interleave
+// of the leading bits of f0, f1, f2 (7 each for one map, fewer per map in large
+// batches); general templates (random control times) put 4 bits each of the
+// start and end column above those, so a warp's templates also cover the same
+// columns.  Map i of a batch owns its own key range and position range.  The
+// sort is two-level, with no global atomics:
+//   keys:    draw each template, write its key, count coarse buckets (the top
+//            key bits) per block in shared memory
+//   columns: per coarse bucket, the exclusive prefix over blocks
+//   bases:   exclusive prefix over coarse buckets (one block)
+//   coarse:  each block places its templates into their coarse buckets
+//   fine:    one block per coarse bucket sorts it by the remaining key bits
+//            (counting sort in shared memory) and writes the positions
+// Within a fine bucket the order is whatever the shared atomics give; no result
+// depends on it (each template's sums run over its own columns in column order).
 #include <algorithm>
+#include <vector>
 
 #include "stk_internal.cuh"
 
@@ -33,19 +36,22 @@ namespace stk {
 
 namespace {
 
-constexpr int kTile = 4096;        // buckets per scan tile
-constexpr int kScanThreads = 256;  // 16 buckets per thread
-constexpr int kBaseThreads = 1024; // one block scans the tile counts
+constexpr int kKeyThreads = 1024;  // keys and coarse kernels
+constexpr int kFineThreads = 256;  // fine kernel
+constexpr int kFineCache = 2048;   // fine kernel: bucket sizes held in registers
+constexpr int kFineShift = 14;     // stored key = coarse << 14 | fine
+constexpr uint32_t kMaxCoarse = 8192;
 
 struct OrderArgs {
-    const OrderMap *maps;  // device array (grid.y = map), or NULL: `single`
+    const OrderMap *maps;  // device array, or NULL: `single`
     OrderMap single;
+    int n_maps;
+    uint64_t total_n;
+    uint32_t nc;           // coarse buckets
+    int grid;              // blocks of the keys and coarse kernels
 };
 
-__device__ __forceinline__ const OrderMap &order_map(const OrderArgs &a)
-{
-    return a.maps ? a.maps[blockIdx.y] : a.single;
-}
+__device__ __forceinline__ const OrderMap &omap(const OrderArgs &a, int i) { return a.maps ? a.maps[i] : a.single; }
 
 // bits 0..9 of x spread to bits 0, 3, 6, ..., 27 (Morton interleave)
 __device__ __forceinline__ uint32_t spread3(uint32_t x)
@@ -58,44 +64,123 @@ __device__ __forceinline__ uint32_t spread3(uint32_t x)
     return x;
 }
 
-__global__ void order_keys_kernel(OrderArgs a, uint32_t *__restrict__ keys, uint32_t *__restrict__ hist)
+// The map holding position p (maps are contiguous in position order).
+__device__ __forceinline__ int map_of(const OrderArgs &a, uint64_t p)
 {
-    const OrderMap &om = order_map(a);
-    const TrackSet ts = om.ts;
-    const uint32_t n_f = om.n_f, bucket0 = om.bucket0, pos0 = om.pos0;
-    const int shift = om.shift;
-    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < ts.n; i += stride) {
-        uint32_t f[3];
-        double tau;
-        draw_track_ts(ts, ts.offset + i, n_f, f, tau);
-        uint32_t key = spread3(f[0] >> shift) | (spread3(f[1] >> shift) << 1) | (spread3(f[2] >> shift) << 2);
-        if (ts.general) {  // start and end column first: a warp's templates cover the same columns
-            uint32_t t[3];
-            draw_times(ts.seed, ts.offset + i, om.n_t, (uint32_t)ts.t_min, t);
-            key |= (((t[0] >> om.tshift) << 4) | (t[2] >> om.tshift)) << 12;
+    int lo = 0, hi = a.n_maps - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if ((uint64_t)omap(a, mid).pos0 <= p) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Block b's share of all positions.
+__device__ __forceinline__ void block_range(const OrderArgs &a, uint64_t &p0, uint64_t &p1)
+{
+    const uint64_t chunk = (a.total_n + a.grid - 1) / a.grid;
+    p0 = (uint64_t)blockIdx.x * chunk;
+    p1 = p0 + chunk < a.total_n ? p0 + chunk : a.total_n;
+}
+
+// Key of one template: Morton code of its control bins (general templates: the
+// start and end column above them), split into coarse bucket and fine bits.
+template <bool GENERAL>
+__device__ __forceinline__ uint32_t template_key(const TrackSet &ts, uint64_t g, uint32_t n_f, uint32_t n_t, int shift,
+                                                 int tshift, int fbits, uint32_t coarse0)
+{
+    uint32_t f[3];
+    double tau;
+    draw_track_ts(ts, g, n_f, f, tau);
+    uint32_t key = spread3(f[0] >> shift) | (spread3(f[1] >> shift) << 1) | (spread3(f[2] >> shift) << 2);
+    if (GENERAL) {  // start and end column first: a warp's templates cover the same columns
+        uint32_t t[3];
+        draw_times(ts.seed, g, n_t, (uint32_t)ts.t_min, t);
+        key |= (((t[0] >> tshift) << 4) | (t[2] >> tshift)) << 12;
+    }
+    const uint32_t c = coarse0 + (key >> fbits);
+    return (c << kFineShift) | (key & ((1u << fbits) - 1u));
+}
+
+// MULTI: several maps (else a.single); GENERAL: general templates (else pinned).
+template <bool MULTI, bool GENERAL>
+__global__ void __launch_bounds__(kKeyThreads, 2) order_keys_kernel(OrderArgs a, uint32_t *__restrict__ keys,
+                                                                    uint32_t *__restrict__ blockhist)
+{
+    extern __shared__ uint32_t hc[];  // [nc]
+    for (uint32_t c = threadIdx.x; c < a.nc; c += blockDim.x) hc[c] = 0;
+    __syncthreads();
+    uint64_t q0, q1;
+    block_range(a, q0, q1);
+    const uint32_t p0 = (uint32_t)q0, p1 = (uint32_t)q1;  // positions are below 2^32
+    if (MULTI) {
+        if (p0 + threadIdx.x < p1) {
+            int mi = map_of(a, p0 + threadIdx.x);
+            for (uint32_t p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
+                while (mi + 1 < a.n_maps && a.maps[mi + 1].pos0 <= p) ++mi;
+                const OrderMap &om = a.maps[mi];
+                const uint32_t k = template_key<GENERAL>(om.ts, om.ts.offset + (p - om.pos0), om.n_f, om.n_t,
+                                                         om.shift, om.tshift, om.fbits, om.coarse0);
+                keys[p] = k;
+                atomicAdd(&hc[k >> kFineShift], 1u);
+            }
         }
-        key += bucket0;
-        keys[pos0 + i] = key;
-        atomicAdd(&hist[key], 1u);
+    } else {
+        const OrderMap &om = a.single;  // read from the parameters where used
+        for (uint32_t p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
+            const uint32_t k = template_key<GENERAL>(om.ts, om.ts.offset + p, om.n_f, om.n_t, om.shift, om.tshift,
+                                                     om.fbits, 0u);
+            keys[p] = k;
+            atomicAdd(&hc[k >> kFineShift], 1u);
+        }
+    }
+    __syncthreads();
+    for (uint32_t c = threadIdx.x; c < a.nc; c += blockDim.x) blockhist[(size_t)blockIdx.x * a.nc + c] = hc[c];
+}
+
+// blockhist[b][c] becomes, for each coarse bucket c, the exclusive prefix over
+// blocks b; total[c] the bucket's size.  A block takes 32 buckets (one per lane)
+// and its 32 warps a share of the blocks each: warp sums, a scan over warps,
+// then each warp writes its share's prefixes.
+__global__ void __launch_bounds__(1024) order_columns_kernel(uint32_t *__restrict__ blockhist, uint32_t nc,
+                                                             int grid, uint32_t *__restrict__ total)
+{
+    __shared__ uint32_t part[32][33];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const uint32_t c = blockIdx.x * 32 + lane;
+    const int per = (grid + 31) / 32, b0 = w * per, b1 = min(grid, b0 + per);
+    uint32_t sum = 0;
+    if (c < nc)
+        for (int b = b0; b < b1; ++b) sum += blockhist[(size_t)b * nc + c];
+    part[w][lane] = sum;
+    __syncthreads();
+    uint32_t before = 0, all = 0;
+    for (int k = 0; k < 32; ++k) {
+        const uint32_t v = part[k][lane];
+        if (k < w) before += v;
+        all += v;
+    }
+    if (c < nc) {
+        for (int b = b0; b < b1; ++b) {
+            uint32_t *e = blockhist + (size_t)b * nc + c;
+            const uint32_t v = *e;
+            *e = before;
+            before += v;
+        }
+        if (w == 0) total[c] = all;
     }
 }
 
-__device__ __forceinline__ uint32_t block_sum(uint32_t v, uint32_t *red)
+// base[c] = exclusive prefix of total over coarse buckets; one block.
+__global__ void __launch_bounds__(1024) order_bases_kernel(const uint32_t *__restrict__ total, uint32_t nc,
+                                                           uint32_t *__restrict__ base)
 {
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    __syncthreads();
-    if (l == 0) red[w] = v;
-    __syncthreads();
-    uint32_t t = 0;
-    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += red[k];
-    return t;
-}
-
-// Exclusive scan of each thread's `run` over the block (warp scans, then warp bases).
-__device__ __forceinline__ uint32_t block_exclusive(uint32_t run, uint32_t *wsum)
-{
+    __shared__ uint32_t wsum[32];
+    const uint32_t per = (nc + blockDim.x - 1) / blockDim.x;
+    const uint32_t c0 = threadIdx.x * per;
+    uint32_t run = 0;
+    for (uint32_t q = 0; q < per && c0 + q < nc; ++q) run += total[c0 + q];
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
     uint32_t inc = run;
     for (int o = 1; o < 32; o <<= 1) {
@@ -104,69 +189,108 @@ __device__ __forceinline__ uint32_t block_exclusive(uint32_t run, uint32_t *wsum
     }
     if (l == 31) wsum[w] = inc;
     __syncthreads();
-    uint32_t wb = 0;
-    for (int k = 0; k < w; ++k) wb += wsum[k];
-    return wb + inc - run;
+    uint32_t acc = inc - run;
+    for (int k = 0; k < w; ++k) acc += wsum[k];
+    for (uint32_t q = 0; q < per && c0 + q < nc; ++q) {
+        base[c0 + q] = acc;
+        acc += total[c0 + q];
+    }
 }
 
-__global__ void __launch_bounds__(kScanThreads) order_tiles_kernel(const uint32_t *__restrict__ hist, uint32_t nb,
-                                                                   uint32_t *__restrict__ tilesum)
+// Each block places its positions into their coarse buckets: tmp[slot] = fine << 32 | position.
+__global__ void __launch_bounds__(kKeyThreads) order_coarse_kernel(OrderArgs a, const uint32_t *__restrict__ keys,
+                                                                   const uint32_t *__restrict__ blockhist,
+                                                                   const uint32_t *__restrict__ base,
+                                                                   unsigned long long *__restrict__ tmp)
 {
-    __shared__ uint32_t red[kScanThreads / 32];
-    const uint32_t base = blockIdx.x * kTile;
-    uint32_t v = 0;
-    for (uint32_t k = threadIdx.x; k < kTile && base + k < nb; k += kScanThreads) v += hist[base + k];
-    const uint32_t t = block_sum(v, red);
-    if (threadIdx.x == 0) tilesum[blockIdx.x] = t;
+    extern __shared__ uint32_t ctr[];  // [nc]
+    for (uint32_t c = threadIdx.x; c < a.nc; c += blockDim.x)
+        ctr[c] = base[c] + blockhist[(size_t)blockIdx.x * a.nc + c];
+    __syncthreads();
+    uint64_t p0, p1;
+    block_range(a, p0, p1);
+    for (uint64_t p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
+        const uint32_t key = keys[p];
+        const uint32_t slot = atomicAdd(&ctr[key >> kFineShift], 1u);
+        tmp[slot] = ((unsigned long long)(key & ((1u << kFineShift) - 1u)) << 32) | (uint32_t)p;
+    }
 }
 
-// tilesum[] (counts) becomes the exclusive prefix over tiles; one block.
-__global__ void __launch_bounds__(kBaseThreads) order_bases_kernel(uint32_t *__restrict__ tilesum, uint32_t ntiles)
+// One block per coarse bucket: counting sort by the fine key bits; perm[pos] =
+// the template's index within its map.
+__global__ void __launch_bounds__(kFineThreads) order_fine_kernel(OrderArgs a,
+                                                                  const unsigned long long *__restrict__ tmp,
+                                                                  const uint32_t *__restrict__ base,
+                                                                  const uint32_t *__restrict__ total,
+                                                                  uint32_t *__restrict__ perm)
 {
-    __shared__ uint32_t wsum[kBaseThreads / 32];
-    const uint32_t per = (ntiles + kBaseThreads - 1) / kBaseThreads;
-    const uint32_t b0 = threadIdx.x * per;
+    extern __shared__ uint32_t hf[];  // [2^fbits]
+    __shared__ uint32_t wsum[kFineThreads / 32];
+    const uint32_t c = blockIdx.x;
+    const uint32_t n = total[c];
+    if (n == 0) return;
+    // the bucket's map: the last one whose first coarse bucket is <= c
+    int lo = 0, hi = a.n_maps - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (omap(a, mid).coarse0 <= c) lo = mid;
+        else hi = mid - 1;
+    }
+    const OrderMap &om = omap(a, lo);
+    const uint32_t nb = 1u << om.fbits, pos0 = om.pos0, b0 = base[c];
+    for (uint32_t i = threadIdx.x; i < nb; i += blockDim.x) hf[i] = 0;
+    __syncthreads();
+    // buckets of up to kFineCache elements stay in registers between the two passes
+    constexpr int kPer = kFineCache / kFineThreads;
+    const bool cached = n <= (uint32_t)kFineCache;
+    unsigned long long r[kPer];
+    if (cached) {
+#pragma unroll
+        for (int u = 0; u < kPer; ++u) {
+            const uint32_t i = threadIdx.x + u * kFineThreads;
+            r[u] = i < n ? tmp[b0 + i] : 0ull;
+            if (i < n) atomicAdd(&hf[(uint32_t)(r[u] >> 32)], 1u);
+        }
+    } else {
+        for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) atomicAdd(&hf[(uint32_t)(tmp[b0 + i] >> 32)], 1u);
+    }
+    __syncthreads();
+    // exclusive scan of hf: each thread a contiguous run of bins
+    const uint32_t per = (nb + blockDim.x - 1) / blockDim.x;
+    const uint32_t f0 = threadIdx.x * per;
     uint32_t run = 0;
-    for (uint32_t q = 0; q < per && b0 + q < ntiles; ++q) run += tilesum[b0 + q];
-    uint32_t acc = block_exclusive(run, wsum);
-    for (uint32_t q = 0; q < per && b0 + q < ntiles; ++q) {
-        const uint32_t c = tilesum[b0 + q];
-        tilesum[b0 + q] = acc;
-        acc += c;
+    for (uint32_t q = 0; q < per && f0 + q < nb; ++q) run += hf[f0 + q];
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    uint32_t inc = run;
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (l >= o) inc += y;
     }
-}
-
-// hist[] (counts) becomes the exclusive prefix over all buckets.
-__global__ void __launch_bounds__(kScanThreads) order_scan_kernel(uint32_t *__restrict__ hist, uint32_t nb,
-                                                                  const uint32_t *__restrict__ tilebase)
-{
-    __shared__ uint32_t wsum[kScanThreads / 32];
-    constexpr int per = kTile / kScanThreads;
-    const uint32_t b0 = blockIdx.x * kTile + threadIdx.x * per;
-    uint32_t c[per], run = 0;
+    if (l == 31) wsum[w] = inc;
+    __syncthreads();
+    uint32_t acc = inc - run;
+    for (int k = 0; k < w; ++k) acc += wsum[k];
+    for (uint32_t q = 0; q < per && f0 + q < nb; ++q) {
+        const uint32_t v = hf[f0 + q];
+        hf[f0 + q] = acc;
+        acc += v;
+    }
+    __syncthreads();
+    if (cached) {
 #pragma unroll
-    for (int q = 0; q < per; ++q) {
-        c[q] = (b0 + q < nb) ? hist[b0 + q] : 0u;
-        run += c[q];
+        for (int u = 0; u < kPer; ++u) {
+            const uint32_t i = threadIdx.x + u * kFineThreads;
+            if (i < n) {
+                const uint32_t q = atomicAdd(&hf[(uint32_t)(r[u] >> 32)], 1u);
+                perm[b0 + q] = (uint32_t)r[u] - pos0;
+            }
+        }
+        return;
     }
-    uint32_t acc = tilebase[blockIdx.x] + block_exclusive(run, wsum);
-#pragma unroll
-    for (int q = 0; q < per; ++q) {
-        if (b0 + q < nb) hist[b0 + q] = acc;
-        acc += c[q];
-    }
-}
-
-__global__ void order_scatter_kernel(OrderArgs a, const uint32_t *__restrict__ keys, uint32_t *__restrict__ offs,
-                                     uint32_t *__restrict__ perm)
-{
-    const OrderMap &om = order_map(a);
-    const uint64_t n = om.ts.n;
-    const uint32_t pos0 = om.pos0;
-    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        const uint32_t pos = atomicAdd(&offs[keys[pos0 + i]], 1u);
-        perm[pos] = (uint32_t)i;
+    for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
+        const unsigned long long e = tmp[b0 + i];
+        const uint32_t q = atomicAdd(&hf[(uint32_t)(e >> 32)], 1u);
+        perm[b0 + q] = (uint32_t)e - pos0;
     }
 }
 
@@ -180,29 +304,107 @@ int bit_length(uint32_t x)
     return b;
 }
 
-cudaError_t run_order(const OrderArgs &oa, int n_maps, uint64_t max_n, uint64_t total_n, uint64_t nb,
-                      void *scratch, int num_sms, cudaStream_t st, const uint32_t **perm_out, int *launches)
+struct Layout {
+    uint32_t *keys, *perm, *blockhist, *total, *base;
+    unsigned long long *tmp;
+};
+
+size_t align256(size_t x) { return (x + 255) / 256 * 256; }
+
+// Scratch layout (and its size): tmp[n] u64, keys[n], perm[n], blockhist[grid][nc], total[nc], base[nc].
+size_t layout_bytes(uint64_t total_n, uint32_t nc, int grid, Layout *L, void *scratch)
 {
-    const uint32_t ntiles = (uint32_t)((nb + kTile - 1) / kTile);
-    uint32_t *keys = reinterpret_cast<uint32_t *>(scratch);
-    uint32_t *perm = keys + total_n;
-    uint32_t *hist = perm + total_n;
-    uint32_t *tilesum = hist + nb;
-    cudaError_t e = cudaMemsetAsync(hist, 0, (size_t)nb * sizeof(uint32_t), st);
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t o = off;
+        off += align256(bytes);
+        return o;
+    };
+    const size_t o_tmp = take(total_n * 8), o_keys = take(total_n * 4), o_perm = take(total_n * 4);
+    const size_t o_bh = take((size_t)nc * grid * 4), o_tot = take((size_t)nc * 4), o_base = take((size_t)nc * 4);
+    if (L) {
+        unsigned char *s = static_cast<unsigned char *>(scratch);
+        L->tmp = reinterpret_cast<unsigned long long *>(s + o_tmp);
+        L->keys = reinterpret_cast<uint32_t *>(s + o_keys);
+        L->perm = reinterpret_cast<uint32_t *>(s + o_perm);
+        L->blockhist = reinterpret_cast<uint32_t *>(s + o_bh);
+        L->total = reinterpret_cast<uint32_t *>(s + o_tot);
+        L->base = reinterpret_cast<uint32_t *>(s + o_base);
+    }
+    return off;
+}
+
+cudaError_t run_order(const OrderArgs &oa, uint32_t max_fbits, void *scratch, cudaStream_t st,
+                      const uint32_t **perm_out, int *launches)
+{
+    Layout L;
+    layout_bytes(oa.total_n, oa.nc, oa.grid, &L, scratch);
+    const size_t smem_c = (size_t)oa.nc * 4, smem_f = (size_t)4 << max_fbits;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(st, &cs);
     if (e != cudaSuccess) return e;
-    const int threads = 256;
-    // about 8 blocks per SM over all maps
-    const uint64_t want = std::max<uint64_t>(1, std::min<uint64_t>((max_n + threads - 1) / threads,
-                                                                    (uint64_t)num_sms * 8 / (uint64_t)n_maps + 1));
-    const dim3 grid((unsigned)want, (unsigned)n_maps);
-    order_keys_kernel<<<grid, threads, 0, st>>>(oa, keys, hist);
-    order_tiles_kernel<<<ntiles, kScanThreads, 0, st>>>(hist, (uint32_t)nb, tilesum);
-    order_bases_kernel<<<1, kBaseThreads, 0, st>>>(tilesum, ntiles);
-    order_scan_kernel<<<ntiles, kScanThreads, 0, st>>>(hist, (uint32_t)nb, tilesum);
-    order_scatter_kernel<<<grid, threads, 0, st>>>(oa, keys, hist, perm);
-    *perm_out = perm;
-    if (launches) *launches = 6;
+    if (cs == cudaStreamCaptureStatusNone && (e = order_prepare(oa.nc, max_fbits)) != cudaSuccess) return e;
+    // batches hold pinned templates only; one map may hold either kind
+    if (oa.maps)
+        order_keys_kernel<true, false><<<oa.grid, kKeyThreads, smem_c, st>>>(oa, L.keys, L.blockhist);
+    else if (oa.single.ts.general)
+        order_keys_kernel<false, true><<<oa.grid, kKeyThreads, smem_c, st>>>(oa, L.keys, L.blockhist);
+    else
+        order_keys_kernel<false, false><<<oa.grid, kKeyThreads, smem_c, st>>>(oa, L.keys, L.blockhist);
+    order_columns_kernel<<<(oa.nc + 31) / 32, 1024, 0, st>>>(L.blockhist, oa.nc, oa.grid, L.total);
+    order_bases_kernel<<<1, 1024, 0, st>>>(L.total, oa.nc, L.base);
+    order_coarse_kernel<<<oa.grid, kKeyThreads, smem_c, st>>>(oa, L.keys, L.blockhist, L.base, L.tmp);
+    order_fine_kernel<<<oa.nc, kFineThreads, smem_f, st>>>(oa, L.tmp, L.base, L.total, L.perm);
+    *perm_out = L.perm;
+    if (launches) *launches = 5;
     return cudaGetLastError();
+}
+
+int order_grid(int num_sms) { return 2 * std::max(1, num_sms); }
+
+}  // namespace
+
+// Shared-memory limits of the order kernels on the current device (not while a
+// stream is being captured: batches call this before capturing their graph).
+cudaError_t order_prepare(uint32_t nc, uint32_t max_fbits)
+{
+    const int smem_c = (int)nc * 4, smem_f = 4 << max_fbits;
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(order_keys_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  smem_c)) != cudaSuccess ||
+        (e = cudaFuncSetAttribute(order_keys_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  smem_c)) != cudaSuccess ||
+        (e = cudaFuncSetAttribute(order_keys_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  smem_c)) != cudaSuccess ||
+        (e = cudaFuncSetAttribute(order_keys_kernel<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  smem_c)) != cudaSuccess ||
+        (e = cudaFuncSetAttribute(order_coarse_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_c)) !=
+            cudaSuccess ||
+        (e = cudaFuncSetAttribute(order_fine_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_f)) !=
+            cudaSuccess)
+        return e;
+    return cudaSuccess;
+}
+
+namespace {
+
+// Single map: the key's top 12 bits (or all, if fewer) are the coarse bucket.
+void single_plan(const MapDev &m, const TrackSet &ts, OrderMap &om, uint32_t &nc)
+{
+    om = OrderMap{};
+    om.ts = ts;
+    om.n_f = (uint32_t)m.n_f;
+    om.n_t = (uint32_t)m.n_t;
+    int bits, tbits;
+    order_shape(m.n_f, ts.general ? 4 : 7, om.shift, bits);
+    order_shape(m.n_t, 4, om.tshift, tbits);
+    // general keys place the time bits at bit 12 whatever the bin bits in use
+    const int kb = ts.general ? 20 : 3 * bits;
+    const int cb = std::min(kb, 12);
+    om.fbits = kb - cb;
+    om.coarse0 = 0;
+    om.pos0 = 0;
+    nc = 1u << cb;
 }
 
 }  // namespace
@@ -214,20 +416,45 @@ void order_shape(int n_f, int max_bits, int &shift, int &bits)
     shift = b - bits;
 }
 
-size_t order_scratch_bytes_total(uint64_t total_n, uint64_t total_buckets)
+void order_plan_maps(OrderMap *maps, int n_maps, uint32_t &nc, uint32_t &max_fbits)
 {
-    const uint64_t ntiles = (total_buckets + kTile - 1) / kTile;
-    return (size_t)(2 * total_n + total_buckets + ntiles) * sizeof(uint32_t) + 256;
+    // coarse bits per map so that all maps together have at most kMaxCoarse
+    // buckets; at most 14 fine bits, which bounds the bits per control bin
+    int cbits = 12;
+    while (cbits > 0 && ((uint64_t)n_maps << cbits) > kMaxCoarse) --cbits;
+    const int max_bits = std::min(7, (kFineShift + cbits) / 3);
+    nc = 0;
+    max_fbits = 0;
+    for (int i = 0; i < n_maps; ++i) {
+        OrderMap &om = maps[i];
+        int bits, tbits;
+        order_shape((int)om.n_f, om.ts.general ? std::min(4, max_bits) : max_bits, om.shift, bits);
+        order_shape((int)om.n_t, 4, om.tshift, tbits);
+        const int kb = om.ts.general ? 20 : 3 * bits;
+        const int cb = std::min(kb, cbits);
+        om.fbits = kb - cb;
+        om.coarse0 = nc;
+        nc += 1u << cb;
+        max_fbits = std::max<uint32_t>(max_fbits, (uint32_t)om.fbits);
+    }
 }
 
-// Pinned templates: 7 bits per control bin (2^21 buckets).  General templates:
-// 4 bits each of the start and end column, then 4 bits per control bin (2^20).
-size_t order_scratch_bytes(uint64_t n, int n_f, bool general)
+size_t order_scratch_bytes_maps(uint64_t total_n, uint32_t nc, int num_sms)
 {
-    int shift, bits;
-    order_shape(n_f, 7, shift, bits);
-    // general keys place the time bits at bit 12 whatever the bin bits in use
-    return order_scratch_bytes_total(n, general ? (1ull << 20) : (1ull << (3 * bits)));
+    return layout_bytes(total_n, nc, order_grid(num_sms), nullptr, nullptr);
+}
+
+size_t order_scratch_bytes(uint64_t n, int n_f, int n_t, bool general, int num_sms)
+{
+    MapDev m{};
+    m.n_f = n_f;
+    m.n_t = n_t;
+    TrackSet ts{};
+    ts.general = general ? 1 : 0;
+    OrderMap om;
+    uint32_t nc;
+    single_plan(m, ts, om, nc);
+    return layout_bytes(n, nc, order_grid(num_sms), nullptr, nullptr);
 }
 
 cudaError_t launch_order(const MapDev &m, const TrackSet &ts, void *scratch, int num_sms, cudaStream_t st,
@@ -235,26 +462,24 @@ cudaError_t launch_order(const MapDev &m, const TrackSet &ts, void *scratch, int
 {
     OrderArgs oa{};
     oa.maps = nullptr;
-    oa.single.ts = ts;
-    oa.single.n_f = (uint32_t)m.n_f;
-    int bits, tbits;
-    order_shape(m.n_f, ts.general ? 4 : 7, oa.single.shift, bits);
-    order_shape(m.n_t, 4, oa.single.tshift, tbits);
-    oa.single.n_t = (uint32_t)m.n_t;
-    oa.single.bucket0 = 0;
-    oa.single.pos0 = 0;
-    // general keys place the time bits at bit 12 whatever the bin bits in use
-    const uint64_t nb = ts.general ? (1ull << 20) : (1ull << (3 * bits));
-    return run_order(oa, 1, ts.n, ts.n, nb, scratch, num_sms, st, perm_out, launches);
+    single_plan(m, ts, oa.single, oa.nc);
+    oa.n_maps = 1;
+    oa.total_n = ts.n;
+    oa.grid = order_grid(num_sms);
+    return run_order(oa, (uint32_t)oa.single.fbits, scratch, st, perm_out, launches);
 }
 
-cudaError_t launch_order_batch(const OrderMap *d_maps, int n_maps, uint64_t max_n, uint64_t total_n,
-                               uint64_t total_buckets, void *scratch, int num_sms, cudaStream_t st,
-                               const uint32_t **perm_out, int *launches)
+cudaError_t launch_order_batch(const OrderMap *d_maps, int n_maps, uint64_t total_n, uint32_t nc, uint32_t max_fbits,
+                               void *scratch, int num_sms, cudaStream_t st, const uint32_t **perm_out,
+                               int *launches)
 {
     OrderArgs oa{};
     oa.maps = d_maps;
-    return run_order(oa, n_maps, max_n, total_n, total_buckets, scratch, num_sms, st, perm_out, launches);
+    oa.n_maps = n_maps;
+    oa.total_n = total_n;
+    oa.nc = nc;
+    oa.grid = order_grid(num_sms);
+    return run_order(oa, max_fbits, scratch, st, perm_out, launches);
 }
 
 }  // namespace stk
