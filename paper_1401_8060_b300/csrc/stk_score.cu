@@ -6,15 +6,19 @@
 // Two kernels compute the same per-template arithmetic in the same order:
 //   score_simple  one thread per template, pixels read from the L2-resident map;
 //                 used for explicit templates, small jobs and maps whose
-//                 rasteriser needs 64-bit numerators.
+//                 rasteriser needs 64-bit numerators or whose phase needs the
+//                 64-bit form (n_f > 8192).
 //   score_staged  persistent CTAs; each CTA holds a batch of R * blockDim
-//                 templates in registers and streams the map through shared
-//                 memory in slabs of S time columns (one bulk copy per slab,
-//                 double-buffered on mbarriers), so every gathered pixel is a
-//                 shared-memory load.  The map is read from L2 once per batch.
+//                 templates in registers (in coherent order, stk_order.cu) and
+//                 streams the map through shared memory in slabs of S time
+//                 columns (one bulk copy per slab, two buffers on mbarriers,
+//                 refilled by the last warp to finish them), so every gathered
+//                 pixel is a shared-memory load.  The map is read from L2 once
+//                 per batch.
 // Both come in two storage precisions (PREC): 8-byte FP32 polar records, or
 // 4-byte records holding |y|/sigma in FP16 and the phase in Q0.16 turns, the
 // per-frequency (or per-pixel) scale 1/sigma then doubling as the weight.
+// General templates (random control times) have their own one-thread kernel.
 #include <cuda_fp16.h>
 
 #include <algorithm>

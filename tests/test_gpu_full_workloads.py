@@ -132,3 +132,31 @@ def test_general_templates_benchmark_size(ctx, realistic):
     print(f"general templates: max |dSNR| / scale = {np.max(err / sc):.3g}")
     assert_topk_matches(hits, o, 0, k, what="general templates top-k")
     m.close()
+
+
+def test_large_template_count(ctx):
+    """3e8 templates in one call (positions and the order's 32-bit indices near
+    their range's upper part; 2.4 GB of SNRs, 4.8 GB of order scratch): the k
+    loudest are exactly the top of the GPU's own SNR array, and a sample of
+    templates plus every selected one agree with the oracle."""
+    n_t, n_f, T, k = 40, 300, 300_000_000, 64
+    sig = synth.sigma_powerlaw(40.0 + 0.5 * np.arange(n_f), 1.1)
+    y = synth.noise_map(n_t, n_f, sig, 91)
+    m = ctx.load_map(torch.from_numpy(y).cuda(), torch.from_numpy(sig).cuda(), 40.0, 0.5)
+    ctx.set_tracks(T, 8, 7, 0.01)
+    hits = ctx.score(m, k)
+    assert ctx.last_plan()["order"] == 1
+    g = ctx.score_all(m)
+    top_v, top_i = torch.sort(g, descending=True, stable=True)
+    np.testing.assert_array_equal(hits["snr"], top_v[:k].cpu().numpy())
+    np.testing.assert_array_equal(hits["index"], top_i[:k].cpu().numpy() + 7)
+    rng = np.random.default_rng(92)
+    idx = np.unique(np.concatenate([rng.integers(0, T, 3000), top_i[:k].cpu().numpy()]))
+    gs = g[torch.from_numpy(idx).cuda()].cpu().numpy()
+    del g, top_v, top_i
+    pr = [oracle.track_params(8, 7 + int(i), n_f, 0.01) for i in idx]
+    om = oracle.OracleMap(y, sig, 40.0, 0.5, True)
+    o, ex = om.score_explicit(np.array([p[0] for p in pr], np.uint32), np.array([p[1] for p in pr]), extras=True)
+    sc = ex["absz"] / np.sqrt(ex["W"])
+    assert np.all(np.abs(gs - o) <= RTOL * np.maximum(np.abs(o), sc))
+    m.close()
