@@ -111,14 +111,13 @@ __global__ void __launch_bounds__(kKeyThreads, 2) order_keys_kernel(OrderArgs a,
     extern __shared__ uint32_t hc[];  // [nc]
     for (uint32_t c = threadIdx.x; c < a.nc; c += blockDim.x) hc[c] = 0;
     __syncthreads();
-    uint64_t q0, q1;
-    block_range(a, q0, q1);
-    const uint32_t p0 = (uint32_t)q0, p1 = (uint32_t)q1;  // positions are below 2^32
+    uint64_t p0, p1;  // 64-bit: positions reach 2^32 - 1, the loop steps past them
+    block_range(a, p0, p1);
     if (MULTI) {
         if (p0 + threadIdx.x < p1) {
             int mi = map_of(a, p0 + threadIdx.x);
-            for (uint32_t p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
-                while (mi + 1 < a.n_maps && a.maps[mi + 1].pos0 <= p) ++mi;
+            for (uint64_t p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
+                while (mi + 1 < a.n_maps && (uint64_t)a.maps[mi + 1].pos0 <= p) ++mi;
                 const OrderMap &om = a.maps[mi];
                 const uint32_t k = template_key<GENERAL>(om.ts, om.ts.offset + (p - om.pos0), om.n_f, om.n_t,
                                                          om.shift, om.tshift, om.fbits, om.coarse0);
@@ -128,7 +127,7 @@ __global__ void __launch_bounds__(kKeyThreads, 2) order_keys_kernel(OrderArgs a,
         }
     } else {
         const OrderMap &om = a.single;  // read from the parameters where used
-        for (uint32_t p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
+        for (uint64_t p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
             const uint32_t k = template_key<GENERAL>(om.ts, om.ts.offset + p, om.n_f, om.n_t, om.shift, om.tshift,
                                                      om.fbits, 0u);
             keys[p] = k;
@@ -252,7 +251,8 @@ __global__ void __launch_bounds__(kFineThreads) order_fine_kernel(OrderArgs a,
             if (i < n) atomicAdd(&hf[(uint32_t)(r[u] >> 32)], 1u);
         }
     } else {
-        for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) atomicAdd(&hf[(uint32_t)(tmp[b0 + i] >> 32)], 1u);
+        for (uint64_t i = threadIdx.x; i < n; i += blockDim.x)
+            atomicAdd(&hf[(uint32_t)(tmp[(uint64_t)b0 + i] >> 32)], 1u);
     }
     __syncthreads();
     // exclusive scan of hf: each thread a contiguous run of bins
@@ -287,10 +287,10 @@ __global__ void __launch_bounds__(kFineThreads) order_fine_kernel(OrderArgs a,
         }
         return;
     }
-    for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
-        const unsigned long long e = tmp[b0 + i];
+    for (uint64_t i = threadIdx.x; i < n; i += blockDim.x) {  // 64-bit: n may approach 2^32
+        const unsigned long long e = tmp[(uint64_t)b0 + i];
         const uint32_t q = atomicAdd(&hf[(uint32_t)(e >> 32)], 1u);
-        perm[b0 + q] = (uint32_t)e - pos0;
+        perm[(uint64_t)b0 + q] = (uint32_t)e - pos0;
     }
 }
 

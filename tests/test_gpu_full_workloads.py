@@ -160,3 +160,26 @@ def test_large_template_count(ctx):
     sc = ex["absz"] / np.sqrt(ex["W"])
     assert np.all(np.abs(gs - o) <= RTOL * np.maximum(np.abs(o), sc))
     m.close()
+
+
+def test_maximum_template_count():
+    """The largest range one call accepts, 2^32 - 1 templates (34 GB of SNRs,
+    68 GB of order scratch), on a 4 x 64 map: the k loudest are distinct, in
+    range and sorted, and each one's SNR is the oracle's."""
+    n_t, n_f, T, k, off = 4, 64, 2**32 - 1, 16, 11
+    ctx = stk.Context(0)                       # its 100 GB of scratch go with it
+    sig = np.full(n_f, 1.0, np.float32)
+    y = synth.noise_map(n_t, n_f, sig, 93)
+    m = ctx.load_map(torch.from_numpy(y).cuda(), torch.from_numpy(sig).cuda(), 40.0, 0.5)
+    ctx.set_tracks(T, 9, off, 0.01)
+    hits = ctx.score(m, k)
+    assert ctx.last_plan()["kernel"] == 2 and ctx.last_plan()["order"] == 1
+    idx = hits["index"].astype(np.int64)
+    assert len(set(idx.tolist())) == k and idx.min() >= off and idx.max() < off + T
+    assert np.all(np.diff(hits["snr"]) <= 0)
+    pr = [oracle.track_params(9, int(i), n_f, 0.01) for i in idx]
+    om = oracle.OracleMap(y, sig, 40.0, 0.5, True)
+    o = om.score_explicit(np.array([p[0] for p in pr], np.uint32), np.array([p[1] for p in pr]))
+    np.testing.assert_allclose(hits["snr"], o, rtol=RTOL)
+    m.close()
+    ctx.close()
