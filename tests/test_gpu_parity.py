@@ -469,6 +469,26 @@ def test_update_map_invalid_data_reported(ctx):
     mc.close()
 
 
+@pytest.mark.parametrize("kernel", [0, 1, 2])
+def test_single_template(ctx, kernel):
+    """One template (the smallest range): both kernels, with and without the
+    coherent order, give the oracle's SNR at its index."""
+    y, sig = rand_map(67, 30, 50, "freq")
+    m, om = load_both(ctx, y, sig, 40.0, 0.5)
+    ctx.set_tracks(1, 3, 12345, 0.01)
+    ctx.set_option(_lib.STK_OPT_KERNEL, kernel)
+    try:
+        h = ctx.score(m, 1)
+        a = ctx.score_all(m).cpu().numpy()
+    finally:
+        ctx.set_option(_lib.STK_OPT_KERNEL, 0)
+    f3, tau = oracle_params(3, 12345, 1, 50, 0.01)
+    o, ex = om.score_explicit(f3, tau, extras=True)
+    assert int(h["index"][0]) == 12345 and a.shape == (1,)
+    assert_snr_close(a, o, ex, False, 30, what="single template")
+    assert h["snr"][0] == a[0]
+
+
 def test_invalid_inputs_rejected(ctx):
     L = _lib
     y = np.ones((10, 8), np.complex64)
