@@ -98,7 +98,8 @@ STK_API int stk_set_stream(stk_ctx *ctx, void *cuda_stream);
  *   default         SNR = sum_j Re[e^{2 pi i f_j tau} y_j sigma_j^-2] / sqrt(sum_j sigma_j^-2)
  *   STK_NORM_PAPER  SNR = (1/n_t) sum_j Re[e^{2 pi i f_j tau} y_j / sigma_j]
  * Arithmetic: pixel magnitude and phase stored FP32 and Q0.32 turns (FP16 and
- * Q0.16 with STK_FP16), sums FP32, normalisation FP64.  The delay phase
+ * Q0.16 with STK_FP16), sums and normalisation FP32 (square root and
+ * division rounded to nearest); the SNR is reported widened to FP64.  The delay phase
  * f tau mod 1 is exact in 64-bit fixed point per template; per pixel it is a
  * 32-bit turn, within 3e-6 rad for n_f <= 8192 (2^-32 turn beyond).
  * The library keeps its own packed copy; the caller may free y and sigma when
@@ -152,7 +153,8 @@ STK_API int stk_score(stk_ctx *ctx, const stk_map *map, int k, stk_hit *out_topk
 
 /* Score every template of the current range and write its SNR (Eq. 7) to
  * out_snr_dev[i] for template counter_offset + i; caller-owned device buffer
- * of n_tracks doubles.  Errors: STK_EINVAL, STK_ESTATE, STK_ECUDA. */
+ * of n_tracks doubles (the FP32 SNRs widened; 4 bytes per template of
+ * context scratch).  Errors: STK_EINVAL, STK_ESTATE, STK_ENOMEM, STK_ECUDA. */
 STK_API int stk_score_all(stk_ctx *ctx, const stk_map *map, double *out_snr_dev);
 
 /* Parameters of template g as the scoring kernels draw them (Sec. III):
@@ -165,9 +167,10 @@ STK_API int stk_track_params(stk_ctx *ctx, const stk_map *map, uint64_t g, uint3
 
 /* Score n explicit templates (Eq. 7): f3_dev [n][3] control bins (each < n_f),
  * tau_dev [n] delays in seconds; SNRs to out_snr_dev [n].  All device
- * pointers, caller-owned.  Bins outside [0, n_f) are clamped to the map edge
- * after the out-of-range template is flagged: the call then returns
- * STK_EINVAL at the next stk_sync.  Errors: STK_EINVAL, STK_ECUDA. */
+ * pointers, caller-owned (4 bytes per template of context scratch).  Bins
+ * outside [0, n_f) are clamped to the map edge after the out-of-range
+ * template is flagged: the call then returns STK_EINVAL at the next
+ * stk_sync.  Errors: STK_EINVAL, STK_ENOMEM, STK_ECUDA. */
 STK_API int stk_score_explicit(stk_ctx *ctx, const stk_map *map, const uint32_t *f3_dev, const double *tau_dev,
                        uint64_t n, double *out_snr_dev);
 
@@ -204,8 +207,9 @@ STK_API int stk_track_times(stk_ctx *ctx, const stk_map *map, uint64_t g, uint32
 
 /* Score n explicit general templates: t3_dev [n][3] control times (t0 <= t1 <=
  * t2 < n_t, t0 < t2), f3_dev [n][3] control bins (< n_f), tau_dev [n] delays;
- * SNRs to out_snr_dev [n]; device pointers.  Invalid templates are flagged
- * (STK_EINVAL at the next stk_sync).  Errors: STK_EINVAL, STK_ECUDA. */
+ * SNRs to out_snr_dev [n]; device pointers (4 bytes per template of context
+ * scratch).  Invalid templates are flagged (STK_EINVAL at the next stk_sync).
+ * Errors: STK_EINVAL, STK_ENOMEM, STK_ECUDA. */
 STK_API int stk_score_explicit_general(stk_ctx *ctx, const stk_map *map, const uint32_t *t3_dev,
                                        const uint32_t *f3_dev, const double *tau_dev, uint64_t n,
                                        double *out_snr_dev);
@@ -310,7 +314,7 @@ STK_API int stk_batch_tune(stk_batch *batch, int k, int64_t out[4]);
  * counter_offset .. counter_offset + n_tracks - 1 (seed, tau_max_s as in
  * stk_set_tracks) and writes the k loudest to out_topk_dev (caller-owned
  * device memory, k entries), asynchronously on cuda_stream.  Its scratch (one
- * SNR per template and the selection state, 9 MiB) is a fixed array
+ * FP32 SNR per template and the selection state, 5 MiB) is a fixed array
  * in device memory that every GPU loading the library holds until the process
  * exits; the call itself calls no cudaMalloc, cudaFree or other allocating
  * routine.  The map must have been loaded earlier (stk_load_map allocates).
@@ -349,7 +353,8 @@ STK_API int stk_score_noalloc(const stk_map *map, uint64_t n_tracks, uint64_t se
                               sort of the template indices by a Z-order key of (f0, f1, f2) -- so a warp's
                               pixel gathers fall in a narrow band of bins and shared-memory banks
                               rarely collide; 0 scores in index order.  Results are identical; the
-                              order costs 8 bytes per template plus 8 MiB of context scratch */
+                              order costs 16 bytes per template plus 4 bytes per coarse bucket
+                              (at most 8192) per block of 2 x SMs blocks of context scratch */
 
 /* Set a tuning option for later scoring calls.  Errors: STK_EINVAL. */
 STK_API int stk_set_option(stk_ctx *ctx, int option, int64_t value);

@@ -353,6 +353,7 @@ static int pack_into(stk_ctx *c, stk_map *m, const void *y_c64, const float *sig
     else if (d.wmode == WMODE_CONST) d.norm = fp16 ? 1.0 / std::sqrt((double)n_t)
                                                    : 1.0 / std::sqrt((double)n_t * (double)d.w_const);
     else d.norm = 0.0;
+    d.norm_f = (float)d.norm;
     d.rec = m->rec_buf;
     d.w = d.wmode == WMODE_CONST ? nullptr : (const float *)m->w_buf;
     return STK_OK;
@@ -468,7 +469,7 @@ int stk_set_tracks(stk_ctx *c, uint64_t n_tracks, uint64_t seed, uint64_t counte
     return STK_OK;
 }
 
-static int score_into(stk_ctx *c, const stk_map *m, double *out)
+static int score_into(stk_ctx *c, const stk_map *m, float *out)
 {
     CUDA_TRY(c, cudaSetDevice(c->device));
     void *order = nullptr;
@@ -492,10 +493,14 @@ int stk_score_all(stk_ctx *c, const stk_map *m, double *out_snr_dev)
     int rc = check_ready(c, m);
     if (rc) return rc;
     if (!out_snr_dev) return set_err(c, STK_EINVAL, "out_snr_dev is NULL");
-    rc = score_into(c, m, out_snr_dev);
+    rc = ensure(c, (void **)&c->snr_buf, &c->snr_cap, c->ts.n * sizeof(float));
     if (rc) return rc;
+    rc = score_into(c, m, c->snr_buf);
+    if (rc) return rc;
+    cudaError_t e = launch_widen(c->snr_buf, out_snr_dev, c->ts.n, c->stream);
+    if (e != cudaSuccess) return set_err(c, STK_ECUDA, "widening launch: %s", cudaGetErrorString(e));
     c->timed = c->profiling;
-    c->last_launches = 1 + (c->plan.order ? c->plan.order_launches : 0);
+    c->last_launches = 2 + (c->plan.order ? c->plan.order_launches : 0);
     if (c->profiling) CUDA_TRY(c, cudaEventRecord(c->ev[2], c->stream));
     return STK_OK;
 }
@@ -509,7 +514,7 @@ int stk_score(stk_ctx *c, const stk_map *m, int k, stk_hit *out, unsigned flags)
     if (flags & ~STK_OUT_HOST) return set_err(c, STK_EINVAL, "unknown flags 0x%x", flags);
     if (k < 1 || k > STK_MAX_K || (uint64_t)k > c->ts.n)
         return set_err(c, STK_EINVAL, "k = %d must be in [1, min(%d, n_tracks))", k, STK_MAX_K);
-    rc = ensure(c, (void **)&c->snr_buf, &c->snr_cap, c->ts.n * sizeof(double));
+    rc = ensure(c, (void **)&c->snr_buf, &c->snr_cap, c->ts.n * sizeof(float));
     if (rc) return rc;
     rc = ensure(c, &c->sel_buf, &c->sel_cap, select_scratch_bytes(c->ts.n, k));
     if (rc) return rc;
@@ -564,7 +569,10 @@ int stk_score_explicit(stk_ctx *c, const stk_map *m, const uint32_t *f3, const d
     if (n == 0) return STK_OK;
     if (!f3 || !tau || !out) return set_err(c, STK_EINVAL, "NULL pointer");
     CUDA_TRY(c, cudaSetDevice(c->device));
-    cudaError_t e = launch_score_explicit(m->dev, f3, tau, n, out, c->d_err, c->stream);
+    int rc = ensure(c, (void **)&c->snr_buf, &c->snr_cap, n * sizeof(float));
+    if (rc) return rc;
+    cudaError_t e = launch_score_explicit(m->dev, f3, tau, n, c->snr_buf, c->d_err, c->stream);
+    if (e == cudaSuccess) e = launch_widen(c->snr_buf, out, n, c->stream);
     if (e != cudaSuccess) return set_err(c, STK_ECUDA, "explicit scoring launch: %s", cudaGetErrorString(e));
     return STK_OK;
 }
@@ -623,7 +631,10 @@ int stk_score_explicit_general(stk_ctx *c, const stk_map *m, const uint32_t *t3,
     if (m->dev.n_t > 4096 || m->dev.n_f > 8192)
         return set_err(c, STK_EINVAL, "general templates need n_t <= 4096 and n_f <= 8192");
     CUDA_TRY(c, cudaSetDevice(c->device));
-    cudaError_t e = launch_score_explicit_general(m->dev, t3, f3, tau, n, out, c->d_err, c->stream);
+    int rc = ensure(c, (void **)&c->snr_buf, &c->snr_cap, n * sizeof(float));
+    if (rc) return rc;
+    cudaError_t e = launch_score_explicit_general(m->dev, t3, f3, tau, n, c->snr_buf, c->d_err, c->stream);
+    if (e == cudaSuccess) e = launch_widen(c->snr_buf, out, n, c->stream);
     if (e != cudaSuccess) return set_err(c, STK_ECUDA, "explicit general scoring launch: %s", cudaGetErrorString(e));
     return STK_OK;
 }
@@ -703,7 +714,7 @@ int stk_last_timings(stk_ctx *c, double out[4])
 namespace {
 
 constexpr uint64_t kNoAllocMaxTracks = STK_NOALLOC_MAX_TRACKS;
-constexpr size_t kNoAllocSnrBytes = kNoAllocMaxTracks * sizeof(double);
+constexpr size_t kNoAllocSnrBytes = kNoAllocMaxTracks * sizeof(float);
 constexpr size_t kNoAllocFlagBytes = 256;
 constexpr size_t kNoAllocSelBytes = 1024 * 1024;
 constexpr int kNoAllocMaxDevices = 64;
@@ -777,7 +788,7 @@ extern "C" int stk_score_noalloc(const stk_map *m, uint64_t n_tracks, uint64_t s
     if (rc == STK_OK) {
         cudaStream_t st = (cudaStream_t)cuda_stream;
         unsigned char *base = (unsigned char *)d.base;
-        double *snr = (double *)base;
+        float *snr = (float *)base;
         int *flags = (int *)(base + kNoAllocSnrBytes);
         void *sel = base + kNoAllocSnrBytes + kNoAllocFlagBytes;
         TrackSet ts{n_tracks, seed, counter_offset, tau_max_s};

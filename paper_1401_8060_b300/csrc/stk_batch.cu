@@ -381,14 +381,11 @@ __global__ void __launch_bounds__(256) batch_rank_kernel(const BatchMap *__restr
             uint32_t f[3];
             double tau;
             draw_track(bm->ts.seed, bm->ts.offset + mi, (uint32_t)bm->m.n_f, bm->ts.tau_max, f, tau);
-            h.snr = 0.0;
+            h.snr = (double)snr_from_key(mk);  // the SNR back from its order-preserving key
             h.index = bm->ts.offset + mi;
             h.f[0] = f[0]; h.f[1] = f[1]; h.f[2] = f[2];
             h.reserved = 0;
             h.tau = tau;
-            // the SNR back from its order-preserving key
-            const unsigned long long b = (mk >> 63) ? (mk & 0x7fffffffffffffffull) : ~mk;
-            h.snr = __longlong_as_double((long long)b);
             out[(size_t)blockIdx.y * K + rank] = h;
         }
     }

@@ -44,6 +44,7 @@ struct MapDev {
     float w_const;    // WMODE_CONST weight (sigma^-2), 1 in paper mode
     double f_min, df; // Hz
     double norm;      // 1 / n_t (paper form) or 1 / sqrt(n_t w_const) (WMODE_CONST); else unused
+    float norm_f;     // norm rounded to FP32
     const void *rec;  // [n_t][ldr] records (uint2 for FP32, uint32 for FP16)
     const float *w;   // [n_f] (WMODE_FREQ) or [n_t][ldw] (WMODE_PIXEL), else null: sigma^-2 or 1/sigma
     // Rasteriser: column j of template (f0, f1, f2) sits at bin floor(N_j / d) with
@@ -527,11 +528,11 @@ struct Tuning {
     int order = 1;       // slab kernel: score templates in coherent order (1) or index order (0)
 };
 
-// Launch the scoring kernel for generated templates; writes n SNRs to out.
+// Launch the scoring kernel for generated templates; writes n FP32 SNRs to out.
 // order_scratch (order_scratch_bytes(n, n_f) bytes, or NULL for index order)
 // holds the coherent-order pre-pass of the slab kernel; order_done, if given,
 // is recorded between that pre-pass and the scoring kernel.
-cudaError_t launch_score_generated(const MapDev &m, const TrackSet &ts, double *out, int *err, const Tuning &tu,
+cudaError_t launch_score_generated(const MapDev &m, const TrackSet &ts, float *out, int *err, const Tuning &tu,
                                    int num_sms, size_t smem_optin, cudaStream_t st, ScorePlan *plan_out,
                                    void *order_scratch = nullptr, cudaEvent_t order_done = nullptr);
 // Whether launch_score_generated would use order scratch for this call.
@@ -564,24 +565,27 @@ cudaError_t order_prepare(uint32_t nc, uint32_t max_fbits);
 cudaError_t launch_order_batch(const OrderMap *d_maps, int n_maps, uint64_t total_n, uint32_t nc, uint32_t max_fbits,
                                void *scratch, int num_sms, cudaStream_t st, const uint32_t **perm_out,
                                int *launches);
-// Explicit templates f3[n][3], tau[n].
-cudaError_t launch_score_explicit(const MapDev &m, const uint32_t *f3, const double *tau, uint64_t n, double *out,
+// Explicit templates f3[n][3], tau[n] (FP32 SNRs to out).
+cudaError_t launch_score_explicit(const MapDev &m, const uint32_t *f3, const double *tau, uint64_t n, float *out,
                                   int *err, cudaStream_t st);
 // Explicit general templates: t3[n][3] control times, f3[n][3] control bins.
 cudaError_t launch_score_explicit_general(const MapDev &m, const uint32_t *t3, const uint32_t *f3, const double *tau,
-                                          uint64_t n, double *out, int *err, cudaStream_t st);
+                                          uint64_t n, float *out, int *err, cudaStream_t st);
 // Parameters (f_dev: 3 bins then 3 times), delay and bins of one template (device buffers).
 cudaError_t launch_track_params(const MapDev &m, const TrackSet &ts, uint64_t g, uint32_t *f_dev, double *tau_dev,
                                 int32_t *bins_dev, cudaStream_t st);
+
+// out[i] = (double)in[i], i < n.
+cudaError_t launch_widen(const float *in, double *out, uint64_t n, cudaStream_t st);
 
 // Interpolated statistic of continuous templates (forward: snr; adjoint: g * gradient).
 cudaError_t launch_interp(const MapDev &m, const float *f3, const float *tau, const float *g, uint64_t n, float *snr,
                           float *gf3, float *gtau, bool adjoint, cudaStream_t st);
 
-// Top-k selection over snr[0..n): hits get (snr, offset + i, params).  Scratch
+// Top-k selection over the FP32 snr[0..n): hits get (snr widened to FP64, offset + i, params).  Scratch
 // is caller-provided: see select_scratch_bytes.
 size_t select_scratch_bytes(uint64_t n, int k);
-cudaError_t launch_select_topk(const double *snr, uint64_t n, int k, const TrackSet &ts, const MapDev &m,
+cudaError_t launch_select_topk(const float *snr, uint64_t n, int k, const TrackSet &ts, const MapDev &m,
                                void *scratch, stk_hit *out_dev, cudaStream_t st, int *launches);
 
 }  // namespace stk

@@ -20,7 +20,7 @@ struct stk_ctx {
     bool have_tracks = false;
     TrackSet ts{};
     int *d_err = nullptr;          // device error/flag word
-    double *snr_buf = nullptr;     // scratch: one SNR per template
+    float *snr_buf = nullptr;      // scratch: one FP32 SNR per template
     size_t snr_cap = 0;
     void *sel_buf = nullptr;       // scratch: selection state
     size_t sel_cap = 0;

@@ -100,26 +100,36 @@ __device__ __forceinline__ void accumulate(typename Pix<PREC>::Rec v, uint32_t b
     accumulate_turn<PREC, WMODE>(v, pixel_turn(bin, ph, Pix<PREC>::arg(v)), wv, acc, W);
 }
 
-// Normalisation (Eq. 7 with the weighting of the footnote to Eq. 5), FP64 on the
-// GPU.  Weighted form with varying weights: S / sqrt(W), where 1 / sqrt(W) is an
-// FP32 seed refined by one Newton-Raphson step y1 = y0 (3 - W y0^2) / 2 in FP64
-// (relative error ~1e-13).  Constant weight or paper form: S times a constant.
+// Normalisation (Eq. 7 with the weighting of the footnote to Eq. 5) in FP32.
+// Weighted form with varying weights: S / sqrt(W), the square root and the
+// division each rounded to nearest, so the result is within 2^-23 (1.2e-7)
+// relative of S / sqrt(W) for the FP32 sums S and W.  Constant weight or paper
+// form: S times the constant rounded to FP32 (within 2^-23 relative).  No FP64
+// arithmetic: this GPU issues FP64 operations at a small fraction of the FP32
+// rate, and a per-template FP64 normalisation cost 4.5 % of the scoring kernel.
 template <int WMODE>
-__device__ __forceinline__ double finalize_snr(float acc, float W, const MapDev &m)
+__device__ __forceinline__ float finalize_snr(float acc, float W, const MapDev &m)
 {
-    if (WMODE == WMODE_CONST || m.paper) return (double)acc * m.norm;
-    const double y0 = (double)rsqrtf(W);
-    const double t = (double)W * y0 * y0;
-    return (double)acc * (y0 * fma(-0.5, t, 1.5));
+    if (WMODE == WMODE_CONST || m.paper) return acc * m.norm_f;
+    return __fdiv_rn(acc, __fsqrt_rn(W));
 }
 
 // ------------------------------------------------------------------ selection order
-// Order-preserving 64-bit key of an FP64 SNR (-0 and +0 share one key).
-__device__ __forceinline__ unsigned long long order_key(double x)
+// Order-preserving key of an FP32 SNR in the upper 32 bits of a 64-bit key
+// (-0 and +0 share one key; the lower 32 bits are zero).
+__device__ __forceinline__ unsigned long long order_key(float x)
 {
-    if (x == 0.0) x = 0.0;
-    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-    return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+    uint32_t b = __float_as_uint(x);
+    if ((b << 1) == 0u) b = 0u;
+    const uint32_t k = (b >> 31) ? ~b : (b | 0x80000000u);
+    return (unsigned long long)k << 32;
+}
+
+// The SNR back from its key.
+__device__ __forceinline__ float snr_from_key(unsigned long long key)
+{
+    const uint32_t k = (uint32_t)(key >> 32);
+    return __uint_as_float((k >> 31) ? (k & 0x7fffffffu) : ~k);
 }
 
 // "a before b": larger key, then smaller index.

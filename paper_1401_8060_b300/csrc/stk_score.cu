@@ -38,7 +38,7 @@ constexpr int kMaxThreads = 1024;
 template <int WMODE, int PREC, bool EXPLICIT, bool FAST32>
 __global__ void __launch_bounds__(256) score_simple_kernel(MapDev m, TrackSet ts, const uint32_t *__restrict__ f3,
                                                            const double *__restrict__ tau_in, uint64_t n,
-                                                           double *__restrict__ out, int *err)
+                                                           float *__restrict__ out, int *err)
 {
     const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -84,14 +84,12 @@ __global__ void __launch_bounds__(256) score_simple_kernel(MapDev m, TrackSet ts
 // only, from the L2-resident map; the exact integer rasteriser (gen_step) moves the
 // pixel from column to column.  N = t2 - t0 + 1 pixels.
 template <int WMODE, int PREC>
-__device__ __forceinline__ double finalize_general(float acc, float W, const MapDev &m, int N)
+__device__ __forceinline__ float finalize_general(float acc, float W, const MapDev &m, int N)
 {
-    if (m.paper) return (double)acc / (double)N;
+    if (m.paper) return __fdiv_rn(acc, (float)N);
     if (WMODE == WMODE_CONST)
-        return (double)acc / sqrt((double)N * (PREC == PREC_FP16 ? 1.0 : (double)m.w_const));
-    const double y0 = (double)rsqrtf(W);
-    const double t = (double)W * y0 * y0;
-    return (double)acc * (y0 * fma(-0.5, t, 1.5));
+        return __fdiv_rn(acc, __fsqrt_rn(PREC == PREC_FP16 ? (float)N : __fmul_rn((float)N, m.w_const)));
+    return __fdiv_rn(acc, __fsqrt_rn(W));
 }
 
 // One thread per template, in coherent order when perm is given (a warp's
@@ -100,7 +98,7 @@ template <int WMODE, int PREC, bool EXPLICIT>
 __global__ void __launch_bounds__(256) score_general_kernel(MapDev m, TrackSet ts, const uint32_t *__restrict__ t3,
                                                             const uint32_t *__restrict__ f3,
                                                             const double *__restrict__ tau_in, uint64_t n,
-                                                            double *__restrict__ out, int *err,
+                                                            float *__restrict__ out, int *err,
                                                             const uint32_t *__restrict__ perm)
 {
     const uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -176,7 +174,7 @@ __global__ void __launch_bounds__(256) score_general_kernel(MapDev m, TrackSet t
 
 template <int WMODE, int PREC, bool EXPLICIT>
 cudaError_t launch_general_W(const MapDev &m, const TrackSet &ts, const uint32_t *t3, const uint32_t *f3,
-                             const double *tau, uint64_t n, double *out, int *err, cudaStream_t st,
+                             const double *tau, uint64_t n, float *out, int *err, cudaStream_t st,
                              const uint32_t *perm)
 {
     const uint64_t blocks = (n + 255) / 256;
@@ -188,7 +186,7 @@ cudaError_t launch_general_W(const MapDev &m, const TrackSet &ts, const uint32_t
 
 template <bool EXPLICIT>
 cudaError_t launch_general(const MapDev &m, const TrackSet &ts, const uint32_t *t3, const uint32_t *f3,
-                           const double *tau, uint64_t n, double *out, int *err, cudaStream_t st,
+                           const double *tau, uint64_t n, float *out, int *err, cudaStream_t st,
                            const uint32_t *perm = nullptr)
 {
 #define STK_GEN(W, P) return launch_general_W<W, P, EXPLICIT>(m, ts, t3, f3, tau, n, out, err, st, perm)
@@ -235,7 +233,7 @@ constexpr int staged_max_threads(int R, int WMODE)
 
 template <int R, int WMODE, int PREC>
 __global__ void __launch_bounds__(staged_max_threads(R, WMODE), 1)
-    score_staged_kernel(MapDev m, TrackSet ts, StagedArgs a, double *__restrict__ out, int *err)
+    score_staged_kernel(MapDev m, TrackSet ts, StagedArgs a, float *__restrict__ out, int *err)
 {
     using Rec = typename Pix<PREC>::Rec;
     extern __shared__ __align__(128) unsigned char smem[];
@@ -409,7 +407,7 @@ __global__ void __launch_bounds__(staged_max_threads(R, WMODE), 1)
 
 template <int R, int WMODE, int PREC>
 cudaError_t launch_staged_R(const MapDev &m, const TrackSet &ts, const StagedArgs &sa, int grid, int threads,
-                            size_t smem, double *out, int *err, cudaStream_t st)
+                            size_t smem, float *out, int *err, cudaStream_t st)
 {
     auto k = score_staged_kernel<R, WMODE, PREC>;
     if (threads > staged_max_threads(R, WMODE)) return cudaErrorInvalidConfiguration;
@@ -421,7 +419,7 @@ cudaError_t launch_staged_R(const MapDev &m, const TrackSet &ts, const StagedArg
 
 template <int WMODE, int PREC>
 cudaError_t launch_staged_W(int R, const MapDev &m, const TrackSet &ts, const StagedArgs &sa, int grid, int threads,
-                            size_t smem, double *out, int *err, cudaStream_t st)
+                            size_t smem, float *out, int *err, cudaStream_t st)
 {
     switch (R) {
     case 1: return launch_staged_R<1, WMODE, PREC>(m, ts, sa, grid, threads, smem, out, err, st);
@@ -445,7 +443,7 @@ cudaError_t launch_staged_W(int R, const MapDev &m, const TrackSet &ts, const St
 
 template <int PREC>
 cudaError_t launch_staged_P(int R, const MapDev &m, const TrackSet &ts, const StagedArgs &sa, int grid, int threads,
-                            size_t smem, double *out, int *err, cudaStream_t st)
+                            size_t smem, float *out, int *err, cudaStream_t st)
 {
     switch (m.wmode) {
     case WMODE_CONST: return launch_staged_W<WMODE_CONST, PREC>(R, m, ts, sa, grid, threads, smem, out, err, st);
@@ -456,7 +454,7 @@ cudaError_t launch_staged_P(int R, const MapDev &m, const TrackSet &ts, const St
 
 template <int WMODE, int PREC, bool EXPLICIT>
 cudaError_t launch_simple_W(const MapDev &m, const TrackSet &ts, const uint32_t *f3, const double *tau, uint64_t n,
-                            double *out, int *err, cudaStream_t st)
+                            float *out, int *err, cudaStream_t st)
 {
     const int threads = 256;
     const uint64_t blocks = (n + threads - 1) / threads;
@@ -472,7 +470,7 @@ cudaError_t launch_simple_W(const MapDev &m, const TrackSet &ts, const uint32_t 
 
 template <int PREC, bool EXPLICIT>
 cudaError_t launch_simple_P(const MapDev &m, const TrackSet &ts, const uint32_t *f3, const double *tau, uint64_t n,
-                            double *out, int *err, cudaStream_t st)
+                            float *out, int *err, cudaStream_t st)
 {
     switch (m.wmode) {
     case WMODE_CONST: return launch_simple_W<WMODE_CONST, PREC, EXPLICIT>(m, ts, f3, tau, n, out, err, st);
@@ -483,10 +481,18 @@ cudaError_t launch_simple_P(const MapDev &m, const TrackSet &ts, const uint32_t 
 
 template <bool EXPLICIT>
 cudaError_t launch_simple(const MapDev &m, const TrackSet &ts, const uint32_t *f3, const double *tau, uint64_t n,
-                          double *out, int *err, cudaStream_t st)
+                          float *out, int *err, cudaStream_t st)
 {
     if (m.prec == PREC_FP16) return launch_simple_P<PREC_FP16, EXPLICIT>(m, ts, f3, tau, n, out, err, st);
     return launch_simple_P<PREC_FP32, EXPLICIT>(m, ts, f3, tau, n, out, err, st);
+}
+
+// ------------------------------------------------------------------ FP32 -> FP64 output
+__global__ void __launch_bounds__(256) widen_kernel(const float *__restrict__ in, double *__restrict__ out,
+                                                    uint64_t n)
+{
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) out[i] = (double)in[i];
 }
 
 // ------------------------------------------------------------------ template-params kernel
@@ -533,7 +539,7 @@ bool score_wants_order(const MapDev &m, const TrackSet &ts, const Tuning &tu)
     return tu.kernel == 2 || ts.n * (uint64_t)m.n_t >= (1ull << 24);
 }
 
-cudaError_t launch_score_generated(const MapDev &m, const TrackSet &ts, double *out, int *err, const Tuning &tu,
+cudaError_t launch_score_generated(const MapDev &m, const TrackSet &ts, float *out, int *err, const Tuning &tu,
                                    int num_sms, size_t smem_optin, cudaStream_t st, ScorePlan *plan,
                                    void *order_scratch, cudaEvent_t order_done)
 {
@@ -646,7 +652,7 @@ cudaError_t launch_score_generated(const MapDev &m, const TrackSet &ts, double *
     return launch_simple<false>(m, ts, nullptr, nullptr, n, out, err, st);
 }
 
-cudaError_t launch_score_explicit(const MapDev &m, const uint32_t *f3, const double *tau, uint64_t n, double *out,
+cudaError_t launch_score_explicit(const MapDev &m, const uint32_t *f3, const double *tau, uint64_t n, float *out,
                                   int *err, cudaStream_t st)
 {
     TrackSet ts{};
@@ -654,10 +660,18 @@ cudaError_t launch_score_explicit(const MapDev &m, const uint32_t *f3, const dou
 }
 
 cudaError_t launch_score_explicit_general(const MapDev &m, const uint32_t *t3, const uint32_t *f3, const double *tau,
-                                          uint64_t n, double *out, int *err, cudaStream_t st)
+                                          uint64_t n, float *out, int *err, cudaStream_t st)
 {
     TrackSet ts{};
     return launch_general<true>(m, ts, t3, f3, tau, n, out, err, st);
+}
+
+cudaError_t launch_widen(const float *in, double *out, uint64_t n, cudaStream_t st)
+{
+    if (n == 0) return cudaSuccess;
+    const uint64_t blocks = (n + 255) / 256;
+    widen_kernel<<<(unsigned)(blocks < 4096 ? blocks : 4096), 256, 0, st>>>(in, out, n);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_track_params(const MapDev &m, const TrackSet &ts, uint64_t g, uint32_t *f_dev, double *tau_dev,

@@ -2,7 +2,8 @@
 // cluster", Sec. III, kept to k > 1 so runs can be merged, Sec. V).
 //
 // Exact and deterministic: order by SNR descending, then template index
-// ascending.  The FP64 SNRs are mapped to order-preserving 64-bit keys.
+// ascending.  The FP32 SNRs are mapped to order-preserving keys: 32 bits, in
+// the upper half of a 64-bit key (the candidate and batch formats).
 //   1. two histogram passes over the 12-bit digits key[63:52] and key[51:40]
 //      fix the 24-bit prefix of the k-th largest key;
 //   2. one pass collects every template whose key prefix is at least that one
@@ -87,7 +88,7 @@ __global__ void sel_init(SelState *st)
 // The leading key bits of SNRs fall into few bins, so lanes of a warp holding the
 // same bin are merged (__match_any_sync) into one shared-memory atomic.
 template <int PASS>
-__global__ void __launch_bounds__(kPassThreads) sel_hist(const double *__restrict__ snr, uint64_t n, SelState *st)
+__global__ void __launch_bounds__(kPassThreads) sel_hist(const float *__restrict__ snr, uint64_t n, SelState *st)
 {
     __shared__ unsigned int h[kBins];
     for (int i = threadIdx.x; i < kBins; i += blockDim.x) h[i] = 0;
@@ -97,11 +98,11 @@ __global__ void __launch_bounds__(kPassThreads) sel_hist(const double *__restric
     const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
     const uint64_t w0 = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     for (uint64_t base = w0 * 128; base < n; base += warps * 128) {
-        double v[4];
+        float v[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {   // four independent loads in flight per lane
             const uint64_t i = base + u * 32 + lane;
-            v[u] = i < n ? snr[i] : 0.0;
+            v[u] = i < n ? snr[i] : 0.f;
         }
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
@@ -136,7 +137,7 @@ __global__ void __launch_bounds__(kFinalThreads) sel_pick(SelState *st, unsigned
 }
 
 // Every key whose 24-bit prefix is >= (d1, d2) becomes a candidate.
-__global__ void __launch_bounds__(kPassThreads) sel_collect(const double *__restrict__ snr, uint64_t n, SelState *st,
+__global__ void __launch_bounds__(kPassThreads) sel_collect(const float *__restrict__ snr, uint64_t n, SelState *st,
                                                             unsigned long long *cand_key, unsigned int *cand_idx)
 {
     const unsigned int pref = (st->d1 << 12) | st->d2;
@@ -144,11 +145,11 @@ __global__ void __launch_bounds__(kPassThreads) sel_collect(const double *__rest
     const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
     const uint64_t w0 = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     for (uint64_t base = w0 * 128; base < n; base += warps * 128) {
-        double v[4];
+        float v[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             const uint64_t i = base + u * 32 + lane;
-            v[u] = i < n ? snr[i] : 0.0;
+            v[u] = i < n ? snr[i] : 0.f;
         }
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
@@ -199,7 +200,7 @@ __device__ void bitonic_sort(unsigned long long *key, unsigned int *ix, int P)
 
 // Source of (key, index) pairs for the final step.
 struct Src {
-    const double *snr;
+    const float *snr;
     const unsigned long long *ckey;
     const unsigned int *cidx;
     uint64_t n;
@@ -217,7 +218,7 @@ __device__ void select_generic(const Src &src, int k, unsigned long long *out_ke
     __shared__ unsigned int d, kr;
     unsigned long long prefix = 0, mask = 0;
     unsigned int krem = (unsigned int)k;
-    for (int shift = 56; shift >= 0; shift -= 8) {
+    for (int shift = 56; shift >= 32; shift -= 8) {  // the lower 32 key bits are zero
         for (int i = threadIdx.x; i < (int)blockDim.x; i += blockDim.x) hp[i] = 0;
         __syncthreads();
         for (uint64_t i = threadIdx.x; i < src.n; i += blockDim.x) {
@@ -264,11 +265,11 @@ __device__ void select_generic(const Src &src, int k, unsigned long long *out_ke
     __syncthreads();
 }
 
-__device__ __forceinline__ void write_hit(const double *snr, unsigned int t, const TrackSet &ts, const MapDev &m,
+__device__ __forceinline__ void write_hit(const float *snr, unsigned int t, const TrackSet &ts, const MapDev &m,
                                           stk_hit *out)
 {
     stk_hit hit;
-    hit.snr = snr[t];
+    hit.snr = (double)snr[t];
     hit.index = ts.offset + t;
     uint32_t f[3];
     double tau;
@@ -285,7 +286,7 @@ __device__ __forceinline__ void write_hit(const double *snr, unsigned int t, con
 // the same comparand: a broadcast).
 constexpr int kRankTile = 1024;
 
-__global__ void __launch_bounds__(256) sel_rank(const double *__restrict__ snr, const SelState *st,
+__global__ void __launch_bounds__(256) sel_rank(const float *__restrict__ snr, const SelState *st,
                                                 const unsigned long long *__restrict__ cand_key,
                                                 const unsigned int *__restrict__ cand_idx, int k, TrackSet ts,
                                                 MapDev m, stk_hit *out)
@@ -325,7 +326,7 @@ __global__ void __launch_bounds__(256) sel_rank(const double *__restrict__ snr, 
 // one block (radix select over keys, then over the tied indices), bitonic sort of
 // the k winners.  Returns at once otherwise.
 __global__ void __launch_bounds__(kFinalThreads)
-    sel_generic(const double *__restrict__ snr, uint64_t n, const SelState *st, const unsigned long long *cand_key,
+    sel_generic(const float *__restrict__ snr, uint64_t n, const SelState *st, const unsigned long long *cand_key,
                 const unsigned int *cand_idx, int k, TrackSet ts, MapDev m, stk_hit *out)
 {
     extern __shared__ unsigned long long sh[];
@@ -357,7 +358,7 @@ size_t select_scratch_bytes(uint64_t /*n*/, int /*k*/)
     return align256(sizeof(SelState)) + align256((size_t)kCandCap * 8) + align256((size_t)kCandCap * 4);
 }
 
-cudaError_t launch_select_topk(const double *snr, uint64_t n, int k, const TrackSet &ts, const MapDev &m,
+cudaError_t launch_select_topk(const float *snr, uint64_t n, int k, const TrackSet &ts, const MapDev &m,
                                void *scratch, stk_hit *out, cudaStream_t st, int *launches)
 {
     if (k <= 0 || (uint64_t)k > n || k > STK_MAX_K || n > 0xffffffffull) return cudaErrorInvalidValue;
