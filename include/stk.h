@@ -355,6 +355,11 @@ STK_API int stk_score_noalloc(const stk_map *map, uint64_t n_tracks, uint64_t se
                               rarely collide; 0 scores in index order.  Results are identical; the
                               order costs 16 bytes per template plus 4 bytes per coarse bucket
                               (at most 8192) per block of 2 x SMs blocks of context scratch */
+#define STK_OPT_SELECT_SAMPLE 9 /* top-k selection: templates whose SNRs are sampled to set the
+                                   candidate threshold, 0 (default: 16384) or 1 .. 49152.  Results do
+                                   not depend on it: a threshold that admits fewer than k templates
+                                   (likelier with a small sample) makes the selection fall back to an
+                                   exact radix select over every SNR, which is slower */
 
 /* Set a tuning option for later scoring calls.  Errors: STK_EINVAL. */
 STK_API int stk_set_option(stk_ctx *ctx, int option, int64_t value);

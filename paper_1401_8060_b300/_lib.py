@@ -20,7 +20,7 @@ STK_OUT_HOST = 0x1
 STK_MAX_K = 4096
 STK_NOALLOC_MAX_TRACKS = 1 << 20
 STK_OPT_KERNEL, STK_OPT_THREADS, STK_OPT_MAX_R, STK_OPT_STAGES, STK_OPT_SMEM_KB = 1, 2, 3, 4, 5
-STK_OPT_WAIT_MS, STK_OPT_WITHHOLD_SLAB, STK_OPT_ORDER = 6, 7, 8
+STK_OPT_WAIT_MS, STK_OPT_WITHHOLD_SLAB, STK_OPT_ORDER, STK_OPT_SELECT_SAMPLE = 6, 7, 8, 9
 
 # Every entry point declared in include/stk.h: (name, restype, argtypes).
 _vp = C.c_void_p

@@ -278,6 +278,10 @@ int stk_set_option(stk_ctx *c, int option, int64_t value)
         if (value < -1 || value > (1 << 30)) return set_err(c, STK_EINVAL, "slab index out of range");
         c->tune.withhold_slab = (int)value;
         return STK_OK;
+    case STK_OPT_SELECT_SAMPLE:
+        if (value < 0 || value > 49152) return set_err(c, STK_EINVAL, "selection sample must be in [0, 49152]");
+        c->tune.select_sample = (int)value;
+        return STK_OK;
     default: return set_err(c, STK_EINVAL, "unknown option %d", option);
     }
 }
@@ -522,7 +526,8 @@ int stk_score(stk_ctx *c, const stk_map *m, int k, stk_hit *out, unsigned flags)
     if (rc) return rc;
     stk_hit *dst = (flags & STK_OUT_HOST) ? c->hits_dev : out;
     int nl = 0;
-    cudaError_t e = launch_select_topk(c->snr_buf, c->ts.n, k, c->ts, m->dev, c->sel_buf, dst, c->stream, &nl);
+    cudaError_t e = launch_select_topk(c->snr_buf, c->ts.n, k, c->ts, m->dev, c->sel_buf, dst, c->stream, &nl,
+                                       (uint32_t)c->tune.select_sample);
     if (e != cudaSuccess) return set_err(c, STK_ECUDA, "selection launch: %s", cudaGetErrorString(e));
     c->last_launches = 1 + nl + (c->plan.order ? c->plan.order_launches : 0);
     c->timed = c->profiling;

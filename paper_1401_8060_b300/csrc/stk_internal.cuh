@@ -526,6 +526,7 @@ struct Tuning {
     int wait_ms = 0;     // slab wait limit, 0: 2000 ms
     int withhold_slab = -1;  // test of the bounded waits: CTA 0 withholds this slab copy (-1: off)
     int order = 1;       // slab kernel: score templates in coherent order (1) or index order (0)
+    int select_sample = 0;  // selection: keys sampled for the threshold (0: default)
 };
 
 // Launch the scoring kernel for generated templates; writes n FP32 SNRs to out.
@@ -583,9 +584,12 @@ cudaError_t launch_interp(const MapDev &m, const float *f3, const float *tau, co
                           float *gf3, float *gtau, bool adjoint, cudaStream_t st);
 
 // Top-k selection over the FP32 snr[0..n): hits get (snr widened to FP64, offset + i, params).  Scratch
-// is caller-provided: see select_scratch_bytes.
+// is caller-provided: see select_scratch_bytes.  sample: keys sampled for the candidate
+// threshold (0: the default, 16384; at most 49152); the result does not depend on it.
 size_t select_scratch_bytes(uint64_t n, int k);
+uint32_t select_sample_size(uint64_t n, uint32_t sample);
 cudaError_t launch_select_topk(const float *snr, uint64_t n, int k, const TrackSet &ts, const MapDev &m,
-                               void *scratch, stk_hit *out_dev, cudaStream_t st, int *launches);
+                               void *scratch, stk_hit *out_dev, cudaStream_t st, int *launches,
+                               uint32_t sample = 0);
 
 }  // namespace stk

@@ -299,9 +299,10 @@ def test_split_ranges_merge_exactly(ctx):
 
 @pytest.mark.parametrize("T,k", [(5000, 10), (20000, 4096), (100000, 100)])
 def test_constant_map_ties_take_smallest_index(ctx, T, k):
-    """Every template ties: the smallest indices win.  The three sizes take the
-    three selection routes (shared-memory sort of the candidates; exact select
-    over candidates beyond that sort; candidate-buffer overflow, full array)."""
+    """Every template ties: the smallest indices win.  Every template becomes a
+    candidate, and the three sizes take the three routes of the final exact
+    select (candidates staged in shared memory; too many to stage, read from
+    global memory; candidate-buffer overflow, the full SNR array)."""
     n_t, n_f = 20, 30
     y = np.full((n_t, n_f), 1 + 0j, np.complex64)
     m = ctx.load_map(torch.from_numpy(y).cuda(), torch.ones(n_f, device="cuda"), 0.0, 1.0)
@@ -325,6 +326,42 @@ def test_selection_with_many_near_ties(ctx):
     order = np.lexsort((np.arange(T), -allg))[:k]
     np.testing.assert_array_equal(hits["index"], order)
     np.testing.assert_array_equal(hits["snr"], allg[order])
+
+
+@pytest.mark.parametrize("sample", [1, 2, 64, 49152])
+def test_selection_sample_sizes_identical(ctx, sample):
+    """The candidate threshold comes from a sample of the SNRs; the k loudest do
+    not depend on its size.  A sample of one or two keys sets the threshold at
+    those templates' own prefix: the candidates then either overflow or, when
+    the sampled templates are among the loudest, number fewer than k; both
+    make the final exact select run over every SNR."""
+    n_t, n_f = 50, 400
+    y, sig = rand_map(71, n_t, n_f, "freq")
+    m, _ = load_both(ctx, y, sig, 40.0, 0.5)
+    cases = [(200000, 1024), (3000, 100)]  # more, and fewer, templates than the default sample
+    refs = []
+    for T, k in cases:
+        ctx.set_tracks(T, 13, 5, 0.01)
+        ref = ctx.score(m, k)
+        allg = ctx.score_all(m).cpu().numpy()
+        order = np.lexsort((np.arange(T), -allg))[:k]
+        np.testing.assert_array_equal(ref["index"], order + 5)
+        np.testing.assert_array_equal(ref["snr"], allg[order])
+        refs.append(ref)
+    ctx.set_option(_lib.STK_OPT_SELECT_SAMPLE, sample)
+    try:
+        for (T, k), ref in zip(cases, refs):
+            ctx.set_tracks(T, 13, 5, 0.01)
+            np.testing.assert_array_equal(ctx.score(m, k), ref)
+    finally:
+        ctx.set_option(_lib.STK_OPT_SELECT_SAMPLE, 0)
+    m.close()
+
+
+def test_selection_sample_option_range(ctx):
+    for bad in (-1, 49153):
+        with pytest.raises(stk.StkError):
+            ctx.set_option(_lib.STK_OPT_SELECT_SAMPLE, bad)
 
 
 # ------------------------------------------------------------------ closed forms through the GPU
