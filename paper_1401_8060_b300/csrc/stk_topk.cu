@@ -4,11 +4,13 @@
 // Exact and deterministic: order by SNR descending, then template index
 // ascending.  The FP32 SNRs are mapped to order-preserving keys: 32 bits, in
 // the upper half of a 64-bit key (the candidate and batch formats).
-//   1. one block reads the keys of S templates in 32 runs spread over the range
-//      (all of them when n <= S) and takes the 24-bit prefix of the q-th
-//      largest sample key, q
-//      chosen so that at least k of all n keys reach that prefix except with
-//      negligible probability;
+//   1. the threshold, a 24-bit key prefix: one block reads the keys of S
+//      templates in 4 runs spread over the range (all of them when n <= S) and
+//      takes the prefix of the q-th largest sample key, q chosen so that at
+//      least k of all n keys reach it except with negligible probability; or,
+//      when that would admit more than a quarter of the candidate buffer (k
+//      small against n / S), the exact prefix of the k-th largest key from two
+//      histogram passes over all keys;
 //   2. one pass collects every template whose key prefix is at least that one
 //      (the k winners and a few thousand more) into a candidate buffer;
 //   3. one block selects exactly: a radix select of the k-th largest key, then
@@ -36,6 +38,7 @@ constexpr int kPassThreads = 512;
 constexpr int kFinalThreads = 1024;
 constexpr int kWarps = kFinalThreads / 32;
 constexpr int kDigits = 256;                // 8-bit radix digits
+constexpr int kBins12 = 4096;               // 12-bit digits of the exact threshold
 constexpr uint32_t kCandCap = 65536;        // candidate buffer
 constexpr uint32_t kSmemCand = 8192;        // candidates staged in shared memory by the final step
 constexpr uint32_t kSampleDefault = 16384;  // keys sampled for the threshold
@@ -46,7 +49,9 @@ struct SelState {
     unsigned int prefix;   // the threshold: 24-bit key prefix
     unsigned int ncand;    // candidates collected
     unsigned int overflow; // candidates exceeded kCandCap
-    unsigned int pad;
+    unsigned int d1, krem; // exact threshold: first digit, places left inside it
+    unsigned int pad[3];
+    unsigned int hist[kBins12];  // exact threshold: digit histogram
 };
 
 // Upper half of order_key: unsigned order is SNR order.
@@ -179,6 +184,107 @@ __global__ void __launch_bounds__(kFinalThreads) sel_threshold(const float *__re
         st->ncand = 0;
         st->overflow = 0;
     }
+}
+
+// ------------------------------------------------------------------ step 1, exact form
+// When a sampled threshold would admit too many candidates (k small against
+// n / S), the threshold is instead the exact 24-bit prefix of the k-th largest
+// key: a histogram pass over all keys for the digit key[31:20], a pick, a pass
+// for key[19:8] among keys with that digit, a pick.  Multi-block passes; lanes
+// of a warp holding the same digit merge into one shared atomic.
+
+// Block-wide: given hist[0..nbins), the digit d with above(d) < krem <= above(d) +
+// hist[d] (above(d) = sum of bins > d) and krem - above(d), through shared memory.
+// nbins must be a multiple of blockDim.x.
+__device__ void pick_digit(const unsigned int *hist, int nbins, unsigned int krem, unsigned int *out_d,
+                           unsigned int *out_krem)
+{
+    __shared__ unsigned int warp_sum[32];
+    const int per = nbins / blockDim.x;
+    const int t = threadIdx.x, lane = t & 31, wid = t >> 5, nw = blockDim.x >> 5;
+    if (t == 0) {  // overwritten below (some digit always qualifies when krem <= the total)
+        *out_d = 0;
+        *out_krem = 1;
+    }
+    unsigned int mine = 0;
+    for (int i = 0; i < per; ++i) mine += hist[t * per + i];
+    unsigned int incl = mine;  // becomes the sum over threads t .. 32 wid + 31
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned int v = __shfl_down_sync(0xffffffffu, incl, o);
+        if (lane + o < 32) incl += v;
+    }
+    if (lane == 0) warp_sum[wid] = incl;
+    __syncthreads();
+    unsigned int above = incl - mine;
+    for (int w = wid + 1; w < nw; ++w) above += warp_sum[w];
+    for (int i = per - 1; i >= 0; --i) {
+        const unsigned int d = (unsigned int)(t * per + i), c = hist[d];
+        if (above < krem && above + c >= krem) {
+            *out_d = d;
+            *out_krem = krem - above;
+        }
+        above += c;
+    }
+    __syncthreads();
+}
+
+__global__ void sel_init(SelState *st)
+{
+    for (int i = threadIdx.x; i < kBins12; i += blockDim.x) st->hist[i] = 0;
+    if (threadIdx.x == 0) {
+        st->ncand = 0;
+        st->overflow = 0;
+    }
+}
+
+// PASS 0: histogram of key[31:20]; PASS 1: of key[19:8] among keys with key[31:20] == d1.
+template <int PASS>
+__global__ void __launch_bounds__(kPassThreads) sel_hist(const float *__restrict__ snr, uint64_t n, SelState *st)
+{
+    __shared__ unsigned int h[kBins12];
+    for (int i = threadIdx.x; i < kBins12; i += blockDim.x) h[i] = 0;
+    __syncthreads();
+    const unsigned int d1 = PASS ? st->d1 : 0u;
+    const int lane = threadIdx.x & 31;
+    const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
+    const uint64_t w0 = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    for (uint64_t base = w0 * 128; base < n; base += warps * 128) {
+        float v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {  // four independent loads in flight per lane
+            const uint64_t i = base + u * 32 + lane;
+            v[u] = i < n ? snr[i] : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            unsigned int bin = 0xffffffffu;  // no bin
+            if (base + u * 32 + lane < n) {
+                const uint32_t key = key32(v[u]);
+                if (PASS == 0) bin = key >> 20;
+                else if ((key >> 20) == d1) bin = (key >> 8) & 4095u;
+            }
+            const unsigned int peers = __match_any_sync(0xffffffffu, bin);
+            if (bin != 0xffffffffu && lane == __ffs(peers) - 1) atomicAdd(&h[bin], (unsigned int)__popc(peers));
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < kBins12; i += blockDim.x)
+        if (h[i]) atomicAdd(&st->hist[i], h[i]);
+}
+
+template <int PASS>
+__global__ void __launch_bounds__(kFinalThreads) sel_pick(SelState *st, unsigned int k)
+{
+    __shared__ unsigned int d, kr;
+    const unsigned int krem = PASS ? st->krem : k;
+    pick_digit(st->hist, kBins12, krem, &d, &kr);
+    if (threadIdx.x == 0) {
+        if (PASS == 0) st->d1 = d;
+        else st->prefix = (st->d1 << 12) | d;
+        st->krem = kr;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < kBins12; i += blockDim.x) st->hist[i] = 0;
 }
 
 // ------------------------------------------------------------------ step 2: candidates
@@ -379,11 +485,25 @@ cudaError_t launch_select_topk(const float *snr, uint64_t n, int k, const TrackS
     if (e != cudaSuccess) return e;
     const uint64_t blocks = (n + kPassThreads * 8 - 1) / (kPassThreads * 8);
     const int grid = (int)(blocks < 592 ? (blocks < 1 ? 1 : blocks) : 592);
-    sel_threshold<<<1, kFinalThreads, smem_t, st>>>(snr, n, S, q, ss);
+    // expected candidates above the sampled threshold: q n / S; beyond a quarter of the
+    // buffer the exact threshold (two full passes) is cheaper than the risk of overflow
+    const double expect = (uint64_t)S < n ? (double)q * (double)n / (double)S : (double)k;
+    int nl = 3;
+    if (expect <= (double)(kCandCap / 4)) {
+        sel_threshold<<<1, kFinalThreads, smem_t, st>>>(snr, n, S, q, ss);
+        nl += 1;
+    } else {
+        sel_init<<<1, 1024, 0, st>>>(ss);
+        sel_hist<0><<<grid, kPassThreads, 0, st>>>(snr, n, ss);
+        sel_pick<0><<<1, kFinalThreads, 0, st>>>(ss, (unsigned int)k);
+        sel_hist<1><<<grid, kPassThreads, 0, st>>>(snr, n, ss);
+        sel_pick<1><<<1, kFinalThreads, 0, st>>>(ss, (unsigned int)k);
+        nl += 5;
+    }
     sel_collect<<<grid, kPassThreads, 0, st>>>(snr, n, ss, ckey, cidx);
     sel_select<<<1, kFinalThreads, smem_s, st>>>(snr, n, ss, ckey, cidx, k, win);
     sel_place<<<(k + kPlaceChunk - 1) / kPlaceChunk, 256, 0, st>>>(snr, win, k, ts, m, out);
-    if (launches) *launches = 4;
+    if (launches) *launches = nl;
     return cudaGetLastError();
 }
 

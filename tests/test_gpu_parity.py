@@ -330,11 +330,12 @@ def test_selection_with_many_near_ties(ctx):
 
 @pytest.mark.parametrize("sample", [1, 2, 64, 49152])
 def test_selection_sample_sizes_identical(ctx, sample):
-    """The candidate threshold comes from a sample of the SNRs; the k loudest do
-    not depend on its size.  A sample of one or two keys sets the threshold at
-    those templates' own prefix: the candidates then either overflow or, when
-    the sampled templates are among the loudest, number fewer than k; both
-    make the final exact select run over every SNR."""
+    """The candidate threshold comes from a sample of the SNRs (or, when the
+    sample would admit too many candidates, from two exact histogram passes);
+    the k loudest do not depend on the sample's size.  With 200 000 templates a
+    sample of 1, 2 or 64 keys takes the exact threshold; with 3 000 it takes
+    the sampled one at the first templates' own prefix, which may admit fewer
+    than k (the final select then runs over every SNR)."""
     n_t, n_f = 50, 400
     y, sig = rand_map(71, n_t, n_f, "freq")
     m, _ = load_both(ctx, y, sig, 40.0, 0.5)
