@@ -40,7 +40,7 @@ constexpr int kWarps = kFinalThreads / 32;
 constexpr int kDigits = 256;                // 8-bit radix digits
 constexpr int kBins12 = 4096;               // 12-bit digits of the exact threshold
 constexpr uint32_t kCandCap = 65536;        // candidate buffer
-constexpr uint32_t kSmemCand = 8192;        // candidates staged in shared memory by the final step
+constexpr uint32_t kSmemCand = 12288;       // candidates staged in shared memory by the final step
 constexpr uint32_t kSampleDefault = 16384;  // keys sampled for the threshold
 constexpr uint32_t kSampleMax = 49152;      // the sample lives in shared memory
 constexpr uint32_t kSampleRuns = 4;         // runs of consecutive templates in the sample
