@@ -281,6 +281,24 @@ def test_topk_sizes_and_device_output(ctx, k):
     np.testing.assert_array_equal(host_hits, hits)
 
 
+def test_exact_threshold_route(ctx):
+    """k small against n / S (here 8 of 4e7): a sampled threshold would admit
+    about q n / S ~ 2e4 candidates, so the selection takes its threshold from two
+    exact histogram passes; the k loudest are the top of the GPU's own SNR array
+    (descending SNR, then ascending index)."""
+    n_t, n_f, T, k = 20, 200, 40_000_000, 8
+    y, sig = rand_map(81, n_t, n_f, "freq")
+    m, _ = load_both(ctx, y, sig, 40.0, 0.5)
+    ctx.set_tracks(T, 21, 3, 0.01)
+    hits = ctx.score(m, k)
+    g = ctx.score_all(m)
+    v, i = torch.sort(g, descending=True, stable=True)
+    np.testing.assert_array_equal(hits["snr"], v[:k].cpu().numpy())
+    np.testing.assert_array_equal(hits["index"], i[:k].cpu().numpy() + 3)
+    del g, v, i
+    m.close()
+
+
 def test_split_ranges_merge_exactly(ctx):
     """Sec. V: runs over disjoint template ranges combine by taking the largest."""
     n_t, n_f, T, k = 80, 300, 40000, 64
