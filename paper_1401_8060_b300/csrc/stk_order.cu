@@ -41,6 +41,8 @@ constexpr int kFineThreads = 256;  // fine kernel
 constexpr int kFineCache = 2048;   // fine kernel: bucket sizes held in registers
 constexpr int kFineShift = 14;     // stored key = coarse << 14 | fine
 constexpr uint32_t kMaxCoarse = 8192;
+constexpr uint32_t kStageSmem = 227 * 1024 - 1024;  // staged coarse kernel: dynamic shared memory budget
+constexpr int kStagedGridMax = 8192;        // blocks beyond which the unstaged coarse kernel runs
 
 struct OrderArgs {
     const OrderMap *maps;  // device array, or NULL: `single`
@@ -215,6 +217,64 @@ __global__ void __launch_bounds__(kKeyThreads) order_coarse_kernel(OrderArgs a, 
     }
 }
 
+// As order_coarse_kernel, for blocks whose positions fit shared memory: the block
+// first sorts its entries by coarse bucket in shared memory, then writes them
+// out in that order, so a warp's stores run through consecutive slots of each
+// bucket (about four per bucket per block) instead of scattering one by one.
+// The block's count per bucket is the next block's prefix minus its own (the
+// last block: the bucket's total).
+__global__ void __launch_bounds__(kKeyThreads) order_coarse_staged_kernel(OrderArgs a,
+                                                                          const uint32_t *__restrict__ keys,
+                                                                          const uint32_t *__restrict__ blockhist,
+                                                                          const uint32_t *__restrict__ total,
+                                                                          const uint32_t *__restrict__ base,
+                                                                          unsigned long long *__restrict__ tmp)
+{
+    extern __shared__ uint32_t sm[];  // cursor[nc], delta[nc], stage[chunk] (8 B), bucket[chunk] (2 B)
+    __shared__ uint32_t wsum[kKeyThreads / 32];
+    const uint32_t nc = a.nc, b = blockIdx.x;
+    const uint64_t chunk = (a.total_n + a.grid - 1) / a.grid;
+    uint32_t *cursor = sm, *delta = sm + nc;
+    unsigned long long *stage = reinterpret_cast<unsigned long long *>(sm + 2 * nc);
+    uint16_t *sbk = reinterpret_cast<uint16_t *>(stage + chunk);
+    // exclusive scan of this block's counts over the buckets: each thread a run of them
+    const uint32_t per = (nc + blockDim.x - 1) / blockDim.x, c0 = threadIdx.x * per;
+    const uint32_t *pre = blockhist + (size_t)b * nc;
+    const uint32_t *nxt = blockhist + (size_t)(b + 1) * nc;
+    const bool last = (int)b + 1 == a.grid;
+    uint32_t run = 0;
+    for (uint32_t q = 0; q < per && c0 + q < nc; ++q) run += (last ? total[c0 + q] : nxt[c0 + q]) - pre[c0 + q];
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    uint32_t inc = run;
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (l >= o) inc += y;
+    }
+    if (l == 31) wsum[w] = inc;
+    __syncthreads();
+    uint32_t acc = inc - run;
+    for (int k = 0; k < w; ++k) acc += wsum[k];
+    for (uint32_t q = 0; q < per && c0 + q < nc; ++q) {
+        const uint32_t c = c0 + q;
+        cursor[c] = acc;
+        delta[c] = base[c] + pre[c] - acc;  // global slot of local position i in bucket c: delta[c] + i
+        acc += (last ? total[c] : nxt[c]) - pre[c];
+    }
+    __syncthreads();
+    uint64_t p0, p1;
+    block_range(a, p0, p1);
+    for (uint64_t p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
+        const uint32_t key = keys[p];
+        const uint32_t c = key >> kFineShift;
+        const uint32_t i = atomicAdd(&cursor[c], 1u);
+        stage[i] = ((unsigned long long)(key & ((1u << kFineShift) - 1u)) << 32) | (uint32_t)p;
+        sbk[i] = (uint16_t)c;
+    }
+    __syncthreads();
+    const uint32_t m = (uint32_t)(p1 > p0 ? p1 - p0 : 0);
+    for (uint32_t i = threadIdx.x; i < m; i += blockDim.x) tmp[delta[sbk[i]] + i] = stage[i];
+}
+
 // One block per coarse bucket: counting sort by the fine key bits; perm[pos] =
 // the template's index within its map.
 __global__ void __launch_bounds__(kFineThreads) order_fine_kernel(OrderArgs a,
@@ -334,6 +394,28 @@ size_t layout_bytes(uint64_t total_n, uint32_t nc, int grid, Layout *L, void *sc
     return off;
 }
 
+// Positions per block the staged coarse kernel holds with nc coarse buckets
+// (8 bytes of entry and 2 of bucket each, after 8 nc bytes of counters).
+uint64_t stage_cap(uint32_t nc) { return (kStageSmem - 8 * (uint64_t)nc) / 10; }
+
+// Blocks of the keys and coarse kernels: twice the SMs when each block's
+// positions fit the staged coarse kernel (or when nothing fits within
+// kStagedGridMax blocks), else the next multiple of that which fits.
+int order_grid(int num_sms, uint64_t total_n, uint32_t nc)
+{
+    const uint64_t g0 = 2 * (uint64_t)std::max(1, num_sms), cap = stage_cap(nc);
+    if ((total_n + g0 - 1) / g0 <= cap) return (int)g0;
+    const uint64_t need = (total_n + cap - 1) / cap, g = (need + g0 - 1) / g0 * g0;
+    return (int)(g <= (uint64_t)kStagedGridMax ? g : g0);
+}
+
+bool staged_ok(uint64_t total_n, int grid, uint32_t nc) { return (total_n + grid - 1) / grid <= stage_cap(nc); }
+
+int staged_smem(uint64_t total_n, int grid, uint32_t nc)
+{
+    return (int)(8 * (uint64_t)nc + 10 * ((total_n + grid - 1) / grid));
+}
+
 cudaError_t run_order(const OrderArgs &oa, uint32_t max_fbits, void *scratch, cudaStream_t st,
                       const uint32_t **perm_out, int *launches)
 {
@@ -353,14 +435,18 @@ cudaError_t run_order(const OrderArgs &oa, uint32_t max_fbits, void *scratch, cu
         order_keys_kernel<false, false><<<oa.grid, kKeyThreads, smem_c, st>>>(oa, L.keys, L.blockhist);
     order_columns_kernel<<<(oa.nc + 31) / 32, 1024, 0, st>>>(L.blockhist, oa.nc, oa.grid, L.total);
     order_bases_kernel<<<1, 1024, 0, st>>>(L.total, oa.nc, L.base);
-    order_coarse_kernel<<<oa.grid, kKeyThreads, smem_c, st>>>(oa, L.keys, L.blockhist, L.base, L.tmp);
+    if (staged_ok(oa.total_n, oa.grid, oa.nc))
+        order_coarse_staged_kernel<<<oa.grid, kKeyThreads, staged_smem(oa.total_n, oa.grid, oa.nc), st>>>(
+            oa, L.keys, L.blockhist, L.total, L.base, L.tmp);
+    else
+        order_coarse_kernel<<<oa.grid, kKeyThreads, smem_c, st>>>(oa, L.keys, L.blockhist, L.base, L.tmp);
     order_fine_kernel<<<oa.nc, kFineThreads, smem_f, st>>>(oa, L.tmp, L.base, L.total, L.perm);
     *perm_out = L.perm;
     if (launches) *launches = 5;
     return cudaGetLastError();
 }
 
-int order_grid(int num_sms) { return 2 * std::max(1, num_sms); }
+
 
 }  // namespace
 
@@ -380,6 +466,8 @@ cudaError_t order_prepare(uint32_t nc, uint32_t max_fbits)
                                   smem_c)) != cudaSuccess ||
         (e = cudaFuncSetAttribute(order_coarse_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_c)) !=
             cudaSuccess ||
+        (e = cudaFuncSetAttribute(order_coarse_staged_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)kStageSmem)) != cudaSuccess ||
         (e = cudaFuncSetAttribute(order_fine_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_f)) !=
             cudaSuccess)
         return e;
@@ -441,7 +529,7 @@ void order_plan_maps(OrderMap *maps, int n_maps, uint32_t &nc, uint32_t &max_fbi
 
 size_t order_scratch_bytes_maps(uint64_t total_n, uint32_t nc, int num_sms)
 {
-    return layout_bytes(total_n, nc, order_grid(num_sms), nullptr, nullptr);
+    return layout_bytes(total_n, nc, order_grid(num_sms, total_n, nc), nullptr, nullptr);
 }
 
 size_t order_scratch_bytes(uint64_t n, int n_f, int n_t, bool general, int num_sms)
@@ -454,7 +542,7 @@ size_t order_scratch_bytes(uint64_t n, int n_f, int n_t, bool general, int num_s
     OrderMap om;
     uint32_t nc;
     single_plan(m, ts, om, nc);
-    return layout_bytes(n, nc, order_grid(num_sms), nullptr, nullptr);
+    return layout_bytes(n, nc, order_grid(num_sms, n, nc), nullptr, nullptr);
 }
 
 cudaError_t launch_order(const MapDev &m, const TrackSet &ts, void *scratch, int num_sms, cudaStream_t st,
@@ -465,7 +553,7 @@ cudaError_t launch_order(const MapDev &m, const TrackSet &ts, void *scratch, int
     single_plan(m, ts, oa.single, oa.nc);
     oa.n_maps = 1;
     oa.total_n = ts.n;
-    oa.grid = order_grid(num_sms);
+    oa.grid = order_grid(num_sms, oa.total_n, oa.nc);
     return run_order(oa, (uint32_t)oa.single.fbits, scratch, st, perm_out, launches);
 }
 
@@ -478,7 +566,7 @@ cudaError_t launch_order_batch(const OrderMap *d_maps, int n_maps, uint64_t tota
     oa.n_maps = n_maps;
     oa.total_n = total_n;
     oa.nc = nc;
-    oa.grid = order_grid(num_sms);
+    oa.grid = order_grid(num_sms, oa.total_n, oa.nc);
     return run_order(oa, max_fbits, scratch, st, perm_out, launches);
 }
 
