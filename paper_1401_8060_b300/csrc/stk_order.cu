@@ -263,12 +263,24 @@ __global__ void __launch_bounds__(kKeyThreads) order_coarse_staged_kernel(OrderA
     __syncthreads();
     uint64_t p0, p1;
     block_range(a, p0, p1);
-    for (uint64_t p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
-        const uint32_t key = keys[p];
-        const uint32_t c = key >> kFineShift;
-        const uint32_t i = atomicAdd(&cursor[c], 1u);
-        stage[i] = ((unsigned long long)(key & ((1u << kFineShift) - 1u)) << 32) | (uint32_t)p;
-        sbk[i] = (uint16_t)c;
+    constexpr int U = 4;  // key loads in flight per thread
+    for (uint64_t pb = p0 + threadIdx.x; pb < p1; pb += U * (uint64_t)blockDim.x) {
+        uint32_t kk[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const uint64_t p = pb + (uint64_t)u * blockDim.x;
+            kk[u] = p < p1 ? keys[p] : 0u;
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const uint64_t p = pb + (uint64_t)u * blockDim.x;
+            if (p < p1) {
+                const uint32_t c = kk[u] >> kFineShift;
+                const uint32_t i = atomicAdd(&cursor[c], 1u);
+                stage[i] = ((unsigned long long)(kk[u] & ((1u << kFineShift) - 1u)) << 32) | (uint32_t)p;
+                sbk[i] = (uint16_t)c;
+            }
+        }
     }
     __syncthreads();
     const uint32_t m = (uint32_t)(p1 > p0 ? p1 - p0 : 0);
