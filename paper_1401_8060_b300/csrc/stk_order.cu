@@ -17,12 +17,13 @@
 // batches); general templates (random control times) put 4 bits each of the
 // start and end column above those, so a warp's templates also cover the same
 // columns.  Map i of a batch owns its own key range and position range.  The
-// sort is two-level, with no global atomics:
+// sort is two-level; its only global atomic is one ticket counter:
 //   keys:    draw each template, write its key, count coarse buckets (the top
 //            key bits) per block in shared memory
-//   columns: per coarse bucket, the exclusive prefix over blocks
-//   bases:   exclusive prefix over coarse buckets (one block)
-//   coarse:  each block places its templates into their coarse buckets
+//   columns: per coarse bucket, the exclusive prefix over blocks and, in the
+//            last of its blocks to finish, the exclusive prefix over buckets
+//   coarse:  each block places its templates into their coarse buckets (sorted
+//            by bucket in shared memory first, when they fit)
 //   fine:    one block per coarse bucket sorts it by the remaining key bits
 //            (counting sort in shared memory) and writes the positions
 // Within a fine bucket the order is whatever the shared atomics give; no result
@@ -108,8 +109,10 @@ __device__ __forceinline__ uint32_t template_key(const TrackSet &ts, uint64_t g,
 // MULTI: several maps (else a.single); GENERAL: general templates (else pinned).
 template <bool MULTI, bool GENERAL>
 __global__ void __launch_bounds__(kKeyThreads, 2) order_keys_kernel(OrderArgs a, uint32_t *__restrict__ keys,
-                                                                    uint32_t *__restrict__ blockhist)
+                                                                    uint32_t *__restrict__ blockhist,
+                                                                    unsigned int *done)
 {
+    if (blockIdx.x == 0 && threadIdx.x == 0) *done = 0u;  // the columns kernel's ticket counter
     extern __shared__ uint32_t hc[];  // [nc]
     for (uint32_t c = threadIdx.x; c < a.nc; c += blockDim.x) hc[c] = 0;
     __syncthreads();
@@ -140,13 +143,39 @@ __global__ void __launch_bounds__(kKeyThreads, 2) order_keys_kernel(OrderArgs a,
     for (uint32_t c = threadIdx.x; c < a.nc; c += blockDim.x) blockhist[(size_t)blockIdx.x * a.nc + c] = hc[c];
 }
 
+// base[c] = exclusive prefix of total over coarse buckets, by one block.
+__device__ void bucket_bases(const uint32_t *total, uint32_t nc, uint32_t *base)
+{
+    __shared__ uint32_t wsum[32];
+    const uint32_t per = (nc + blockDim.x - 1) / blockDim.x;
+    const uint32_t c0 = threadIdx.x * per;
+    uint32_t run = 0;
+    for (uint32_t q = 0; q < per && c0 + q < nc; ++q) run += __ldcg(total + c0 + q);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    uint32_t inc = run;
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (l >= o) inc += y;
+    }
+    if (l == 31) wsum[w] = inc;
+    __syncthreads();
+    uint32_t acc = inc - run;
+    for (int k = 0; k < w; ++k) acc += wsum[k];
+    for (uint32_t q = 0; q < per && c0 + q < nc; ++q) {
+        base[c0 + q] = acc;
+        acc += __ldcg(total + c0 + q);
+    }
+}
+
 // blockhist[b][c] becomes, for each coarse bucket c, the exclusive prefix over
-// blocks b; total[c] the bucket's size.  A block takes 32 buckets (one per lane)
+// blocks b; total[c] the bucket's size; then base[c], the prefix over buckets.  A block takes 32 buckets (one per lane)
 // and its 32 warps a share of the blocks each: warp sums, a scan over warps,
 // then each warp writes its share's prefixes.
 __global__ void __launch_bounds__(1024) order_columns_kernel(uint32_t *__restrict__ blockhist, uint32_t nc,
-                                                             int grid, uint32_t *__restrict__ total)
+                                                             int grid, uint32_t *__restrict__ total,
+                                                             uint32_t *__restrict__ base, unsigned int *done)
 {
+    __shared__ bool last;
     __shared__ uint32_t part[32][33];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const uint32_t c = blockIdx.x * 32 + lane;
@@ -171,31 +200,15 @@ __global__ void __launch_bounds__(1024) order_columns_kernel(uint32_t *__restric
         }
         if (w == 0) total[c] = all;
     }
-}
-
-// base[c] = exclusive prefix of total over coarse buckets; one block.
-__global__ void __launch_bounds__(1024) order_bases_kernel(const uint32_t *__restrict__ total, uint32_t nc,
-                                                           uint32_t *__restrict__ base)
-{
-    __shared__ uint32_t wsum[32];
-    const uint32_t per = (nc + blockDim.x - 1) / blockDim.x;
-    const uint32_t c0 = threadIdx.x * per;
-    uint32_t run = 0;
-    for (uint32_t q = 0; q < per && c0 + q < nc; ++q) run += total[c0 + q];
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    uint32_t inc = run;
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
-        if (l >= o) inc += y;
-    }
-    if (l == 31) wsum[w] = inc;
+    // the last block to finish (a ticket counter, zeroed by the keys kernel) also
+    // takes the prefix over buckets; no block waits for another
+    __threadfence();
     __syncthreads();
-    uint32_t acc = inc - run;
-    for (int k = 0; k < w; ++k) acc += wsum[k];
-    for (uint32_t q = 0; q < per && c0 + q < nc; ++q) {
-        base[c0 + q] = acc;
-        acc += total[c0 + q];
-    }
+    if (threadIdx.x == 0) last = atomicAdd(done, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    bucket_bases(total, nc, base);
 }
 
 // Each block places its positions into their coarse buckets: tmp[slot] = fine << 32 | position.
@@ -378,12 +391,14 @@ int bit_length(uint32_t x)
 
 struct Layout {
     uint32_t *keys, *perm, *blockhist, *total, *base;
+    unsigned int *done;
     unsigned long long *tmp;
 };
 
 size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 
-// Scratch layout (and its size): tmp[n] u64, keys[n], perm[n], blockhist[grid][nc], total[nc], base[nc].
+// Scratch layout (and its size): tmp[n] u64, keys[n], perm[n], blockhist[grid][nc], total[nc], base[nc],
+// the columns kernel's ticket counter.
 size_t layout_bytes(uint64_t total_n, uint32_t nc, int grid, Layout *L, void *scratch)
 {
     size_t off = 0;
@@ -394,6 +409,7 @@ size_t layout_bytes(uint64_t total_n, uint32_t nc, int grid, Layout *L, void *sc
     };
     const size_t o_tmp = take(total_n * 8), o_keys = take(total_n * 4), o_perm = take(total_n * 4);
     const size_t o_bh = take((size_t)nc * grid * 4), o_tot = take((size_t)nc * 4), o_base = take((size_t)nc * 4);
+    const size_t o_done = take(4);
     if (L) {
         unsigned char *s = static_cast<unsigned char *>(scratch);
         L->tmp = reinterpret_cast<unsigned long long *>(s + o_tmp);
@@ -402,6 +418,7 @@ size_t layout_bytes(uint64_t total_n, uint32_t nc, int grid, Layout *L, void *sc
         L->blockhist = reinterpret_cast<uint32_t *>(s + o_bh);
         L->total = reinterpret_cast<uint32_t *>(s + o_tot);
         L->base = reinterpret_cast<uint32_t *>(s + o_base);
+        L->done = reinterpret_cast<unsigned int *>(s + o_done);
     }
     return off;
 }
@@ -440,13 +457,12 @@ cudaError_t run_order(const OrderArgs &oa, uint32_t max_fbits, void *scratch, cu
     if (cs == cudaStreamCaptureStatusNone && (e = order_prepare(oa.nc, max_fbits)) != cudaSuccess) return e;
     // batches hold pinned templates only; one map may hold either kind
     if (oa.maps)
-        order_keys_kernel<true, false><<<oa.grid, kKeyThreads, smem_c, st>>>(oa, L.keys, L.blockhist);
+        order_keys_kernel<true, false><<<oa.grid, kKeyThreads, smem_c, st>>>(oa, L.keys, L.blockhist, L.done);
     else if (oa.single.ts.general)
-        order_keys_kernel<false, true><<<oa.grid, kKeyThreads, smem_c, st>>>(oa, L.keys, L.blockhist);
+        order_keys_kernel<false, true><<<oa.grid, kKeyThreads, smem_c, st>>>(oa, L.keys, L.blockhist, L.done);
     else
-        order_keys_kernel<false, false><<<oa.grid, kKeyThreads, smem_c, st>>>(oa, L.keys, L.blockhist);
-    order_columns_kernel<<<(oa.nc + 31) / 32, 1024, 0, st>>>(L.blockhist, oa.nc, oa.grid, L.total);
-    order_bases_kernel<<<1, 1024, 0, st>>>(L.total, oa.nc, L.base);
+        order_keys_kernel<false, false><<<oa.grid, kKeyThreads, smem_c, st>>>(oa, L.keys, L.blockhist, L.done);
+    order_columns_kernel<<<(oa.nc + 31) / 32, 1024, 0, st>>>(L.blockhist, oa.nc, oa.grid, L.total, L.base, L.done);
     if (staged_ok(oa.total_n, oa.grid, oa.nc))
         order_coarse_staged_kernel<<<oa.grid, kKeyThreads, staged_smem(oa.total_n, oa.grid, oa.nc), st>>>(
             oa, L.keys, L.blockhist, L.total, L.base, L.tmp);
@@ -454,7 +470,7 @@ cudaError_t run_order(const OrderArgs &oa, uint32_t max_fbits, void *scratch, cu
         order_coarse_kernel<<<oa.grid, kKeyThreads, smem_c, st>>>(oa, L.keys, L.blockhist, L.base, L.tmp);
     order_fine_kernel<<<oa.nc, kFineThreads, smem_f, st>>>(oa, L.tmp, L.base, L.total, L.perm);
     *perm_out = L.perm;
-    if (launches) *launches = 5;
+    if (launches) *launches = 4;
     return cudaGetLastError();
 }
 
