@@ -330,11 +330,13 @@ __global__ void __launch_bounds__(kFineThreads) order_fine_kernel(OrderArgs a,
     unsigned long long r[kPer];
     if (cached) {
 #pragma unroll
-        for (int u = 0; u < kPer; ++u) {
+        for (int u = 0; u < kPer; ++u) {  // every load in flight before the first atomic
             const uint32_t i = threadIdx.x + u * kFineThreads;
             r[u] = i < n ? tmp[b0 + i] : 0ull;
-            if (i < n) atomicAdd(&hf[(uint32_t)(r[u] >> 32)], 1u);
         }
+#pragma unroll
+        for (int u = 0; u < kPer; ++u)
+            if (threadIdx.x + u * kFineThreads < n) atomicAdd(&hf[(uint32_t)(r[u] >> 32)], 1u);
     } else {
         for (uint64_t i = threadIdx.x; i < n; i += blockDim.x)
             atomicAdd(&hf[(uint32_t)(tmp[(uint64_t)b0 + i] >> 32)], 1u);
