@@ -541,8 +541,8 @@ cudaError_t launch_score_generated(const MapDev &m, const TrackSet &ts, float *o
 bool score_wants_order(const MapDev &m, const TrackSet &ts, const Tuning &tu);
 
 // Coherent-order pre-pass (stk_order.cu).  One map: the key is 7 bits per
-// control bin (general templates: 4 bits each of the start and end column and
-// of the bins); *perm_out = the scoring order inside scratch (perm[p] =
+// control bin (general templates: 6 bits each of the start and end column, 3 of
+// each bin); *perm_out = the scoring order inside scratch (perm[p] =
 // template index relative to the range's offset).
 size_t order_scratch_bytes(uint64_t n, int n_f, int n_t, bool general, int num_sms);
 cudaError_t launch_order(const MapDev &m, const TrackSet &ts, void *scratch, int num_sms, cudaStream_t st,
@@ -550,11 +550,12 @@ cudaError_t launch_order(const MapDev &m, const TrackSet &ts, void *scratch, int
 // Many maps: map i's templates take positions pos0 .. pos0 + n - 1 of perm
 // (values relative to its offset) and coarse buckets from coarse0.
 struct OrderMap {
-    TrackSet ts;       // with ts.general: key = (t0, t2, Z-order of the bins), 4 + 4 + 12 bits
+    TrackSet ts;       // with ts.general: key = (t0, t2, Z-order of the bins), tbits + tbits + 9 bits
     uint32_t n_f;
     uint32_t n_t;
     int shift;         // control bins >> shift form the key
-    int tshift;        // general templates: control times >> tshift (4 bits each)
+    int tshift;        // general templates: control times >> tshift (tbits bits each)
+    int tbits;
     int fbits;         // key bits below the coarse bucket
     uint32_t coarse0;  // first coarse bucket
     uint32_t pos0;     // first position

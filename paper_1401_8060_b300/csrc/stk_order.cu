@@ -14,9 +14,9 @@
 //
 // The order sorts template positions by a key: the Morton (Z-order) interleave
 // of the leading bits of f0, f1, f2 (7 each for one map, fewer per map in large
-// batches); general templates (random control times) put 4 bits each of the
-// start and end column above those, so a warp's templates also cover the same
-// columns.  Map i of a batch owns its own key range and position range.  The
+// batches); general templates (random control times) put 6 bits each of the
+// start and end column above 3 bits per bin, so a warp's templates also cover
+// the same columns.  Map i of a batch owns its own key range and position range.  The
 // sort is two-level; its only global atomic is one ticket counter:
 //   keys:    draw each template, write its key, count coarse buckets (the top
 //            key bits) per block in shared memory
@@ -42,6 +42,8 @@ constexpr int kFineThreads = 256;  // fine kernel
 constexpr int kFineCache = 2048;   // fine kernel: bucket sizes held in registers
 constexpr int kFineShift = 14;     // stored key = coarse << 14 | fine
 constexpr uint32_t kMaxCoarse = 8192;
+constexpr int kGenTimeBits = 6;             // general templates: key bits of the start and of the end column
+constexpr int kGenBinBits = 3;              // general templates: key bits of each control bin
 constexpr uint32_t kStageSmem = 227 * 1024 - 1024;  // staged coarse kernel: dynamic shared memory budget
 constexpr int kStagedGridMax = 8192;        // blocks beyond which the unstaged coarse kernel runs
 
@@ -91,7 +93,7 @@ __device__ __forceinline__ void block_range(const OrderArgs &a, uint64_t &p0, ui
 // start and end column above them), split into coarse bucket and fine bits.
 template <bool GENERAL>
 __device__ __forceinline__ uint32_t template_key(const TrackSet &ts, uint64_t g, uint32_t n_f, uint32_t n_t, int shift,
-                                                 int tshift, int fbits, uint32_t coarse0)
+                                                 int tshift, int tbits, int fbits, uint32_t coarse0)
 {
     uint32_t f[3];
     double tau;
@@ -100,7 +102,7 @@ __device__ __forceinline__ uint32_t template_key(const TrackSet &ts, uint64_t g,
     if (GENERAL) {  // start and end column first: a warp's templates cover the same columns
         uint32_t t[3];
         draw_times(ts.seed, g, n_t, (uint32_t)ts.t_min, t);
-        key |= (((t[0] >> tshift) << 4) | (t[2] >> tshift)) << 12;
+        key |= (((t[0] >> tshift) << tbits) | (t[2] >> tshift)) << (3 * kGenBinBits);
     }
     const uint32_t c = coarse0 + (key >> fbits);
     return (c << kFineShift) | (key & ((1u << fbits) - 1u));
@@ -125,7 +127,7 @@ __global__ void __launch_bounds__(kKeyThreads, 2) order_keys_kernel(OrderArgs a,
                 while (mi + 1 < a.n_maps && (uint64_t)a.maps[mi + 1].pos0 <= p) ++mi;
                 const OrderMap &om = a.maps[mi];
                 const uint32_t k = template_key<GENERAL>(om.ts, om.ts.offset + (p - om.pos0), om.n_f, om.n_t,
-                                                         om.shift, om.tshift, om.fbits, om.coarse0);
+                                                         om.shift, om.tshift, om.tbits, om.fbits, om.coarse0);
                 keys[p] = k;
                 atomicAdd(&hc[k >> kFineShift], 1u);
             }
@@ -134,7 +136,7 @@ __global__ void __launch_bounds__(kKeyThreads, 2) order_keys_kernel(OrderArgs a,
         const OrderMap &om = a.single;  // read from the parameters where used
         for (uint64_t p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
             const uint32_t k = template_key<GENERAL>(om.ts, om.ts.offset + p, om.n_f, om.n_t, om.shift, om.tshift,
-                                                     om.fbits, 0u);
+                                                     om.tbits, om.fbits, 0u);
             keys[p] = k;
             atomicAdd(&hc[k >> kFineShift], 1u);
         }
@@ -513,11 +515,14 @@ void single_plan(const MapDev &m, const TrackSet &ts, OrderMap &om, uint32_t &nc
     om.ts = ts;
     om.n_f = (uint32_t)m.n_f;
     om.n_t = (uint32_t)m.n_t;
-    int bits, tbits;
-    order_shape(m.n_f, ts.general ? 4 : 7, om.shift, bits);
-    order_shape(m.n_t, 4, om.tshift, tbits);
-    // general keys place the time bits at bit 12 whatever the bin bits in use
-    const int kb = ts.general ? 20 : 3 * bits;
+    int bits;
+    order_shape(m.n_f, ts.general ? kGenBinBits : 7, om.shift, bits);
+    order_shape(m.n_t, kGenTimeBits, om.tshift, om.tbits);
+    // general keys: 2 x 6 bits of start and end column above 3 x 3 bits of the
+    // bins (at bit 9 whatever the bin bits in use); the columns group a warp's
+    // templates more than the bins do (measured: 1.26 ms with 4 bits for each
+    // column and bin, 1.22 ms with 6 and 3 or 6 and 4)
+    const int kb = ts.general ? 3 * kGenBinBits + 2 * om.tbits : 3 * bits;
     const int cb = std::min(kb, 12);
     om.fbits = kb - cb;
     om.coarse0 = 0;
@@ -545,10 +550,13 @@ void order_plan_maps(OrderMap *maps, int n_maps, uint32_t &nc, uint32_t &max_fbi
     max_fbits = 0;
     for (int i = 0; i < n_maps; ++i) {
         OrderMap &om = maps[i];
-        int bits, tbits;
-        order_shape((int)om.n_f, om.ts.general ? std::min(4, max_bits) : max_bits, om.shift, bits);
-        order_shape((int)om.n_t, 4, om.tshift, tbits);
-        const int kb = om.ts.general ? 20 : 3 * bits;
+        int bits;
+        order_shape((int)om.n_f, om.ts.general ? std::min(kGenBinBits, max_bits) : max_bits, om.shift, bits);
+        // general keys: time bits limited so that at most kFineShift bits lie below the coarse bucket
+        order_shape((int)om.n_t,
+                    std::max(0, std::min(kGenTimeBits, (kFineShift + cbits - 3 * kGenBinBits) / 2)), om.tshift,
+                    om.tbits);
+        const int kb = om.ts.general ? 3 * kGenBinBits + 2 * om.tbits : 3 * bits;
         const int cb = std::min(kb, cbits);
         om.fbits = kb - cb;
         om.coarse0 = nc;
