@@ -77,3 +77,42 @@ def test_no_oracle_on_product_path():
                 text = open(os.path.join(dirpath, f)).read()
                 assert not re.search(r"^\s*(import|from)\s+oracle", text, flags=re.M), f
                 assert "stk_oracle" not in text and "liboracle" not in text, f
+
+
+C_PROGRAM = r"""
+#include <stdio.h>
+#include <string.h>
+#include "stk.h"
+
+int main(void)
+{
+    /* the boundary is plain C: these calls need no GPU and must reject bad arguments */
+    stk_hit h;
+    if (sizeof(h) != 40) return 1;
+    if (stk_create(NULL, 0, NULL) != STK_EINVAL) return 2;
+    if (stk_set_tracks(NULL, 1, 0, 0, 0.0) != STK_EINVAL) return 3;
+    if (stk_score(NULL, NULL, 1, NULL, 0) != STK_EINVAL) return 4;
+    if (stk_sync(NULL) != STK_EINVAL) return 5;
+    stk_destroy(NULL);
+    stk_free_map(NULL);
+    const char *msg = stk_last_error(NULL);
+    if (msg == NULL) return 6;
+    if (stk_version() < 100) return 7;
+    printf("ok %d\n", stk_version());
+    return 0;
+}
+"""
+
+
+def test_header_compiles_as_c_and_links(built, tmp_path):
+    """A C99 program (gcc, no C++) includes include/stk.h, links libstk.so and
+    calls the argument checks of the ABI."""
+    src = tmp_path / "use_stk.c"
+    exe = tmp_path / "use_stk"
+    src.write_text(C_PROGRAM)
+    libdir = os.path.dirname(built)
+    subprocess.run(["gcc", "-std=c99", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"), str(src), "-L",
+                    libdir, "-lstk", "-Wl,-rpath," + libdir, "-o", str(exe)], check=True)
+    run = subprocess.run([str(exe)], capture_output=True, text=True)
+    assert run.returncode == 0, (run.returncode, run.stdout, run.stderr)
+    assert run.stdout.startswith("ok ")
