@@ -269,10 +269,10 @@ def main():
     import paper_1401_8060_b300 as stk
     from paper_1401_8060_b300 import _lib, build, search, synth
 
+    torch.cuda.set_device(local)             # before the process group: NCCL binds the current device
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", init_method="env://")
-    torch.cuda.set_device(local)
     build.build()
 
     w = synth.WORKLOADS[WORKLOAD]
@@ -532,11 +532,17 @@ def main():
             ctx.update_map(mm, y_pin, s_pin)
             ctx.score(mm, K)
         torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
         t0 = time.perf_counter()
         for _ in range(args.steps):
             ctx.update_map(mm, y_pin, s_pin)   # this step's map: host -> device copy + pack
             h = ctx.score(mm, K)               # host output: waits for the result
         dt_serial = (time.perf_counter() - t0) / args.steps
+        if world > 1:                          # the slowest rank's time, as for the device-timed value
+            tt = torch.tensor([dt_serial], device="cuda")
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            dt_serial = float(tt.item())
         mm.close()
         assert np.array_equal(h["index"], hits["index"]) or world > 1
 
@@ -568,9 +574,15 @@ def main():
             torch.cuda.synchronize()
 
         pipelined(4)
+        if world > 1:
+            dist.barrier()
         t0 = time.perf_counter()
         pipelined(args.steps)
         dt = (time.perf_counter() - t0) / args.steps
+        if world > 1:
+            tt = torch.tensor([dt], device="cuda")
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            dt = float(tt.item())
         ectx.sync()
         hp = out_host[(args.steps - 1) % 2].numpy().view(stk.HIT_DTYPE)
         assert np.array_equal(hp["index"], hits["index"]) or world > 1
