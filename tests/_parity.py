@@ -1,6 +1,6 @@
 """Helpers for comparing the CUDA path with the FP64 oracle.
 
-Tolerance (spec bar: SNRs within 1e-5 relative in FP32).  Relative error
+Tolerance: SNRs within 1e-5 relative of the FP64 oracle in FP32.  Relative error
 is ill-conditioned for SNRs near zero, so each template is held to
     |SNR_gpu - SNR_oracle| <= RTOL * max(|SNR_oracle|, sum_j |z_j| / norm)
 where norm is sqrt(sum_j w_j) (weighted) or N (paper form): the FP32 pixel
