@@ -110,8 +110,8 @@ def inject(y: np.ndarray, bins: np.ndarray, amplitude, tau_s: float, f_min: floa
     y[j, b] = (y[j, b].astype(np.complex128) + sig).astype(np.complex64)
 
 
-# Workloads: the tiny 200 x 100 map, the realistic 500 x 1600 map (sizes and bands of the
-# searches of Sec. IV-V), its FP16 form, the 256 ragged maps of a batch and the refinement run.
+# Workloads: a tiny 200 x 100 map and the realistic 500 x 1600 map (the bands and
+# resolutions of the paper's searches).
 WORKLOADS = {
     "tiny": dict(n_t=200, n_f=100, f_min=100.0, df=1.0, n_tracks=10_000, seed=1,
                  tau_max=0.010, k=16, noise_seed=11),
