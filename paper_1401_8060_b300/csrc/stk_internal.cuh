@@ -264,10 +264,12 @@ __host__ __device__ __forceinline__ int32_t gen_step(const GenCurve &c, int64_t 
 // farther than `margin` from a rounding boundary; otherwise the exact test does.
 // Error of the estimate (IEEE sqrt and divide, FMA evaluation): Delta_j < 2^27 is
 // rounded once (2^-24), s = sqrt once more, D = s + B and xi = u / D each add one
-// rounding, so |d xi| <= 4 2^-24 xi; f = f0 + xi (G + F xi) then errs by at most
-// (|G| + 2|F|) |d xi| + 3 ulp(f0 + |G| + |F|) < 2.4e-7 (|G| + 2|F|) + 3.6e-7 (f0 + |G| + |F|),
-// and f + 1/2 one more ulp.  The margin takes twice that (the largest error seen
-// over 4e5 random curve-column pairs is 0.28 of the bound).
+// rounding, so |d xi| <= 4 2^-24 xi <= 4 2^-24.  f' = G + 2 F xi is linear, so on [0, 1]
+// |f'| <= Gmax = max(|G|, |G + 2F|); f is a convex combination of the control bins, so
+// f and xi (G + F xi) = f - f0 lie in [-fmax, fmax], fmax = max(f0, f1, f2).  The inner
+// FMA (G + F xi) and the outer one (f0 + xi inner) each round once, f + 1/2 once more:
+// the estimate of f + 1/2 errs by at most 2^-24 (4.01 (Gmax + 1) + 3.01 (fmax + 1) + 1)
+// < 2.4e-7 (Gmax + 1) + 1.8e-7 (fmax + 1) + 6e-8.  The margin takes twice that.
 struct GenFilter {
     float F, G, f0, B, margin;
 };
@@ -279,8 +281,12 @@ __host__ __device__ __forceinline__ GenFilter gen_filter(const GenCurve &c)
     g.G = (float)c.G;
     g.f0 = (float)c.f0;
     g.B = (float)c.B;
-    const float aF = fabsf(g.F), aG = fabsf(g.G);
-    g.margin = 2.f * (2.4e-7f * (aG + 2.f * aF) + 3.6e-7f * (g.f0 + aG + aF + 1.f)) + 1e-6f;
+    const int32_t f1 = c.f0 + c.G / 2, f2 = c.f0 + c.G + c.F;  // G = 2 (f1 - f0), F = f0 - 2 f1 + f2
+    const int32_t aG = c.G < 0 ? -c.G : c.G, aG2 = c.G + 2 * c.F < 0 ? -(c.G + 2 * c.F) : c.G + 2 * c.F;
+    const float gmax = (float)(aG > aG2 ? aG : aG2);
+    const int32_t f12 = f1 > f2 ? f1 : f2;
+    const float fmax = (float)(c.f0 > f12 ? c.f0 : f12);
+    g.margin = 2.f * (2.4e-7f * (gmax + 1.f) + 1.8e-7f * (fmax + 1.f) + 6e-8f) + 1e-6f;
     return g;
 }
 
