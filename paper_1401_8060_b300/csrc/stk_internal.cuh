@@ -310,17 +310,8 @@ __device__ __forceinline__ bool gen_estimate(const GenCurve &c, const GenFilter 
 
 __device__ __forceinline__ int32_t gen_pixel(const GenCurve &c, const GenFilter &g, int64_t j, int32_t n_f)
 {
-    const int32_t du = (int32_t)(j - c.t0);
-    const int32_t Dl = c.B * c.B + 4 * c.A * du;   // exact, < 2^27
-    const float s = __fsqrt_rn((float)Dl);
-    const float xi = __fdiv_rn((float)(2 * du), __fadd_rn(s, g.B));
-    const float fx = fmaf(xi, fmaf(g.F, xi, g.G), g.f0);
-    const float h = fx + 0.5f;
-    const float k = floorf(h);
-    const float d = h - k;
-    int32_t b = (int32_t)k;
-    b = b < 0 ? 0 : (b > n_f - 1 ? n_f - 1 : b);
-    if (d > g.margin && d < 1.f - g.margin) return b;
+    int32_t b;
+    if (gen_estimate(c, g, j, n_f, b)) return b;
     return gen_step(c, j, b, n_f);                 // near a boundary: exact
 }
 
