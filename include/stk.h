@@ -238,6 +238,21 @@ STK_API int stk_interp_forward(stk_ctx *ctx, const stk_map *map, const float *f3
 STK_API int stk_interp_adjoint(stk_ctx *ctx, const stk_map *map, const float *f3_dev, const float *tau_dev,
                                const float *g_dev, uint64_t n, float *grad_f3_dev, float *grad_tau_dev);
 
+/* Gradient ascent of n continuous templates' SNR (the follow-up of the loudest
+ * events, Sec. V), all steps on the device.  Each step evaluates the SNR and its
+ * gradient (stk_interp_adjoint with g = 1) and takes one Adam step (betas 0.9,
+ * 0.999, eps 1e-8, bias-corrected) on the loss -SNR over (f0, f1, f2) in bins
+ * (learning rate lr_bins) and u = tau / tau_max (learning rate lr_tau_frac),
+ * then projects onto f in [0, n_f - 1] and |u| <= 1.  f3_dev float [n][3] and
+ * tau_dev float [n] (seconds) are device memory, caller-owned, updated in place.
+ * hist_dev (optional, NULL to skip): float [steps + 1][n] device memory, row t
+ * the SNRs before step t + 1 (row steps: after the last step).  Context scratch:
+ * 36 bytes per template.  2 launches per step, plus 1, plus 1 when hist_dev is
+ * given.  Errors: STK_EINVAL (NULL pointer, steps < 0, tau_max <= 0, negative or
+ * non-finite rates), STK_ENOMEM, STK_ECUDA. */
+STK_API int stk_refine(stk_ctx *ctx, const stk_map *map, float *f3_dev, float *tau_dev, uint64_t n, int steps,
+                       float lr_bins, float lr_tau_frac, float tau_max, float *hist_dev);
+
 /* Wait for the context's stream and report the first deferred error raised
  * by a kernel since the last stk_sync (bounded-wait timeout, bad explicit
  * template).  Clears it. */

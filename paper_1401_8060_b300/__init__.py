@@ -278,6 +278,21 @@ class Context:
                                              C.c_void_p(gt.data_ptr())))
         return gf, gt
 
+    def refine(self, m: Map, f3, tau, tau_max: float, steps: int = 50, lr_bins: float = 0.25,
+               lr_tau_frac: float = 0.02, history: bool = True):
+        """stk_refine: `steps` Adam steps of gradient ascent on the device.  Returns new
+        tensors (f3, tau, snr_history [steps + 1][n] or None); the inputs are not modified."""
+        torch = self._torch
+        self._bind_stream()
+        f = f3.detach().to(torch.float32).contiguous().clone()
+        t = tau.detach().to(torch.float32).contiguous().clone()
+        n = t.numel()
+        h = torch.empty((steps + 1, n), dtype=torch.float32, device=t.device) if history else None
+        self._check(lib().stk_refine(self._h, m.handle, C.c_void_p(f.data_ptr()), C.c_void_p(t.data_ptr()), n,
+                                     int(steps), float(lr_bins), float(lr_tau_frac), float(tau_max),
+                                     C.c_void_p(h.data_ptr() if h is not None else 0)))
+        return f, t, h
+
     def sync(self):
         """stk_sync: wait and raise the first deferred kernel error."""
         self._check(lib().stk_sync(self._h))
@@ -390,21 +405,6 @@ def refine(ctx: Context, m: Map, f3, tau, tau_max: float, steps: int = 50, lr_bi
            lr_tau_frac: float = 0.02):
     """Gradient ascent of the interpolated SNR over (f0, f1, f2, tau) of each template
     (Adam; f in bins, tau in units of tau_max), projected onto f in [0, n_f - 1] and
-    |tau| <= tau_max.  Returns (f3, tau, snr_history [steps + 1][n]) as tensors."""
-    import torch
-    f = f3.detach().to(torch.float32).clone().requires_grad_(True)
-    u = (tau.detach().to(torch.float32) / tau_max).clone().requires_grad_(True)
-    opt = torch.optim.Adam([{"params": [f], "lr": lr_bins}, {"params": [u], "lr": lr_tau_frac}])
-    hist = []
-    for _ in range(steps):
-        opt.zero_grad()
-        snr = interp_snr(ctx, m, f, u * tau_max)
-        hist.append(snr.detach().clone())
-        (-snr.sum()).backward()
-        opt.step()
-        with torch.no_grad():
-            f.clamp_(0.0, float(m.n_f - 1))
-            u.clamp_(-1.0, 1.0)
-    final = ctx.interp_forward(m, f.detach(), u.detach() * tau_max)
-    hist.append(final)
-    return f.detach(), (u.detach() * tau_max), torch.stack(hist)
+    |tau| <= tau_max, every step on the device (stk_refine).  Returns (f3, tau,
+    snr_history [steps + 1][n]) as tensors."""
+    return ctx.refine(m, f3, tau, tau_max, steps, lr_bins, lr_tau_frac)

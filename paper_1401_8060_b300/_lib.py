@@ -51,6 +51,7 @@ SIGNATURES = [
     ("stk_score_explicit_general", C.c_int, [_vp, _vp, _vp, _vp, _vp, C.c_uint64, _vp]),
     ("stk_interp_forward", C.c_int, [_vp, _vp, _vp, _vp, C.c_uint64, _vp]),
     ("stk_interp_adjoint", C.c_int, [_vp, _vp, _vp, _vp, _vp, C.c_uint64, _vp, _vp]),
+    ("stk_refine", C.c_int, [_vp, _vp, _vp, _vp, C.c_uint64, C.c_int, C.c_float, C.c_float, C.c_float, _vp]),
     ("stk_batch_create", C.c_int, [_vp, _vp, C.c_int, _vp, _vp, _vp, C.c_double, C.POINTER(_vp)]),
     ("stk_batch_destroy", None, [_vp]),
     ("stk_batch_score", C.c_int, [_vp, C.c_int, _vp, C.c_uint]),

@@ -12,6 +12,7 @@
 
 #include "stk_internal.cuh"
 #include "stk_objects.cuh"
+#include "stk_refine.cuh"
 
 using namespace stk;
 
@@ -230,6 +231,7 @@ void stk_destroy(stk_ctx *c)
     cudaFree(c->stage_y);
     cudaFree(c->stage_s);
     cudaFree(c->order_buf);
+    cudaFree(c->refine_buf);
     for (auto &ev : c->ev)
         if (ev) cudaEventDestroy(ev);
     delete c;
@@ -666,6 +668,26 @@ int stk_interp_adjoint(stk_ctx *c, const stk_map *m, const float *f3, const floa
     CUDA_TRY(c, cudaSetDevice(c->device));
     cudaError_t e = launch_interp(m->dev, f3, tau, g, n, nullptr, grad_f3, grad_tau, true, c->stream);
     if (e != cudaSuccess) return set_err(c, STK_ECUDA, "interpolated adjoint launch: %s", cudaGetErrorString(e));
+    return STK_OK;
+}
+
+int stk_refine(stk_ctx *c, const stk_map *m, float *f3, float *tau, uint64_t n, int steps, float lr_bins,
+               float lr_tau_frac, float tau_max, float *hist)
+{
+    if (!c) return STK_EINVAL;
+    if (!m || m->ctx != c) return set_err(c, STK_EINVAL, "map is NULL or belongs to another context");
+    if (steps < 0) return set_err(c, STK_EINVAL, "steps < 0");
+    if (!(tau_max > 0.f) || !std::isfinite(tau_max)) return set_err(c, STK_EINVAL, "tau_max must be > 0 and finite");
+    if (!std::isfinite(lr_bins) || !std::isfinite(lr_tau_frac) || lr_bins < 0.f || lr_tau_frac < 0.f)
+        return set_err(c, STK_EINVAL, "learning rates must be >= 0 and finite");
+    if (n == 0) return STK_OK;
+    if (!f3 || !tau) return set_err(c, STK_EINVAL, "NULL pointer");
+    CUDA_TRY(c, cudaSetDevice(c->device));
+    int rc = ensure(c, &c->refine_buf, &c->refine_cap, refine_scratch_bytes(n));
+    if (rc) return rc;
+    cudaError_t e = launch_refine(m->dev, f3, tau, n, steps, lr_bins, lr_tau_frac, tau_max, hist, c->refine_buf,
+                                  c->stream);
+    if (e != cudaSuccess) return set_err(c, STK_ECUDA, "refinement launch: %s", cudaGetErrorString(e));
     return STK_OK;
 }
 

@@ -35,6 +35,8 @@ struct stk_ctx {
     size_t stage_s_cap = 0;
     void *order_buf = nullptr;     // coherent-order pre-pass of the slab kernel
     size_t order_cap = 0;
+    void *refine_buf = nullptr;    // refinement: Adam moments and gradients
+    size_t refine_cap = 0;
     Tuning tune{};
     ScorePlan plan{};
     bool profiling = false;

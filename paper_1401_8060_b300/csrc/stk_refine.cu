@@ -10,13 +10,19 @@
 //   SNR = S / sqrt(W) (weighted) or S / N (paper form) -- Eq. 7 at integer bins.
 // The forward kernel returns SNR; the adjoint kernel returns g * dSNR/d(f0, f1,
 // f2, tau) for an upstream gradient g, differentiating each of those steps.
-// One thread per template.  Sums and the pixel arithmetic are FP32; the curve
-// position x_j and the phase argument are FP64, since FP32 resolves x_j ~ 10^3
-// only to 6e-5 bins.
+// One warp per template: lane l takes the columns j = l (mod 32) in order, then
+// the lanes' partial sums meet in a fixed shuffle tree (deterministic).  Sums and
+// the pixel arithmetic are FP32; the curve position x_j and the phase argument are
+// FP64, since FP32 resolves x_j ~ 10^3 only to 6e-5 bins (with one thread per
+// template, a few SMs' FP64 units did all of that work: 1 ms a step for 1024
+// templates).
 #include <cuda_fp16.h>
+
+#include <cmath>
 
 #include "stk_internal.cuh"
 #include "stk_pixel.cuh"
+#include "stk_refine.cuh"
 
 namespace stk {
 
@@ -51,7 +57,8 @@ __global__ void __launch_bounds__(128) interp_kernel(MapDev m, const float *__re
                                                      uint64_t n, float *__restrict__ snr_out,
                                                      float *__restrict__ gf3, float *__restrict__ gtau)
 {
-    const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const uint64_t i = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;  // the same for a whole warp
+    const int lane = threadIdx.x & 31;
     if (i >= n) return;
     const double f0 = f3[3 * i], f1 = f3[3 * i + 1], f2 = f3[3 * i + 2];
     const double tau = tau_in[i];
@@ -62,7 +69,7 @@ __global__ void __launch_bounds__(128) interp_kernel(MapDev m, const float *__re
     const float two_pi = 6.28318530717958647692f;
     float S = 0.f, W = 0.f;
     float dS0 = 0.f, dS1 = 0.f, dS2 = 0.f, dS3 = 0.f, dW0 = 0.f, dW1 = 0.f, dW2 = 0.f;
-    for (int j = 0; j < n_t; ++j) {
+    for (int j = lane; j < n_t; j += 32) {
         const double jd = (double)j;
         double x = ((a2 * jd + a1) * jd + a0) * inv_M2;
         bool clamped = false;
@@ -99,13 +106,25 @@ __global__ void __launch_bounds__(128) interp_kernel(MapDev m, const float *__re
             dS3 = fmaf(-im, two_pi * (float)(m.f_min + x * m.df), dS3);
         }
     }
+    for (int o = 16; o > 0; o >>= 1) {
+        S += __shfl_xor_sync(0xffffffffu, S, o);
+        W += __shfl_xor_sync(0xffffffffu, W, o);
+        if (ADJOINT) {
+            dS0 += __shfl_xor_sync(0xffffffffu, dS0, o);
+            dS1 += __shfl_xor_sync(0xffffffffu, dS1, o);
+            dS2 += __shfl_xor_sync(0xffffffffu, dS2, o);
+            dS3 += __shfl_xor_sync(0xffffffffu, dS3, o);
+            dW0 += __shfl_xor_sync(0xffffffffu, dW0, o);
+            dW1 += __shfl_xor_sync(0xffffffffu, dW1, o);
+            dW2 += __shfl_xor_sync(0xffffffffu, dW2, o);
+        }
+    }
+    if (lane != 0) return;
     const bool varying = WMODE != WMODE_CONST && !m.paper;
     const float scale = varying ? rsqrtf(W) : (float)m.norm;
-    if (!ADJOINT) {
-        snr_out[i] = S * scale;
-        return;
-    }
-    const float gi = g[i];
+    if (!ADJOINT || snr_out) snr_out[i] = S * scale;
+    if (!ADJOINT) return;
+    const float gi = g ? g[i] : 1.f;
     if (varying) {
         const float h = 0.5f * S * scale * scale * scale;
         gf3[3 * i] = gi * (dS0 * scale - h * dW0);
@@ -123,8 +142,8 @@ template <bool ADJ>
 cudaError_t launch_interp_A(const MapDev &m, const float *f3, const float *tau, const float *g, uint64_t n,
                             float *snr, float *gf3, float *gtau, cudaStream_t st)
 {
-    const int threads = 128;
-    const uint64_t blocks = (n + threads - 1) / threads;
+    const int threads = 128;                                  // 4 templates (warps) per block
+    const uint64_t blocks = (n * 32 + threads - 1) / threads;
     if (blocks > 0x7fffffffull) return cudaErrorInvalidValue;
     const unsigned b = (unsigned)blocks;
 #define STK_INTERP(W, P) interp_kernel<W, P, ADJ><<<b, threads, 0, st>>>(m, f3, tau, g, n, snr, gf3, gtau)
@@ -141,7 +160,81 @@ cudaError_t launch_interp_A(const MapDev &m, const float *f3, const float *tau, 
     return cudaGetLastError();
 }
 
+// One Adam step of the gradient ascent of every template's SNR (Adam with betas
+// 0.9, 0.999 and eps 1e-8 on the loss -SNR, in torch's arithmetic order), then the
+// projection onto f in [0, n_f - 1] and |u| <= 1, u = tau / tau_max.  st[2i] and
+// st[2i+1] hold the first and second moments of (f0, f1, f2, u).  The bias
+// corrections come from the host: step_f = lr_f / (1 - 0.9^t), step_u likewise,
+// sbc2 = sqrt(1 - 0.999^t).
+__global__ void __launch_bounds__(256) adam_kernel(float *__restrict__ f3, float *__restrict__ u,
+                                                   float *__restrict__ tau, const float *__restrict__ gf3,
+                                                   const float *__restrict__ gtau, float4 *__restrict__ st,
+                                                   uint64_t n, float step_f, float step_u, float sbc2,
+                                                   float tau_max, float f_hi)
+{
+    const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float w1 = 0.1f, b2 = 0.999f, w2 = 0.001f, eps = 1e-8f;
+    float4 m = st[2 * i], v = st[2 * i + 1];
+    const float g[4] = {-gf3[3 * i], -gf3[3 * i + 1], -gf3[3 * i + 2], -gtau[i] * tau_max};  // d(-SNR)/d(f, u)
+    float p[4] = {f3[3 * i], f3[3 * i + 1], f3[3 * i + 2], u[i]};
+    float *mm = &m.x, *vv = &v.x;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        mm[q] = mm[q] + w1 * (g[q] - mm[q]);
+        vv[q] = vv[q] * b2 + w2 * g[q] * g[q];
+        const float denom = __fsqrt_rn(vv[q]) / sbc2 + eps;
+        p[q] = p[q] - (q < 3 ? step_f : step_u) * (mm[q] / denom);
+    }
+    st[2 * i] = m;
+    st[2 * i + 1] = v;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) f3[3 * i + q] = fminf(fmaxf(p[q], 0.f), f_hi);
+    const float uu = fminf(fmaxf(p[3], -1.f), 1.f);
+    u[i] = uu;
+    tau[i] = uu * tau_max;
+}
+
+__global__ void __launch_bounds__(256) refine_init_kernel(const float *__restrict__ tau, float *__restrict__ u,
+                                                          float4 *__restrict__ st, uint64_t n, float tau_max)
+{
+    const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    u[i] = tau[i] / tau_max;
+    st[2 * i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    st[2 * i + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
 }  // namespace
+
+size_t refine_scratch_bytes(uint64_t n)
+{
+    return (size_t)n * (sizeof(float4) * 2 + sizeof(float) * 5);  // moments, u, gradients (f3, tau)
+}
+
+cudaError_t launch_refine(const MapDev &m, float *f3, float *tau, uint64_t n, int steps, float lr_f, float lr_u,
+                          float tau_max, float *hist, void *scratch, cudaStream_t st)
+{
+    if (n == 0 || steps < 0) return cudaSuccess;
+    float4 *mom = static_cast<float4 *>(scratch);
+    float *u = reinterpret_cast<float *>(mom + 2 * n), *gf3 = u + n, *gtau = gf3 + 3 * n;
+    const unsigned blocks = (unsigned)((n + 255) / 256);
+    refine_init_kernel<<<blocks, 256, 0, st>>>(tau, u, mom, n, tau_max);
+    cudaError_t e = cudaGetLastError();
+    const float f_hi = (float)(m.n_f - 1);
+    for (int t = 1; t <= steps && e == cudaSuccess; ++t) {
+        // the step's SNR (history row t - 1) and its gradient, then the update
+        e = launch_interp(m, f3, tau, nullptr, n, hist ? hist + (size_t)(t - 1) * n : nullptr, gf3, gtau, true, st);
+        if (e != cudaSuccess) break;
+        const double bc1 = 1.0 - std::pow(0.9, t), bc2 = 1.0 - std::pow(0.999, t);
+        adam_kernel<<<blocks, 256, 0, st>>>(f3, u, tau, gf3, gtau, mom, n, (float)(lr_f / bc1), (float)(lr_u / bc1),
+                                            (float)std::sqrt(bc2), tau_max, f_hi);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess && hist)
+        e = launch_interp(m, f3, tau, nullptr, n, hist + (size_t)steps * n, nullptr, nullptr, false, st);
+    return e;
+}
 
 cudaError_t launch_interp(const MapDev &m, const float *f3, const float *tau, const float *g, uint64_t n, float *snr,
                           float *gf3, float *gtau, bool adjoint, cudaStream_t st)

@@ -148,3 +148,128 @@ def test_autograd_and_refinement(ctx):
     np.testing.assert_allclose(d, o, rtol=1e-5, atol=1e-5)
     print(f"refine: interpolated SNR {hist[0].mean():.3f} -> {hist[-1].mean():.3f}; "
           f"discrete before {hits['snr'].mean():.3f}, after rounding {d.mean():.3f}")
+
+
+def _torch_adam_refine(ctx, m, f3, tau, tau_max, steps, lr_bins=0.25, lr_tau_frac=0.02):
+    """The ascent written with torch.autograd and torch.optim.Adam over the same
+    interpolated statistic: the comparison for the loop that runs on the device."""
+    f = f3.detach().clone().requires_grad_(True)
+    u = (tau.detach() / tau_max).clone().requires_grad_(True)
+    opt = torch.optim.Adam([{"params": [f], "lr": lr_bins}, {"params": [u], "lr": lr_tau_frac}])
+    hist = []
+    for _ in range(steps):
+        opt.zero_grad()
+        snr = stk.interp_snr(ctx, m, f, u * tau_max)
+        hist.append(snr.detach().clone())
+        (-snr.sum()).backward()
+        opt.step()
+        with torch.no_grad():
+            f.clamp_(0.0, float(m.n_f - 1))
+            u.clamp_(-1.0, 1.0)
+    hist.append(ctx.interp_forward(m, f.detach(), u.detach() * tau_max))
+    return f.detach(), u.detach() * tau_max, torch.stack(hist)
+
+
+def _loud_templates(ctx, n):
+    fm = synth.realistic_map(n_t=200, n_f=400)
+    m = ctx.load_map(torch.from_numpy(fm.y).cuda(), torch.from_numpy(fm.sigma).cuda(), fm.f_min, fm.df)
+    ctx.set_tracks(200_000, 2, 0, TAU_MAX)
+    hits = ctx.score(m, n)
+    f3 = torch.tensor(np.array([list(h) for h in hits["f"]]), dtype=torch.float32, device="cuda")
+    tau = torch.tensor(hits["tau"], dtype=torch.float32, device="cuda")
+    return fm, m, f3, tau
+
+
+def test_device_loop_matches_torch_adam(ctx):
+    """The device loop against torch's Adam over autograd, 50 steps of 256 loud
+    templates: the same ascent up to FP32 rounding order."""
+    fm, m, f3, tau = _loud_templates(ctx, 256)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    ctx.refine(m, f3, tau, TAU_MAX, steps=2)
+    _torch_adam_refine(ctx, m, f3, tau, TAU_MAX, 2)
+    torch.cuda.synchronize()
+    ev[0].record()
+    f_d, t_d, h_d = ctx.refine(m, f3, tau, TAU_MAX, steps=50)
+    ev[1].record()
+    ev[2].record()
+    f_t, t_t, h_t = _torch_adam_refine(ctx, m, f3, tau, TAU_MAX, 50)
+    ev[3].record()
+    torch.cuda.synchronize()
+    print(f"refine 50 steps x 256: device loop {ev[0].elapsed_time(ev[1]):.2f} ms, "
+          f"torch Adam over autograd {ev[2].elapsed_time(ev[3]):.2f} ms")
+    assert h_d.shape == h_t.shape == (51, 256)
+    # the device loop starts from the given delays; the torch loop from (tau / tau_max) * tau_max
+    assert torch.equal(h_d[0], ctx.interp_forward(m, f3, tau))
+    assert torch.allclose(h_d[0], h_t[0], rtol=1e-5, atol=1e-5)
+    d = (h_d - h_t).abs().cpu().numpy()
+    scale = h_t.abs().cpu().numpy() + 1.0
+    # Adam normalises each step, so rounding differences stay at the ulp level
+    # except where a curve point sits within an ulp of a bin knot (a kink)
+    assert np.quantile(d / scale, 0.99) < 1e-4, np.quantile(d / scale, 0.99)
+    assert abs(float(h_d[-1].mean() - h_t[-1].mean())) < 1e-3 * float(h_t[-1].abs().mean())
+    assert float((f_d - f_t).abs().max()) < 0.5 and float((t_d - t_t).abs().max()) <= 0.1 * TAU_MAX
+    # the inputs are untouched; the last history row is the SNR at the returned templates
+    assert torch.equal(h_d[-1], ctx.interp_forward(m, f_d, t_d))
+
+
+def test_first_step_is_signed_learning_rate(ctx):
+    """Adam's first step from zero moments is lr * g / (|g| + eps) per coordinate: a
+    step of the learning rate along the sign of the oracle's FP64 gradient,
+    then the projection."""
+    n_t, n_f, n = 160, 300, 200
+    y, sig = _map("freq", n_t, n_f, 84)
+    m = ctx.load_map(torch.from_numpy(y).cuda(), torch.from_numpy(sig).cuda(), 40.0, 0.5)
+    om = oracle.OracleMap(y, sig, 40.0, 0.5, True)
+    rng = np.random.default_rng(85)
+    f3 = _away_from_knots(rng, n, n_t, n_f, 2e-3).astype(np.float32)
+    f3[:8, 0] = 0.0                                            # some start on the band edge
+    tau = (rng.uniform(-1.0, 1.0, n) * TAU_MAX).astype(np.float32)
+    tau[8:16] = TAU_MAX                                        # and some on the delay bound
+    lr_f, lr_u = 0.3, 0.05
+    f_new, t_new, h = ctx.refine(m, torch.from_numpy(f3).cuda(), torch.from_numpy(tau).cuda(), TAU_MAX, steps=1,
+                                 lr_bins=lr_f, lr_tau_frac=lr_u)
+    snr0, og = om.interp_score(f3.astype(np.float64), tau.astype(np.float64), grad=True)
+    og[:, 3] *= TAU_MAX
+    f_new, t_new = f_new.cpu().numpy(), t_new.cpu().numpy()
+    exp_f = np.clip(f3 + lr_f * np.sign(og[:, :3]), 0, n_f - 1)
+    exp_u = np.clip(tau / TAU_MAX + lr_u * np.sign(og[:, 3]), -1, 1)
+    # where the gradient is too small to have a reliable sign in FP32 the step may go
+    # either way; everywhere else it is the signed learning rate, to FP32 rounding
+    sure = np.abs(og) > 1e-3 * np.max(np.abs(og), axis=0)
+    assert np.mean(sure) > 0.95
+    err_f = np.abs(f_new - exp_f)
+    assert np.all(err_f[sure[:, :3]] <= 1e-4 * (1 + np.abs(exp_f[sure[:, :3]]))), np.max(err_f[sure[:, :3]])
+    err_u = np.abs(t_new / TAU_MAX - exp_u)
+    assert np.all(err_u[sure[:, 3]] <= 1e-5), np.max(err_u[sure[:, 3]])
+    assert np.all(f_new >= 0) and np.all(f_new <= n_f - 1) and np.all(np.abs(t_new) <= TAU_MAX)
+    # history rows: the oracle's SNR before the step, the forward kernel's after it
+    sc = np.abs(snr0) + 1.0
+    assert np.all(np.abs(h[0].cpu().numpy() - snr0) <= 2e-5 * sc * np.sqrt(n_t))
+    assert torch.equal(h[1], ctx.interp_forward(m, torch.from_numpy(f_new).cuda(), torch.from_numpy(t_new).cuda()))
+
+
+def test_refine_edge_cases(ctx):
+    n_t, n_f = 64, 50
+    y, sig = _map("const", n_t, n_f, 86)
+    m = ctx.load_map(torch.from_numpy(y).cuda(), torch.from_numpy(sig).cuda(), 40.0, 0.5)
+    rng = np.random.default_rng(87)
+    f3 = torch.tensor(rng.uniform(0, n_f - 1, (33, 3)), dtype=torch.float32, device="cuda")
+    tau = torch.tensor(rng.uniform(-TAU_MAX, TAU_MAX, 33), dtype=torch.float32, device="cuda")
+    # zero steps: parameters unchanged, one history row
+    f0, t0, h0 = ctx.refine(m, f3, tau, TAU_MAX, steps=0)
+    assert torch.equal(f0, f3) and torch.equal(h0[0], ctx.interp_forward(m, f3, tau))
+    # no templates
+    fe, te, he = ctx.refine(m, f3[:0], tau[:0], TAU_MAX, steps=5)
+    assert fe.numel() == 0 and he.shape == (6, 0)
+    # no history requested
+    f1, t1, h1 = ctx.refine(m, f3, tau, TAU_MAX, steps=3, history=False)
+    f2, t2, h2 = ctx.refine(m, f3, tau, TAU_MAX, steps=3)
+    assert h1 is None and torch.equal(f1, f2) and torch.equal(t1, t2)  # deterministic
+    # zero learning rates leave the parameters where they are
+    fz, tz, _ = ctx.refine(m, f3, tau, TAU_MAX, steps=4, lr_bins=0.0, lr_tau_frac=0.0)
+    assert torch.equal(fz, f3) and torch.allclose(tz, tau, rtol=1e-6, atol=0)
+    for bad in ({"tau_max": 0.0}, {"tau_max": -1.0}, {"steps": -1}, {"lr_bins": -0.1}, {"lr_tau_frac": float("nan")}):
+        kw = {"tau_max": TAU_MAX, "steps": 2}
+        kw.update(bad)
+        with pytest.raises(stk.StkError):
+            ctx.refine(m, f3, tau, **kw)
