@@ -63,6 +63,8 @@ def test_null_arguments_rejected_without_gpu(built):
     assert L.stk_set_tracks(None, 1, 0, 0, 0.0) == _lib.STK_EINVAL
     assert L.stk_score(None, None, 1, None, 0) == _lib.STK_EINVAL
     assert L.stk_sync(None) == _lib.STK_EINVAL
+    assert L.stk_refine(None, None, None, None, 1, 1, 0.1, 0.1, 1.0, None) == _lib.STK_EINVAL
+    assert L.stk_interp_forward(None, None, None, None, 1, None) == _lib.STK_EINVAL
     L.stk_destroy(None)
     L.stk_free_map(None)
     assert isinstance(L.stk_last_error(None), bytes)
