@@ -13,9 +13,9 @@
 // One warp per template: lane l takes the columns j = l (mod 32) in order, then
 // the lanes' partial sums meet in a fixed shuffle tree (deterministic).  Sums and
 // the pixel arithmetic are FP32; the curve position x_j and the phase argument are
-// FP64, since FP32 resolves x_j ~ 10^3 only to 6e-5 bins (with one thread per
-// template, a few SMs' FP64 units did all of that work: 1 ms a step for 1024
-// templates).
+// FP64, since FP32 resolves x_j ~ 10^3 only to 6e-5 bins.  FP64 is a slow pipe on
+// this GPU, so x_j advances by forward differences and only the position, its
+// split into bin and fraction, and the phase's turns use it.
 #include <cuda_fp16.h>
 
 #include <cmath>
@@ -67,11 +67,19 @@ __global__ void __launch_bounds__(128) interp_kernel(MapDev m, const float *__re
     const double a2 = f0 - 2.0 * f1 + f2, a1 = 2.0 * M * (f1 - f0), a0 = M * M * f0;
     const double fa = m.df * tau, fb = m.f_min * tau;      // turns per bin, turns at bin 0
     const float two_pi = 6.28318530717958647692f;
+    const float inv_Mf = 1.f / (float)M, df_f = (float)m.df, fmin_f = (float)m.f_min;
+    // x_j by forward differences along the lane's columns j, j + 32, ...: two FP64
+    // additions a column (the quadratic's second difference is constant)
+    const double jl = (double)lane;
+    double x_next = ((a2 * jl + a1) * jl + a0) * inv_M2;
+    double dx = (a2 * (64.0 * jl + 1024.0) + 32.0 * a1) * inv_M2;
+    const double ddx = 2048.0 * a2 * inv_M2;
     float S = 0.f, W = 0.f;
     float dS0 = 0.f, dS1 = 0.f, dS2 = 0.f, dS3 = 0.f, dW0 = 0.f, dW1 = 0.f, dW2 = 0.f;
     for (int j = lane; j < n_t; j += 32) {
-        const double jd = (double)j;
-        double x = ((a2 * jd + a1) * jd + a0) * inv_M2;
+        double x = x_next;
+        x_next += dx;
+        dx += ddx;
         bool clamped = false;
         if (x < 0.0) { x = 0.0; clamped = true; }
         if (x > (double)(n_f - 1)) { x = (double)(n_f - 1); clamped = true; }
@@ -96,14 +104,14 @@ __global__ void __launch_bounds__(128) interp_kernel(MapDev m, const float *__re
             // d re/dx = -im 2 pi df tau + Re[e^{i phi} dz/dx]; d re/dtau = -im 2 pi f
             const float dre_dx = clamped ? 0.f : fmaf(-im, two_pi * (float)fa, c * dzr - s * dzi);
             const float dw_dx = clamped ? 0.f : dw;
-            const float u = (float)(jd / M), c0 = (1.f - u) * (1.f - u), c1 = 2.f * (1.f - u) * u, c2 = u * u;
+            const float u = (float)j * inv_Mf, c0 = (1.f - u) * (1.f - u), c1 = 2.f * (1.f - u) * u, c2 = u * u;
             dS0 = fmaf(dre_dx, c0, dS0);
             dS1 = fmaf(dre_dx, c1, dS1);
             dS2 = fmaf(dre_dx, c2, dS2);
             dW0 = fmaf(dw_dx, c0, dW0);
             dW1 = fmaf(dw_dx, c1, dW1);
             dW2 = fmaf(dw_dx, c2, dW2);
-            dS3 = fmaf(-im, two_pi * (float)(m.f_min + x * m.df), dS3);
+            dS3 = fmaf(-im, two_pi * fmaf((float)x, df_f, fmin_f), dS3);
         }
     }
     for (int o = 16; o > 0; o >>= 1) {
