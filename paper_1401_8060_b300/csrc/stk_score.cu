@@ -154,19 +154,42 @@ __global__ void __launch_bounds__(256, 4) score_general_kernel(MapDev m, TrackSe
         }
         np = 0;
     };
+    auto push = [&](int j, int32_t b) {
+        if (np == 0) { pj0 = j; pb0 = b; }
+        else if (np == 1) { pj1 = j; pb1 = b; }
+        else if (np == 2) { pj2 = j; pb2 = b; }
+        else { pj3 = j; pb3 = b; }
+        ++np;
+    };
+    // Two columns a step: both estimates, then both gathers in flight together (an
+    // estimate's bin is always inside the map, so an undecided pixel's gather is
+    // harmless and unused), then the sums in column order.
+    using Rec = typename Pix<PREC>::Rec;
+    auto gather = [&](int j, int32_t b, Rec &v, float &wv) {
+        v = Pix<PREC>::load_global(m.rec, (size_t)j * m.ldr + (uint32_t)b);
+        wv = 0.f;
+        if (WMODE == WMODE_FREQ) wv = __ldg(m.w + b);
+        if (WMODE == WMODE_PIXEL) wv = __ldg(m.w + (size_t)j * m.ldw + b);
+    };
     add((int)t[0], (int32_t)f[0], acc, W);
-    for (int j = (int)t[0] + 1; j <= (int)t[2]; ++j) {
-        int32_t b;
-        if (gen_estimate(c, gf, j, m.n_f, b)) {
-            add(j, b, acc, W);
-        } else {
-            if (np == 0) { pj0 = j; pb0 = b; }
-            else if (np == 1) { pj1 = j; pb1 = b; }
-            else if (np == 2) { pj2 = j; pb2 = b; }
-            else { pj3 = j; pb3 = b; }
-            ++np;
+    const int jend = (int)t[2];
+    for (int j = (int)t[0] + 1; j <= jend; j += 2) {
+        const bool has1 = j < jend;
+        const int j1 = has1 ? j + 1 : j;
+        int32_t b0, b1;
+        const bool ok0 = gen_estimate(c, gf, j, m.n_f, b0);
+        const bool ok1 = gen_estimate(c, gf, j1, m.n_f, b1);
+        Rec v0, v1;
+        float w0, w1;
+        gather(j, b0, v0, w0);
+        gather(j1, b1, v1, w1);
+        if (ok0) accumulate<PREC, WMODE>(v0, (uint32_t)b0, ph, w0, acc, W);
+        else push(j, b0);
+        if (has1) {
+            if (ok1) accumulate<PREC, WMODE>(v1, (uint32_t)b1, ph, w1, acc, W);
+            else push(j1, b1);
         }
-        if (__any_sync(__activemask(), np == 4)) flush();
+        if (__any_sync(__activemask(), np >= 3)) flush();  // room for the next step's two
     }
     flush();
     acc += acc_x;
