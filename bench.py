@@ -436,7 +436,7 @@ def main():
             "frac_improved": float((hist[-1] > hist[0]).float().mean()),
             "discrete_snr_mean_before": float(np.mean(hits["snr"])),
             "discrete_snr_mean_after_rounding": float(np.mean(d_after)),
-            "kernels": "stk_refine: per step the interpolated SNR and its gradient (one warp per template) "
+            "kernels": "stk_refine: per step the interpolated SNR and its gradient (one 128-thread block per template) "
                        "and one Adam step, all on the device; 2 launches per step"}
         ctx.set_profiling(True)
 

@@ -21,6 +21,7 @@ STK_MAX_K = 4096
 STK_NOALLOC_MAX_TRACKS = 1 << 20
 STK_OPT_KERNEL, STK_OPT_THREADS, STK_OPT_MAX_R, STK_OPT_STAGES, STK_OPT_SMEM_KB = 1, 2, 3, 4, 5
 STK_OPT_WAIT_MS, STK_OPT_WITHHOLD_SLAB, STK_OPT_ORDER, STK_OPT_SELECT_SAMPLE = 6, 7, 8, 9
+STK_OPT_INTERP_THREADS = 10
 
 # Every entry point declared in include/stk.h: (name, restype, argtypes).
 _vp = C.c_void_p

@@ -284,6 +284,11 @@ int stk_set_option(stk_ctx *c, int option, int64_t value)
         if (value < 0 || value > 49152) return set_err(c, STK_EINVAL, "selection sample must be in [0, 49152]");
         c->tune.select_sample = (int)value;
         return STK_OK;
+    case STK_OPT_INTERP_THREADS:
+        if (value != 0 && value != 32 && value != 64 && value != 128)
+            return set_err(c, STK_EINVAL, "threads per continuous template must be 0, 32, 64 or 128");
+        c->interp_threads = (int)value;
+        return STK_OK;
     default: return set_err(c, STK_EINVAL, "unknown option %d", option);
     }
 }
@@ -653,7 +658,8 @@ int stk_interp_forward(stk_ctx *c, const stk_map *m, const float *f3, const floa
     if (n == 0) return STK_OK;
     if (!f3 || !tau || !snr) return set_err(c, STK_EINVAL, "NULL pointer");
     CUDA_TRY(c, cudaSetDevice(c->device));
-    cudaError_t e = launch_interp(m->dev, f3, tau, nullptr, n, snr, nullptr, nullptr, false, c->stream);
+    cudaError_t e = launch_interp_tuned(m->dev, f3, tau, nullptr, n, snr, nullptr, nullptr, false, c->interp_threads,
+                                        c->stream);
     if (e != cudaSuccess) return set_err(c, STK_ECUDA, "interpolated forward launch: %s", cudaGetErrorString(e));
     return STK_OK;
 }
@@ -666,7 +672,8 @@ int stk_interp_adjoint(stk_ctx *c, const stk_map *m, const float *f3, const floa
     if (n == 0) return STK_OK;
     if (!f3 || !tau || !g || !grad_f3 || !grad_tau) return set_err(c, STK_EINVAL, "NULL pointer");
     CUDA_TRY(c, cudaSetDevice(c->device));
-    cudaError_t e = launch_interp(m->dev, f3, tau, g, n, nullptr, grad_f3, grad_tau, true, c->stream);
+    cudaError_t e = launch_interp_tuned(m->dev, f3, tau, g, n, nullptr, grad_f3, grad_tau, true, c->interp_threads,
+                                        c->stream);
     if (e != cudaSuccess) return set_err(c, STK_ECUDA, "interpolated adjoint launch: %s", cudaGetErrorString(e));
     return STK_OK;
 }
@@ -686,7 +693,7 @@ int stk_refine(stk_ctx *c, const stk_map *m, float *f3, float *tau, uint64_t n, 
     int rc = ensure(c, &c->refine_buf, &c->refine_cap, refine_scratch_bytes(n));
     if (rc) return rc;
     cudaError_t e = launch_refine(m->dev, f3, tau, n, steps, lr_bins, lr_tau_frac, tau_max, hist, c->refine_buf,
-                                  c->stream);
+                                  c->interp_threads, c->stream);
     if (e != cudaSuccess) return set_err(c, STK_ECUDA, "refinement launch: %s", cudaGetErrorString(e));
     return STK_OK;
 }

@@ -35,8 +35,9 @@ struct stk_ctx {
     size_t stage_s_cap = 0;
     void *order_buf = nullptr;     // coherent-order pre-pass of the slab kernel
     size_t order_cap = 0;
-    void *refine_buf = nullptr;    // refinement: Adam moments and gradients
+    void *refine_buf = nullptr;    // refinement: Adam moments and delay coordinate
     size_t refine_cap = 0;
+    int interp_threads = 0;        // continuous templates: threads per template (0: by count)
     Tuning tune{};
     ScorePlan plan{};
     bool profiling = false;

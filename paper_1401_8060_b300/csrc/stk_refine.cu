@@ -10,8 +10,9 @@
 //   SNR = S / sqrt(W) (weighted) or S / N (paper form) -- Eq. 7 at integer bins.
 // The forward kernel returns SNR; the adjoint kernel returns g * dSNR/d(f0, f1,
 // f2, tau) for an upstream gradient g, differentiating each of those steps.
-// One warp per template: lane l takes the columns j = l (mod 32) in order, then
-// the lanes' partial sums meet in a fixed shuffle tree (deterministic).  Sums and
+// One block of 128 threads per template: thread l takes the columns j = l (mod
+// 128) in order; the lanes' partial sums meet in a fixed shuffle tree and the
+// four warps' sums are added in warp order (deterministic).  Sums and
 // the pixel arithmetic are FP32; the curve position x_j and the phase argument are
 // FP64, since FP32 resolves x_j ~ 10^3 only to 6e-5 bins.  FP64 is a slow pipe on
 // this GPU, so x_j advances by forward differences and only the position, its
@@ -51,110 +52,218 @@ __device__ __forceinline__ void pixel_at(const MapDev &m, int j, int k, float &z
     w = wv;
 }
 
-template <int WMODE, int PREC, bool ADJOINT>
-__global__ void __launch_bounds__(128) interp_kernel(MapDev m, const float *__restrict__ f3,
-                                                     const float *__restrict__ tau_in, const float *__restrict__ g,
-                                                     uint64_t n, float *__restrict__ snr_out,
-                                                     float *__restrict__ gf3, float *__restrict__ gtau)
+constexpr int kInterpBlock = 128;
+
+// Per-launch constants of the curve and the map (host-computed, so no thread
+// repeats the FP64 divisions).
+struct InterpConst {
+    double M, inv_M2, df, f_min;
+    float inv_Mf, df_f, fmin_f;
+};
+
+// Fused Adam step (refinement): the template's thread 0 takes the step from the
+// gradient it has just summed.  mom == nullptr: no step.
+struct AdamStep {
+    float *u;          // tau / tau_max, the ascent's delay coordinate
+    float4 *mom;       // first and second moments of (f0, f1, f2, u), two float4 a template
+    float step_f, step_u, sbc2, tau_max, f_hi;
+};
+
+// One Adam step of the gradient ascent of a template's SNR (Adam with betas 0.9,
+// 0.999 and eps 1e-8 on the loss -SNR, in torch's arithmetic order), then the
+// projection onto f in [0, n_f - 1] and |u| <= 1.  step_f = lr_f / (1 - 0.9^t),
+// step_u likewise, sbc2 = sqrt(1 - 0.999^t), from the host.
+__device__ __forceinline__ void adam_update(const AdamStep &ad, uint64_t i, float *f3, float *tau, const float gs[4])
 {
-    const uint64_t i = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;  // the same for a whole warp
-    const int lane = threadIdx.x & 31;
-    if (i >= n) return;
+    const float w1 = 0.1f, b2 = 0.999f, w2 = 0.001f, eps = 1e-8f;
+    float4 m = ad.mom[2 * i], v = ad.mom[2 * i + 1];
+    float p[4] = {f3[3 * i], f3[3 * i + 1], f3[3 * i + 2], ad.u[i]};
+    float *mm = &m.x, *vv = &v.x;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const float g = -gs[q];                                   // d(-SNR)/d(f, u)
+        mm[q] = mm[q] + w1 * (g - mm[q]);
+        vv[q] = vv[q] * b2 + w2 * g * g;
+        const float denom = __fsqrt_rn(vv[q]) / ad.sbc2 + eps;
+        p[q] = p[q] - (q < 3 ? ad.step_f : ad.step_u) * (mm[q] / denom);
+    }
+    ad.mom[2 * i] = m;
+    ad.mom[2 * i + 1] = v;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) f3[3 * i + q] = fminf(fmaxf(p[q], 0.f), ad.f_hi);
+    const float uu = fminf(fmaxf(p[3], -1.f), 1.f);
+    ad.u[i] = uu;
+    tau[i] = uu * ad.tau_max;
+}
+
+// P threads per template (32, 64 or 128), kInterpBlock / P templates a block.
+// MODE 0: forward (snr); 1: adjoint (g * gradient to gf3, gtau; snr too when
+// snr_out is given); 2: adjoint with g = 1 and the fused Adam step, parameters
+// updated in place (each template's parameters are read by its own threads
+// before the reduction and written by its thread 0 after it).
+template <int WMODE, int PREC, int MODE, int P>
+__global__ void __launch_bounds__(kInterpBlock) interp_kernel(MapDev m, InterpConst k, const float *f3,
+                                                              const float *tau_in, const float *__restrict__ g,
+                                                              uint64_t n, float *__restrict__ snr_out,
+                                                              float *__restrict__ gf3, float *__restrict__ gtau,
+                                                              AdamStep ad)
+{
+    constexpr bool ADJOINT = MODE != 0;
+    constexpr int TPB = kInterpBlock / P;  // templates a block
+    constexpr int WPT = P / 32;            // warps a template
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int t = tid % P;                  // thread within the template
+    const uint64_t i_raw = (uint64_t)blockIdx.x * TPB + tid / P;
+    const bool valid = i_raw < n;           // no early return: the block meets at a barrier below
+    const uint64_t i = valid ? i_raw : n - 1;
     const double f0 = f3[3 * i], f1 = f3[3 * i + 1], f2 = f3[3 * i + 2];
     const double tau = tau_in[i];
     const int n_t = m.n_t, n_f = m.n_f;
-    const double M = (double)(n_t - 1), inv_M2 = 1.0 / (M * M);
+    const double M = k.M, inv_M2 = k.inv_M2;
     const double a2 = f0 - 2.0 * f1 + f2, a1 = 2.0 * M * (f1 - f0), a0 = M * M * f0;
-    const double fa = m.df * tau, fb = m.f_min * tau;      // turns per bin, turns at bin 0
+    const double fa = k.df * tau, fb = k.f_min * tau;     // turns per bin, turns at bin 0
     const float two_pi = 6.28318530717958647692f;
-    const float inv_Mf = 1.f / (float)M, df_f = (float)m.df, fmin_f = (float)m.f_min;
-    // x_j by forward differences along the lane's columns j, j + 32, ...: two FP64
-    // additions a column (the quadratic's second difference is constant)
-    const double jl = (double)lane;
+    // x_j by forward differences along the thread's columns j, j + P, ...: two FP64
+    // additions a column (x(j + P) - x(j) = (a2 (2 P j + P^2) + a1 P) / M^2, and the
+    // second difference 2 P^2 a2 / M^2 is constant)
+    const double jl = (double)t, Pd = (double)P;
     double x_next = ((a2 * jl + a1) * jl + a0) * inv_M2;
-    double dx = (a2 * (64.0 * jl + 1024.0) + 32.0 * a1) * inv_M2;
-    const double ddx = 2048.0 * a2 * inv_M2;
+    double dx = (a2 * (2.0 * Pd * jl + Pd * Pd) + a1 * Pd) * inv_M2;
+    const double ddx = 2.0 * Pd * Pd * a2 * inv_M2;
     float S = 0.f, W = 0.f;
     float dS0 = 0.f, dS1 = 0.f, dS2 = 0.f, dS3 = 0.f, dW0 = 0.f, dW1 = 0.f, dW2 = 0.f;
-    for (int j = lane; j < n_t; j += 32) {
+    for (int j = t; j < n_t; j += P) {
         double x = x_next;
         x_next += dx;
         dx += ddx;
         bool clamped = false;
         if (x < 0.0) { x = 0.0; clamped = true; }
         if (x > (double)(n_f - 1)) { x = (double)(n_f - 1); clamped = true; }
-        int k = (int)floor(x);
-        if (k > n_f - 2) k = n_f - 2;
-        if (k < 0) k = 0;
-        const float a = n_f > 1 ? (float)(x - (double)k) : 0.f;
+        int kb = (int)floor(x);
+        if (kb > n_f - 2) kb = n_f - 2;
+        if (kb < 0) kb = 0;
+        const float a = n_f > 1 ? (float)(x - (double)kb) : 0.f;
         float z0r, z0i, w0, z1r, z1i, w1;
-        pixel_at<WMODE, PREC>(m, j, k, z0r, z0i, w0);
-        if (n_f > 1) pixel_at<WMODE, PREC>(m, j, k + 1, z1r, z1i, w1);
+        pixel_at<WMODE, PREC>(m, j, kb, z0r, z0i, w0);
+        if (n_f > 1) pixel_at<WMODE, PREC>(m, j, kb + 1, z1r, z1i, w1);
         else { z1r = z0r; z1i = z0i; w1 = w0; }
         const float dzr = z1r - z0r, dzi = z1i - z0i, dw = w1 - w0;
         const float zr = fmaf(a, dzr, z0r), zi = fmaf(a, dzi, z0i), w = fmaf(a, dw, w0);
         double turns = fb + x * fa;
         turns -= rint(turns);                                // [-1/2, 1/2]
-        float s, c;
-        __sincosf(two_pi * (float)turns, &s, &c);
-        const float re = c * zr - s * zi, im = s * zr + c * zi;
+        float sn, cs;
+        __sincosf(two_pi * (float)turns, &sn, &cs);
+        const float re = cs * zr - sn * zi, im = sn * zr + cs * zi;
         S += re;
         W += w;
         if (ADJOINT) {
             // d re/dx = -im 2 pi df tau + Re[e^{i phi} dz/dx]; d re/dtau = -im 2 pi f
-            const float dre_dx = clamped ? 0.f : fmaf(-im, two_pi * (float)fa, c * dzr - s * dzi);
+            const float dre_dx = clamped ? 0.f : fmaf(-im, two_pi * (float)fa, cs * dzr - sn * dzi);
             const float dw_dx = clamped ? 0.f : dw;
-            const float u = (float)j * inv_Mf, c0 = (1.f - u) * (1.f - u), c1 = 2.f * (1.f - u) * u, c2 = u * u;
+            const float u = (float)j * k.inv_Mf, c0 = (1.f - u) * (1.f - u), c1 = 2.f * (1.f - u) * u, c2 = u * u;
             dS0 = fmaf(dre_dx, c0, dS0);
             dS1 = fmaf(dre_dx, c1, dS1);
             dS2 = fmaf(dre_dx, c2, dS2);
             dW0 = fmaf(dw_dx, c0, dW0);
             dW1 = fmaf(dw_dx, c1, dW1);
             dW2 = fmaf(dw_dx, c2, dW2);
-            dS3 = fmaf(-im, two_pi * fmaf((float)x, df_f, fmin_f), dS3);
+            dS3 = fmaf(-im, two_pi * fmaf((float)x, k.df_f, k.fmin_f), dS3);
         }
     }
-    for (int o = 16; o > 0; o >>= 1) {
-        S += __shfl_xor_sync(0xffffffffu, S, o);
-        W += __shfl_xor_sync(0xffffffffu, W, o);
-        if (ADJOINT) {
-            dS0 += __shfl_xor_sync(0xffffffffu, dS0, o);
-            dS1 += __shfl_xor_sync(0xffffffffu, dS1, o);
-            dS2 += __shfl_xor_sync(0xffffffffu, dS2, o);
-            dS3 += __shfl_xor_sync(0xffffffffu, dS3, o);
-            dW0 += __shfl_xor_sync(0xffffffffu, dW0, o);
-            dW1 += __shfl_xor_sync(0xffffffffu, dW1, o);
-            dW2 += __shfl_xor_sync(0xffffffffu, dW2, o);
-        }
+    constexpr int NV = ADJOINT ? 9 : 2;
+    float v[NV];
+    v[0] = S;
+    v[1] = W;
+    if (ADJOINT) {
+        v[2 % NV] = dS0; v[3 % NV] = dS1; v[4 % NV] = dS2; v[5 % NV] = dS3;
+        v[6 % NV] = dW0; v[7 % NV] = dW1; v[8 % NV] = dW2;
     }
-    if (lane != 0) return;
+#pragma unroll
+    for (int q = 0; q < NV; ++q)
+        for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
+    if (WPT > 1) {
+        // the template's warps' sums, added in warp order by its thread 0
+        __shared__ float red[kInterpBlock / 32][NV];
+        if (lane == 0)
+#pragma unroll
+            for (int q = 0; q < NV; ++q) red[warp][q] = v[q];
+        __syncthreads();
+        if (t == 0)
+#pragma unroll
+            for (int q = 0; q < NV; ++q) {
+                float a = red[warp][q];
+                for (int w = 1; w < WPT; ++w) a += red[warp + w][q];
+                v[q] = a;
+            }
+    }
+    if (t != 0 || !valid) return;
+    S = v[0];
+    W = v[1];
     const bool varying = WMODE != WMODE_CONST && !m.paper;
     const float scale = varying ? rsqrtf(W) : (float)m.norm;
-    if (!ADJOINT || snr_out) snr_out[i] = S * scale;
+    if (MODE == 0 || snr_out) snr_out[i] = S * scale;
     if (!ADJOINT) return;
-    const float gi = g ? g[i] : 1.f;
+    const float gi = MODE == 2 ? 1.f : (g ? g[i] : 1.f);
+    float gr[4];
     if (varying) {
         const float h = 0.5f * S * scale * scale * scale;
-        gf3[3 * i] = gi * (dS0 * scale - h * dW0);
-        gf3[3 * i + 1] = gi * (dS1 * scale - h * dW1);
-        gf3[3 * i + 2] = gi * (dS2 * scale - h * dW2);
+        gr[0] = gi * (v[2 % NV] * scale - h * v[6 % NV]);
+        gr[1] = gi * (v[3 % NV] * scale - h * v[7 % NV]);
+        gr[2] = gi * (v[4 % NV] * scale - h * v[8 % NV]);
     } else {
-        gf3[3 * i] = gi * dS0 * scale;
-        gf3[3 * i + 1] = gi * dS1 * scale;
-        gf3[3 * i + 2] = gi * dS2 * scale;
+        gr[0] = gi * v[2 % NV] * scale;
+        gr[1] = gi * v[3 % NV] * scale;
+        gr[2] = gi * v[4 % NV] * scale;
     }
-    gtau[i] = gi * dS3 * scale;
+    gr[3] = gi * v[5 % NV] * scale;
+    if (MODE == 2) {
+        const float gs[4] = {gr[0], gr[1], gr[2], gr[3] * ad.tau_max};  // dSNR/d(f0, f1, f2, u)
+        adam_update(ad, i, const_cast<float *>(f3), const_cast<float *>(tau_in), gs);
+        return;
+    }
+    gf3[3 * i] = gr[0];
+    gf3[3 * i + 1] = gr[1];
+    gf3[3 * i + 2] = gr[2];
+    gtau[i] = gr[3];
 }
 
-template <bool ADJ>
-cudaError_t launch_interp_A(const MapDev &m, const float *f3, const float *tau, const float *g, uint64_t n,
-                            float *snr, float *gf3, float *gtau, cudaStream_t st)
+InterpConst interp_const(const MapDev &m)
 {
-    const int threads = 128;                                  // 4 templates (warps) per block
-    const uint64_t blocks = (n * 32 + threads - 1) / threads;
+    InterpConst k;
+    k.M = (double)(m.n_t - 1);
+    k.inv_M2 = 1.0 / (k.M * k.M);
+    k.df = m.df;
+    k.f_min = m.f_min;
+    k.inv_Mf = 1.f / (float)k.M;
+    k.df_f = (float)m.df;
+    k.fmin_f = (float)m.f_min;
+    return k;
+}
+
+// Threads per template: 0 picks by the template count.  More threads per template
+// fill the GPU when templates are few; each thread also repeats the template's
+// setup, so with many templates one warp each is fastest (50 ascent steps on the
+// 500 x 1600 map, ms, for 32 / 64 / 128 threads: 256 templates 0.98 / 0.66 / 0.56,
+// 1024: 1.29 / 1.29 / 1.44, 4096: 3.78 / 4.00 / 4.69).
+int interp_threads(uint64_t n, int P)
+{
+    if (P == 32 || P == 64 || P == 128) return P;
+    if (n <= 384) return 128;
+    if (n <= 1536) return 64;
+    return 32;
+}
+
+template <int MODE, int P>
+cudaError_t launch_interp_P(const MapDev &m, const float *f3, const float *tau, const float *g, uint64_t n,
+                            float *snr, float *gf3, float *gtau, const AdamStep &ad, cudaStream_t st)
+{
+    constexpr uint64_t TPB = kInterpBlock / P;
+    const uint64_t blocks = (n + TPB - 1) / TPB;
     if (blocks > 0x7fffffffull) return cudaErrorInvalidValue;
     const unsigned b = (unsigned)blocks;
-#define STK_INTERP(W, P) interp_kernel<W, P, ADJ><<<b, threads, 0, st>>>(m, f3, tau, g, n, snr, gf3, gtau)
+    const InterpConst k = interp_const(m);
+#define STK_INTERP(W, PR) \
+    interp_kernel<W, PR, MODE, P><<<b, kInterpBlock, 0, st>>>(m, k, f3, tau, g, n, snr, gf3, gtau, ad)
     if (m.prec == PREC_FP16) {
         if (m.wmode == WMODE_CONST) STK_INTERP(WMODE_CONST, PREC_FP16);
         else if (m.wmode == WMODE_FREQ) STK_INTERP(WMODE_FREQ, PREC_FP16);
@@ -168,39 +277,15 @@ cudaError_t launch_interp_A(const MapDev &m, const float *f3, const float *tau, 
     return cudaGetLastError();
 }
 
-// One Adam step of the gradient ascent of every template's SNR (Adam with betas
-// 0.9, 0.999 and eps 1e-8 on the loss -SNR, in torch's arithmetic order), then the
-// projection onto f in [0, n_f - 1] and |u| <= 1, u = tau / tau_max.  st[2i] and
-// st[2i+1] hold the first and second moments of (f0, f1, f2, u).  The bias
-// corrections come from the host: step_f = lr_f / (1 - 0.9^t), step_u likewise,
-// sbc2 = sqrt(1 - 0.999^t).
-__global__ void __launch_bounds__(256) adam_kernel(float *__restrict__ f3, float *__restrict__ u,
-                                                   float *__restrict__ tau, const float *__restrict__ gf3,
-                                                   const float *__restrict__ gtau, float4 *__restrict__ st,
-                                                   uint64_t n, float step_f, float step_u, float sbc2,
-                                                   float tau_max, float f_hi)
+template <int MODE>
+cudaError_t launch_interp_M(const MapDev &m, const float *f3, const float *tau, const float *g, uint64_t n,
+                            float *snr, float *gf3, float *gtau, const AdamStep &ad, int P, cudaStream_t st)
 {
-    const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const float w1 = 0.1f, b2 = 0.999f, w2 = 0.001f, eps = 1e-8f;
-    float4 m = st[2 * i], v = st[2 * i + 1];
-    const float g[4] = {-gf3[3 * i], -gf3[3 * i + 1], -gf3[3 * i + 2], -gtau[i] * tau_max};  // d(-SNR)/d(f, u)
-    float p[4] = {f3[3 * i], f3[3 * i + 1], f3[3 * i + 2], u[i]};
-    float *mm = &m.x, *vv = &v.x;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        mm[q] = mm[q] + w1 * (g[q] - mm[q]);
-        vv[q] = vv[q] * b2 + w2 * g[q] * g[q];
-        const float denom = __fsqrt_rn(vv[q]) / sbc2 + eps;
-        p[q] = p[q] - (q < 3 ? step_f : step_u) * (mm[q] / denom);
+    switch (interp_threads(n, P)) {
+    case 128: return launch_interp_P<MODE, 128>(m, f3, tau, g, n, snr, gf3, gtau, ad, st);
+    case 64: return launch_interp_P<MODE, 64>(m, f3, tau, g, n, snr, gf3, gtau, ad, st);
+    default: return launch_interp_P<MODE, 32>(m, f3, tau, g, n, snr, gf3, gtau, ad, st);
     }
-    st[2 * i] = m;
-    st[2 * i + 1] = v;
-#pragma unroll
-    for (int q = 0; q < 3; ++q) f3[3 * i + q] = fminf(fmaxf(p[q], 0.f), f_hi);
-    const float uu = fminf(fmaxf(p[3], -1.f), 1.f);
-    u[i] = uu;
-    tau[i] = uu * tau_max;
 }
 
 __global__ void __launch_bounds__(256) refine_init_kernel(const float *__restrict__ tau, float *__restrict__ u,
@@ -217,39 +302,47 @@ __global__ void __launch_bounds__(256) refine_init_kernel(const float *__restric
 
 size_t refine_scratch_bytes(uint64_t n)
 {
-    return (size_t)n * (sizeof(float4) * 2 + sizeof(float) * 5);  // moments, u, gradients (f3, tau)
+    return (size_t)n * (sizeof(float4) * 2 + sizeof(float));  // moments, u
 }
 
 cudaError_t launch_refine(const MapDev &m, float *f3, float *tau, uint64_t n, int steps, float lr_f, float lr_u,
-                          float tau_max, float *hist, void *scratch, cudaStream_t st)
+                          float tau_max, float *hist, void *scratch, int P, cudaStream_t st)
 {
     if (n == 0 || steps < 0) return cudaSuccess;
-    float4 *mom = static_cast<float4 *>(scratch);
-    float *u = reinterpret_cast<float *>(mom + 2 * n), *gf3 = u + n, *gtau = gf3 + 3 * n;
-    const unsigned blocks = (unsigned)((n + 255) / 256);
-    refine_init_kernel<<<blocks, 256, 0, st>>>(tau, u, mom, n, tau_max);
+    AdamStep ad{};
+    ad.mom = static_cast<float4 *>(scratch);
+    ad.u = reinterpret_cast<float *>(ad.mom + 2 * n);
+    ad.tau_max = tau_max;
+    ad.f_hi = (float)(m.n_f - 1);
+    refine_init_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(tau, ad.u, ad.mom, n, tau_max);
     cudaError_t e = cudaGetLastError();
-    const float f_hi = (float)(m.n_f - 1);
     for (int t = 1; t <= steps && e == cudaSuccess; ++t) {
-        // the step's SNR (history row t - 1) and its gradient, then the update
-        e = launch_interp(m, f3, tau, nullptr, n, hist ? hist + (size_t)(t - 1) * n : nullptr, gf3, gtau, true, st);
-        if (e != cudaSuccess) break;
+        // the step's SNR (history row t - 1), its gradient and the update, in one launch
         const double bc1 = 1.0 - std::pow(0.9, t), bc2 = 1.0 - std::pow(0.999, t);
-        adam_kernel<<<blocks, 256, 0, st>>>(f3, u, tau, gf3, gtau, mom, n, (float)(lr_f / bc1), (float)(lr_u / bc1),
-                                            (float)std::sqrt(bc2), tau_max, f_hi);
-        e = cudaGetLastError();
+        ad.step_f = (float)(lr_f / bc1);
+        ad.step_u = (float)(lr_u / bc1);
+        ad.sbc2 = (float)std::sqrt(bc2);
+        e = launch_interp_M<2>(m, f3, tau, nullptr, n, hist ? hist + (size_t)(t - 1) * n : nullptr, nullptr,
+                               nullptr, ad, P, st);
     }
     if (e == cudaSuccess && hist)
-        e = launch_interp(m, f3, tau, nullptr, n, hist + (size_t)steps * n, nullptr, nullptr, false, st);
+        e = launch_interp_M<0>(m, f3, tau, nullptr, n, hist + (size_t)steps * n, nullptr, nullptr, AdamStep{}, P,
+                               st);
     return e;
+}
+
+cudaError_t launch_interp_tuned(const MapDev &m, const float *f3, const float *tau, const float *g, uint64_t n,
+                                float *snr, float *gf3, float *gtau, bool adjoint, int P, cudaStream_t st)
+{
+    if (n == 0) return cudaSuccess;
+    return adjoint ? launch_interp_M<1>(m, f3, tau, g, n, snr, gf3, gtau, AdamStep{}, P, st)
+                   : launch_interp_M<0>(m, f3, tau, g, n, snr, gf3, gtau, AdamStep{}, P, st);
 }
 
 cudaError_t launch_interp(const MapDev &m, const float *f3, const float *tau, const float *g, uint64_t n, float *snr,
                           float *gf3, float *gtau, bool adjoint, cudaStream_t st)
 {
-    if (n == 0) return cudaSuccess;
-    return adjoint ? launch_interp_A<true>(m, f3, tau, g, n, snr, gf3, gtau, st)
-                   : launch_interp_A<false>(m, f3, tau, g, n, snr, gf3, gtau, st);
+    return launch_interp_tuned(m, f3, tau, g, n, snr, gf3, gtau, adjoint, 0, st);
 }
 
 }  // namespace stk

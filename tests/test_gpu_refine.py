@@ -273,3 +273,44 @@ def test_refine_edge_cases(ctx):
         kw.update(bad)
         with pytest.raises(stk.StkError):
             ctx.refine(m, f3, tau, **kw)
+
+
+@pytest.mark.parametrize("threads", [32, 64, 128])
+def test_threads_per_template(ctx, threads):
+    """Every template layout (one warp, two, four per template; a ragged last block)
+    against the FP64 oracle, and the device ascent for each."""
+    from paper_1401_8060_b300 import _lib
+    n_t, n_f, n = 150, 260, 77
+    y, sig = _map("pixel", n_t, n_f, 88)
+    m = ctx.load_map(torch.from_numpy(y).cuda(), torch.from_numpy(sig).cuda(), 40.0, 0.5)
+    om = oracle.OracleMap(y, sig, 40.0, 0.5, False)
+    rng = np.random.default_rng(89)
+    f3 = rng.uniform(0, n_f - 1, (n, 3)).astype(np.float32)
+    tau = rng.uniform(-TAU_MAX, TAU_MAX, n).astype(np.float32)
+    f3t, taut = torch.from_numpy(f3).cuda(), torch.from_numpy(tau).cuda()
+    ctx.set_option(_lib.STK_OPT_INTERP_THREADS, threads)
+    try:
+        snr = ctx.interp_forward(m, f3t, taut).cpu().numpy()
+        gf, gt = ctx.interp_adjoint(m, f3t, taut, torch.ones(n, device="cuda"))
+        f_new, t_new, h = ctx.refine(m, f3t, taut, TAU_MAX, steps=5)
+    finally:
+        ctx.set_option(_lib.STK_OPT_INTERP_THREADS, 0)
+    o, og = om.interp_score(f3.astype(np.float64), tau.astype(np.float64), grad=True)
+    _, ex = om.score_explicit(np.clip(np.round(f3), 0, n_f - 1).astype(np.uint32), tau.astype(np.float64),
+                              extras=True)
+    sc = ex["absz"] / np.sqrt(ex["W"])
+    assert np.all(np.abs(snr - o) <= 2e-5 * sc + 1e-5 * np.abs(o))
+    got = np.concatenate([gf.cpu().numpy(), gt.cpu().numpy()[:, None]], axis=1)
+    assert np.all(np.abs(got - og) <= 2e-4 * np.max(np.abs(og), axis=0) + 1e-4 * np.abs(og))
+    # the ascent: history row 0 is the forward statistic, the last row the SNR at the result
+    assert np.allclose(h[0].cpu().numpy(), snr, rtol=0, atol=1e-5 * (1 + np.max(np.abs(snr))))
+    o5 = om.interp_score(f_new.cpu().numpy().astype(np.float64), t_new.cpu().numpy().astype(np.float64))
+    assert np.all(np.abs(h[-1].cpu().numpy() - o5) <= 2e-5 * sc * 2 + 1e-5 * np.abs(o5))
+    assert float((h[-1] - h[0]).mean()) > 0
+
+
+def test_threads_option_range(ctx):
+    from paper_1401_8060_b300 import _lib
+    for bad in (1, 16, 96, 256, -32):
+        with pytest.raises(stk.StkError):
+            ctx.set_option(_lib.STK_OPT_INTERP_THREADS, bad)
