@@ -224,7 +224,9 @@ STK_API int stk_score_explicit_general(stk_ctx *ctx, const stk_map *map, const u
  *   S = sum_j Re[exp(2 pi i (f_min + x_j df) tau) z(j, x_j)],  W = sum_j w(j, x_j),
  *   SNR = S / sqrt(W), or S / N with STK_NORM_PAPER (Eq. 7 at integer bins).
  * f3_dev: float [n][3]; tau_dev: float [n] seconds; device memory, caller-owned.
- * Arithmetic is FP32 except the curve position and phase argument (FP64). */
+ * Arithmetic is FP32 except the curve position and phase (fixed point, Q32.32
+ * bins and Q0.64 turns).  A template with a control frequency of magnitude
+ * 2^30 bins or more, or a non-finite one or delay, gets NaN. */
 
 /* snr_dev[i] = SNR of continuous template i (float [n]).  Errors: STK_EINVAL, STK_ECUDA. */
 STK_API int stk_interp_forward(stk_ctx *ctx, const stk_map *map, const float *f3_dev, const float *tau_dev,
@@ -376,8 +378,8 @@ STK_API int stk_score_noalloc(const stk_map *map, uint64_t n_tracks, uint64_t se
                                    (likelier with a small sample) makes the selection fall back to an
                                    exact radix select over every SNR, which is slower */
 #define STK_OPT_INTERP_THREADS 10 /* continuous templates (stk_interp_*, stk_refine): threads per
-                                     template, 0 (default: 128 up to 384 templates, 64 up to 1536,
-                                     else 32), 32, 64 or 128.  Results may differ in the last bits
+                                     template, 0 (default: 64 up to 512 templates, else 32), 32, 64
+                                     or 128.  Results may differ in the last bits
                                      (the order of the column sums) */
 
 /* Set a tuning option for later scoring calls.  Errors: STK_EINVAL. */

@@ -123,36 +123,56 @@ __global__ void __launch_bounds__(kInterpBlock) interp_kernel(MapDev m, InterpCo
     const double a2 = f0 - 2.0 * f1 + f2, a1 = 2.0 * M * (f1 - f0), a0 = M * M * f0;
     const double fa = k.df * tau, fb = k.f_min * tau;     // turns per bin, turns at bin 0
     const float two_pi = 6.28318530717958647692f;
-    // x_j by forward differences along the thread's columns j, j + P, ...: two FP64
-    // additions a column (x(j + P) - x(j) = (a2 (2 P j + P^2) + a1 P) / M^2, and the
-    // second difference 2 P^2 a2 / M^2 is constant)
+    // Column j, j + P, ... of this thread by forward differences (x(j + P) - x(j) =
+    // (a2 (2 P j + P^2) + a1 P) / M^2, second difference 2 P^2 a2 / M^2), in fixed
+    // point so the column loop has no FP64 arithmetic (a slow pipe on this GPU):
+    // the position X = x 2^32 (Q32.32) and the phase T = frac(fb + fa x) 2^64
+    // (Q0.64, wrapping), each a quadratic in j, advance by exact integer additions.
+    // The differences are rounded once from FP64, so after s steps the position is
+    // within about s^2 2^-33 bins and the phase within s^2 2^-65 turns (s <= n_t /
+    // P).  |x| <= max |f| by the convex hull, so |f| < 2^30 keeps X in range;
+    // larger or non-finite control frequencies give NaN.
+    const bool finite = fabs(f0) < 1073741824.0 && fabs(f1) < 1073741824.0 && fabs(f2) < 1073741824.0 &&
+                        fabs(tau) < 1e30;
     const double jl = (double)t, Pd = (double)P;
-    double x_next = ((a2 * jl + a1) * jl + a0) * inv_M2;
-    double dx = (a2 * (2.0 * Pd * jl + Pd * Pd) + a1 * Pd) * inv_M2;
-    const double ddx = 2.0 * Pd * Pd * a2 * inv_M2;
+    const double x_t = finite ? ((a2 * jl + a1) * jl + a0) * inv_M2 : 0.0;
+    const double dx = finite ? (a2 * (2.0 * Pd * jl + Pd * Pd) + a1 * Pd) * inv_M2 : 0.0;
+    const double ddx = finite ? 2.0 * Pd * Pd * a2 * inv_M2 : 0.0;
+    const double two32 = 4294967296.0;
+    int64_t X = __double2ll_rn(x_t * two32), DX = __double2ll_rn(dx * two32);
+    const int64_t DDX = __double2ll_rn(ddx * two32);
+    auto q64 = [](double turns) {                         // frac(turns) as Q0.64
+        const double fr = turns - floor(turns);           // [0, 1]
+        return (uint64_t)__double2ll_rn(ldexp(fr - rint(fr), 63)) << 1;  // signed [-1/2, 1/2] turn, 2^-63 steps
+    };
+    uint64_t T = finite ? q64(fb + fa * x_t) : 0, DT = finite ? q64(fa * dx) : 0;
+    const uint64_t DDT = finite ? q64(fa * ddx) : 0;
+    const uint64_t T_lo = finite ? q64(fb) : 0, T_hi = finite ? q64(fb + fa * (double)(n_f - 1)) : 0;
+    const int64_t X_hi = (int64_t)(n_f - 1) << 32;
     float S = 0.f, W = 0.f;
     float dS0 = 0.f, dS1 = 0.f, dS2 = 0.f, dS3 = 0.f, dW0 = 0.f, dW1 = 0.f, dW2 = 0.f;
     for (int j = t; j < n_t; j += P) {
-        double x = x_next;
-        x_next += dx;
-        dx += ddx;
+        int64_t Xc = X;
+        uint64_t Tc = T;
+        X += DX;
+        DX += DDX;
+        T += DT;
+        DT += DDT;
         bool clamped = false;
-        if (x < 0.0) { x = 0.0; clamped = true; }
-        if (x > (double)(n_f - 1)) { x = (double)(n_f - 1); clamped = true; }
-        int kb = (int)floor(x);
-        if (kb > n_f - 2) kb = n_f - 2;
-        if (kb < 0) kb = 0;
-        const float a = n_f > 1 ? (float)(x - (double)kb) : 0.f;
+        if (Xc < 0) { Xc = 0; Tc = T_lo; clamped = true; }
+        if (Xc > X_hi) { Xc = X_hi; Tc = T_hi; clamped = true; }
+        int kb = (int)(Xc >> 32);
+        float a = (float)(uint32_t)Xc * 2.3283064365386963e-10f;  // fraction of the bin, 2^-32
+        if (kb > n_f - 2) { a += (float)(kb - (n_f - 2)); kb = n_f - 2; }  // x = n_f - 1: the top knot
+        if (n_f < 2) { kb = 0; a = 0.f; }
         float z0r, z0i, w0, z1r, z1i, w1;
         pixel_at<WMODE, PREC>(m, j, kb, z0r, z0i, w0);
         if (n_f > 1) pixel_at<WMODE, PREC>(m, j, kb + 1, z1r, z1i, w1);
         else { z1r = z0r; z1i = z0i; w1 = w0; }
         const float dzr = z1r - z0r, dzi = z1i - z0i, dw = w1 - w0;
         const float zr = fmaf(a, dzr, z0r), zi = fmaf(a, dzi, z0i), w = fmaf(a, dw, w0);
-        double turns = fb + x * fa;
-        turns -= rint(turns);                                // [-1/2, 1/2]
         float sn, cs;
-        __sincosf(two_pi * (float)turns, &sn, &cs);
+        __sincosf((float)(int32_t)(Tc >> 32) * (two_pi * 2.3283064365386963e-10f), &sn, &cs);
         const float re = cs * zr - sn * zi, im = sn * zr + cs * zi;
         S += re;
         W += w;
@@ -167,7 +187,7 @@ __global__ void __launch_bounds__(kInterpBlock) interp_kernel(MapDev m, InterpCo
             dW0 = fmaf(dw_dx, c0, dW0);
             dW1 = fmaf(dw_dx, c1, dW1);
             dW2 = fmaf(dw_dx, c2, dW2);
-            dS3 = fmaf(-im, two_pi * fmaf((float)x, k.df_f, k.fmin_f), dS3);
+            dS3 = fmaf(-im, two_pi * fmaf((float)kb + a, k.df_f, k.fmin_f), dS3);
         }
     }
     constexpr int NV = ADJOINT ? 9 : 2;
@@ -197,6 +217,9 @@ __global__ void __launch_bounds__(kInterpBlock) interp_kernel(MapDev m, InterpCo
             }
     }
     if (t != 0 || !valid) return;
+    if (!finite)
+#pragma unroll
+        for (int q = 0; q < NV; ++q) v[q] = __int_as_float(0x7fc00000);  // NaN
     S = v[0];
     W = v[1];
     const bool varying = WMODE != WMODE_CONST && !m.paper;
@@ -243,14 +266,12 @@ InterpConst interp_const(const MapDev &m)
 // Threads per template: 0 picks by the template count.  More threads per template
 // fill the GPU when templates are few; each thread also repeats the template's
 // setup, so with many templates one warp each is fastest (50 ascent steps on the
-// 500 x 1600 map, ms, for 32 / 64 / 128 threads: 256 templates 0.98 / 0.66 / 0.56,
-// 1024: 1.29 / 1.29 / 1.44, 4096: 3.78 / 4.00 / 4.69).
+// 500 x 1600 map, ms, for 32 / 64 / 128 threads: 256 templates 0.88 / 0.66 / 0.66,
+// 1024: 0.98 / 1.13 / 1.46, 4096: 1.90 / 2.75 / 4.87, 16384: 5.27 / 9.47 / 18.1).
 int interp_threads(uint64_t n, int P)
 {
     if (P == 32 || P == 64 || P == 128) return P;
-    if (n <= 384) return 128;
-    if (n <= 1536) return 64;
-    return 32;
+    return n <= 512 ? 64 : 32;
 }
 
 template <int MODE, int P>
