@@ -34,6 +34,16 @@ BYTES_PER_TRACK_PIXEL = 8     # one complex FP32 pixel (the per-frequency weight
 SMEM_BYTES_PER_CLK_PER_SM = 128
 
 
+def hbm_peak_gbs():
+    """Measured HBM copy bandwidth of this GPU model (GB/s) from MEASURED_PEAKS.json beside
+    this script, else None."""
+    try:
+        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        return None
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -290,7 +300,21 @@ def main():
     T, K = (args.tracks or w["n_tracks"]), w["k"]
     stream = torch.cuda.current_stream()
     ctx = stk.Context(local, stream)
-    m = ctx.load_map(torch.from_numpy(fm.y).cuda(), torch.from_numpy(fm.sigma).cuda(), fm.f_min, fm.df)
+    y_dev, s_dev = torch.from_numpy(fm.y).cuda(), torch.from_numpy(fm.sigma).cuda()
+    m = ctx.load_map(y_dev, s_dev, fm.f_min, fm.df)
+    # map pack (row a1, once per map, outside the track-pixel rate): stk_update_map from device
+    # buffers is the pack kernel alone (y and sigma read, packed records and weights written)
+    for _ in range(3):
+        ctx.update_map(m, y_dev, s_dev)
+    torch.cuda.synchronize()
+    pk0, pk1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    pk0.record(stream)
+    for _ in range(20):                     # back to back: the GPU time per pack unless enqueueing is slower
+        ctx.update_map(m, y_dev, s_dev)
+    pk1.record(stream)
+    torch.cuda.synchronize()
+    pack_ms = pk0.elapsed_time(pk1) / 20
+    pack_bytes = fm.y.nbytes + fm.sigma.nbytes + fm.n_t * fm.n_f * 8 + fm.n_f * 4
     offset = rank * T                       # each rank: its own T templates
     ctx.set_tracks(T, w["seed"], offset, w["tau_max"])
     out = torch.zeros(K * 40, dtype=torch.uint8, device="cuda")
@@ -639,6 +663,11 @@ def main():
                          "peak_source": f"derived: {SMEM_BYTES_PER_CLK_PER_SM} B/clk/SM x {n_sm} SMs x "
                                         f"{sm_mhz:.0f} MHz (median SM clock sampled in the timed region)"},
             "select_ms": sum(select_ms) / len(select_ms), "order_ms": sum(order_ms) / len(order_ms),
+            "map_pack": {"ms": pack_ms, "bytes": pack_bytes, "GB_per_s": pack_bytes / pack_ms / 1e6,
+                         "frac_of_hbm": pack_bytes / pack_ms / 1e6 / hbm_peak_gbs() if hbm_peak_gbs() else None,
+                         "api": "stk_update_map from device buffers (a weight-table clear and the pack kernel: "
+                                "y, sigma in; FP32 records and the weight table out), 20 back to back, per call; "
+                                "not in the track-pixel rate"},
             "clocks": clocks,
             "gpu_launches": launches,
             "wall_s_timed_region": wall,

@@ -65,7 +65,9 @@ __global__ void pack_kernel(const float2 *__restrict__ y, const float *__restric
     const uint64_t total = (uint64_t)n_t * ldr;
     for (uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; p < total;
          p += (uint64_t)gridDim.x * blockDim.x) {
-        const int t = (int)(p / ldr), k = (int)(p % ldr);
+        // row and column: a 32-bit division when the map has fewer than 2^32 records
+        const int t = total <= 0xffffffffull ? (int)((uint32_t)p / (uint32_t)ldr) : (int)(p / ldr);
+        const int k = (int)(p - (uint64_t)t * ldr);
         if (k >= n_f) {
             rec[p] = make_uint2(0u, 0u);
             continue;
@@ -98,7 +100,9 @@ __global__ void pack_fp16_kernel(const float2 *__restrict__ y, const float *__re
     const uint64_t total = (uint64_t)n_t * ldr;
     for (uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; p < total;
          p += (uint64_t)gridDim.x * blockDim.x) {
-        const int t = (int)(p / ldr), k = (int)(p % ldr);
+        // row and column: a 32-bit division when the map has fewer than 2^32 records
+        const int t = total <= 0xffffffffull ? (int)((uint32_t)p / (uint32_t)ldr) : (int)(p / ldr);
+        const int k = (int)(p - (uint64_t)t * ldr);
         if (k >= n_f) {
             rec[p] = 0u;
             continue;
