@@ -378,8 +378,8 @@ STK_API int stk_score_noalloc(const stk_map *map, uint64_t n_tracks, uint64_t se
                                    (likelier with a small sample) makes the selection fall back to an
                                    exact radix select over every SNR, which is slower */
 #define STK_OPT_INTERP_THREADS 10 /* continuous templates (stk_interp_*, stk_refine): threads per
-                                     template, 0 (default: 64 up to 512 templates, else 32), 32, 64
-                                     or 128.  Results may differ in the last bits
+                                     template, 0 (default: 128 up to 512 templates, 64 up to 1536,
+                                     else 32), 32, 64 or 128.  Results may differ in the last bits
                                      (the order of the column sums) */
 
 /* Set a tuning option for later scoring calls.  Errors: STK_EINVAL. */

@@ -128,9 +128,9 @@ __global__ void __launch_bounds__(kInterpBlock) interp_kernel(MapDev m, InterpCo
     // point so the column loop has no FP64 arithmetic (a slow pipe on this GPU):
     // the position X = x 2^32 (Q32.32) and the phase T = frac(fb + fa x) 2^64
     // (Q0.64, wrapping), each a quadratic in j, advance by exact integer additions.
-    // The differences are rounded once from FP64, so after s steps the position is
-    // within about s^2 2^-33 bins and the phase within s^2 2^-65 turns (s <= n_t /
-    // P).  |x| <= max |f| by the convex hull, so |f| < 2^30 keeps X in range;
+    // The position's differences are rounded once from FP64, so after s steps it is
+    // within about s^2 2^-33 bins (s <= n_t / P); the phase is exact given its
+    // coefficients, each within 2^-64 turn.  |x| <= max |f| by the convex hull, so |f| < 2^30 keeps X in range;
     // larger or non-finite control frequencies give NaN.
     const bool finite = fabs(f0) < 1073741824.0 && fabs(f1) < 1073741824.0 && fabs(f2) < 1073741824.0 &&
                         fabs(tau) < 1e30;
@@ -141,13 +141,31 @@ __global__ void __launch_bounds__(kInterpBlock) interp_kernel(MapDev m, InterpCo
     const double two32 = 4294967296.0;
     int64_t X = __double2ll_rn(x_t * two32), DX = __double2ll_rn(dx * two32);
     const int64_t DDX = __double2ll_rn(ddx * two32);
-    auto q64 = [](double turns) {                         // frac(turns) as Q0.64
-        const double fr = turns - floor(turns);           // [0, 1]
-        return (uint64_t)__double2ll_rn(ldexp(fr - rint(fr), 63)) << 1;  // signed [-1/2, 1/2] turn, 2^-63 steps
-    };
-    uint64_t T = finite ? q64(fb + fa * x_t) : 0, DT = finite ? q64(fa * dx) : 0;
-    const uint64_t DDT = finite ? q64(fa * ddx) : 0;
-    const uint64_t T_lo = finite ? q64(fb) : 0, T_hi = finite ? q64(fb + fa * (double)(n_f - 1)) : 0;
+    // The phase is a quadratic in j modulo one turn: T(j) = tau0 + tau1 j + tau2 j^2
+    // with tau0 = frac(fb + fa C0), tau1 = frac(fa C1), tau2 = frac(fa C2) and
+    // x(j) = C0 + C1 j + C2 j^2.  The template's thread 0 converts them to Q0.64
+    // (FP64, once a template); every thread's start value and differences follow
+    // in wrapping 64-bit integer arithmetic, exact given the three coefficients.
+    __shared__ uint64_t tq[TPB][5];  // tau0, tau1, tau2, and the phases at the band edges
+    const int tl = tid / P;
+    if (t == 0) {
+        auto q64 = [](double turns) {                      // frac(turns) as Q0.64
+            const double fr = turns - floor(turns);        // [0, 1]
+            return (uint64_t)__double2ll_rn(ldexp(fr - rint(fr), 63)) << 1;  // signed [-1/2, 1/2] turn
+        };
+        tq[tl][0] = finite ? q64(fb + fa * (a0 * inv_M2)) : 0;
+        tq[tl][1] = finite ? q64(fa * (a1 * inv_M2)) : 0;
+        tq[tl][2] = finite ? q64(fa * (a2 * inv_M2)) : 0;
+        tq[tl][3] = finite ? q64(fb) : 0;
+        tq[tl][4] = finite ? q64(fb + fa * (double)(n_f - 1)) : 0;
+    }
+    if (WPT > 1) __syncthreads();
+    else __syncwarp();  // one warp a template: its lane 0 wrote, its lanes read
+    const uint64_t tau1 = tq[tl][1], tau2 = tq[tl][2], T_lo = tq[tl][3], T_hi = tq[tl][4];
+    const uint64_t tt = (uint64_t)t, PP = (uint64_t)P;
+    uint64_t T = tq[tl][0] + tau1 * tt + tau2 * (tt * tt);
+    uint64_t DT = tau1 * PP + tau2 * (2 * PP * tt + PP * PP);
+    const uint64_t DDT = tau2 * (2 * PP * PP);
     const int64_t X_hi = (int64_t)(n_f - 1) << 32;
     float S = 0.f, W = 0.f;
     float dS0 = 0.f, dS1 = 0.f, dS2 = 0.f, dS3 = 0.f, dW0 = 0.f, dW1 = 0.f, dW2 = 0.f;
@@ -264,14 +282,17 @@ InterpConst interp_const(const MapDev &m)
 }
 
 // Threads per template: 0 picks by the template count.  More threads per template
-// fill the GPU when templates are few; each thread also repeats the template's
-// setup, so with many templates one warp each is fastest (50 ascent steps on the
-// 500 x 1600 map, ms, for 32 / 64 / 128 threads: 256 templates 0.88 / 0.66 / 0.66,
-// 1024: 0.98 / 1.13 / 1.46, 4096: 1.90 / 2.75 / 4.87, 16384: 5.27 / 9.47 / 18.1).
+// fill the GPU when templates are few; each thread also repeats part of the
+// template's setup, so with many templates one warp each is fastest (50 ascent
+// steps on the 500 x 1600 map, ms, for 32 / 64 / 128 threads: 256 templates
+// 0.78 / 0.69 / 0.57, 1024: 0.98 / 0.98 / 0.98, 4096: 1.93 / 2.19 / 3.00,
+// 16384: 5.43 / 7.13 / 10.5).
 int interp_threads(uint64_t n, int P)
 {
     if (P == 32 || P == 64 || P == 128) return P;
-    return n <= 512 ? 64 : 32;
+    if (n <= 512) return 128;
+    if (n <= 1536) return 64;
+    return 32;
 }
 
 template <int MODE, int P>
