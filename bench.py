@@ -460,8 +460,8 @@ def main():
             "frac_improved": float((hist[-1] > hist[0]).float().mean()),
             "discrete_snr_mean_before": float(np.mean(hits["snr"])),
             "discrete_snr_mean_after_rounding": float(np.mean(d_after)),
-            "kernels": "stk_refine: per step the interpolated SNR and its gradient (one 128-thread block per template) "
-                       "and one Adam step, all on the device; 2 launches per step"}
+            "kernels": "stk_refine: per step one launch computes the interpolated SNR, its gradient and the Adam "
+                       "step (32-128 threads per template, chosen by count; position and phase in fixed point)"}
         ctx.set_profiling(True)
 
     # 256 ragged maps in one persistent launch vs 256 sequential single-map launches
