@@ -1,6 +1,7 @@
 """Build libstk.so (the CUDA scorer, sm_103a) in-tree with nvcc."""
 from __future__ import annotations
 
+import concurrent.futures
 import glob
 import os
 import subprocess
@@ -42,7 +43,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_v: bool = False) -> 
         return LIB
     objdir = os.path.join(HERE, "_build")
     os.makedirs(objdir, exist_ok=True)
-    objs = []
+    objs, cmds = [], []
     for src in sources():
         obj = os.path.join(objdir, os.path.basename(src) + ".o")
         cmd = [NVCC] + NVCC_FLAGS + ["-I", os.path.join(ROOT, "include"), "-c", src, "-o", obj]
@@ -50,8 +51,13 @@ def build(force: bool = False, verbose: bool = False, ptxas_v: bool = False) -> 
             cmd += ["-Xptxas", "-v"]
         if verbose:
             print(" ".join(cmd), file=sys.stderr)
-        subprocess.run(cmd, check=True)
+        cmds.append(cmd)
         objs.append(obj)
+    # the translation units are independent: compile them side by side
+    workers = max(1, min(len(cmds), os.cpu_count() or 1))
+    with concurrent.futures.ThreadPoolExecutor(workers) as pool:
+        for f in [pool.submit(subprocess.run, cmd, check=True) for cmd in cmds]:
+            f.result()
     tmp = LIB + ".tmp.%d" % os.getpid()
     subprocess.run([NVCC, "-shared", "-cudart", "static", "-o", tmp] + objs, check=True)
     os.replace(tmp, LIB)
