@@ -335,11 +335,22 @@ STK_API int stk_batch_tune(stk_batch *batch, int k, int64_t out[4]);
  * in device memory that every GPU loading the library holds until the process
  * exits; the call itself calls no cudaMalloc, cudaFree or other allocating
  * routine.  The map must have been loaded earlier (stk_load_map allocates).
+ * cuda_stream first waits for the work already issued on the map context's
+ * stream (a pending stk_update_map pack), so the call sees the map's latest
+ * data whichever stream the caller uses.  The launch shape and wait limits
+ * follow the map context's tuning options (stk_set_option); templates are
+ * scored in index order.
  *   n_tracks    1 .. STK_NOALLOC_MAX_TRACKS (2^20); larger ranges: split them
- *               over several calls and keep the largest SNRs (Sec. V rule)
+ *               over several calls and keep the k largest SNRs of all of them
+ *               (SNR descending, then template index ascending)
  *   k           1 .. min(STK_MAX_K, n_tracks)
- *   status_dev  caller-owned device int or NULL; set to STK_OK, or to
- *               STK_ETIMEOUT when a bounded in-kernel wait gave up
+ *   status_dev  caller-owned device int or NULL; set to STK_OK, to
+ *               STK_ETIMEOUT when a bounded in-kernel wait gave up, or to
+ *               STK_EINVAL when the map context holds a deferred error from
+ *               packing bad data (non-finite y, sigma <= 0, FP16 range; read and
+ *               cleared by the context's next stk_sync)
+ * In both failure cases every output hit is marked invalid (snr NaN, index
+ * UINT64_MAX), with or without status_dev.
  * The first call on a device resolves the array's device address
  * (cudaGetSymbolAddress, with the map's device current); make that first call
  * before any stream capture.  Every call on a device shares the one array,

@@ -53,9 +53,9 @@ int flags_to_status(stk_ctx *c, int f)
 
 namespace {
 
-// Pack y, sigma into polar records z = |z| e^{2 pi i arg} with
-// z = y sigma^-2 (weighted) or y / sigma (paper form), and the weights.  FP32
-// arithmetic (|z| to about 2 ulp, the angle to about 1e-7 rad).
+// Pack y, sigma into polar records z = |z| e^{i arg} with z = y sigma^-2
+// (weighted) or y / sigma (paper form), and the weights.  FP32 arithmetic (|z|
+// to about 2 ulp; the angle, in radians in [-pi, pi], to about 2 ulp).
 __global__ void pack_kernel(const float2 *__restrict__ y, const float *__restrict__ sigma, int per_freq, int n_t,
                             int n_f, int ldr, int ldw, int paper, uint2 *__restrict__ rec, float *__restrict__ wout,
                             int *err)
@@ -80,8 +80,7 @@ __global__ void pack_kernel(const float2 *__restrict__ y, const float *__restric
         const float w = paper ? 1.f : 1.f / (s * s);
         const float h = hypotf(v.x, v.y);
         const float mag = paper ? h / s : h * w;
-        const float turns = atan2f(v.y, v.x) * 0.159154943091895336f;  // [-1/2, 1/2]; a positive scale keeps it
-        rec[p] = make_uint2(__float_as_uint(mag), (uint32_t)llrintf(turns * 4294967296.0f));
+        rec[p] = make_uint2(__float_as_uint(mag), __float_as_uint(atan2f(v.y, v.x)));
         if (wout) {
             if (!per_freq) wout[(size_t)t * ldw + k] = w;
             else if (t == 0) wout[k] = w;
@@ -90,7 +89,7 @@ __global__ void pack_kernel(const float2 *__restrict__ y, const float *__restric
     if (flags) atomicOr(err, flags);
 }
 
-// FP16 storage: record = (Q0.16 arg y) << 16 | FP16(|y| / sigma); weights r = 1/sigma.
+// FP16 storage: record = FP16(|y| / sigma) << 16 | (Q0.16 arg y); weights r = 1/sigma.
 __global__ void pack_fp16_kernel(const float2 *__restrict__ y, const float *__restrict__ sigma, int per_freq, int n_t,
                                  int n_f, int ldr, int ldw, uint32_t *__restrict__ rec, float *__restrict__ rout,
                                  int *err)
@@ -117,7 +116,7 @@ __global__ void pack_fp16_kernel(const float2 *__restrict__ y, const float *__re
         const float turns = atan2f(v.y, v.x) * 0.159154943091895336f;  // [-1/2, 1/2]
         const uint32_t a16 = (uint32_t)llrintf(turns * 65536.f) & 0xffffu;
         const unsigned short hb = __half_as_ushort(__float2half_rn(h));
-        rec[p] = (a16 << 16) | (uint32_t)hb;
+        rec[p] = ((uint32_t)hb << 16) | a16;
         if (rout) {
             const float r = 1.f / s;
             if (!per_freq) rout[(size_t)t * ldw + k] = r;
@@ -216,6 +215,7 @@ int stk_create(stk_ctx **out, int device, void *cuda_stream)
     }
     cudaMemset(c->d_err, 0, sizeof(int));
     for (auto &ev : c->ev) cudaEventCreate(&ev);
+    cudaEventCreateWithFlags(&c->stream_mark, cudaEventDisableTiming);
     cudaDeviceSynchronize();
     *out = c;
     return STK_OK;
@@ -236,6 +236,7 @@ void stk_destroy(stk_ctx *c)
     cudaFree(c->stage_s);
     cudaFree(c->order_buf);
     cudaFree(c->refine_buf);
+    if (c->stream_mark) cudaEventDestroy(c->stream_mark);
     for (auto &ev : c->ev)
         if (ev) cudaEventDestroy(ev);
     delete c;
@@ -791,9 +792,20 @@ int noalloc_setup(int dev, NoAllocDevice *out)
     return STK_OK;
 }
 
-__global__ void noalloc_status_kernel(const int *flags, int *status)
+// After the selection: on a timeout (some templates' SNRs were not written and
+// the array still holds an earlier call's values) or on bad map data reported
+// by a deferred pack, every output hit is marked invalid (SNR NaN, index all
+// ones); the status word, if given, gets STK_ETIMEOUT, STK_EINVAL or STK_OK.
+__global__ void noalloc_finish_kernel(const int *flags, const int *ctx_flags, int k, stk_hit *out, int *status)
 {
-    *status = (*flags & ERR_TIMEOUT) ? STK_ETIMEOUT : STK_OK;
+    const bool timeout = (*flags & ERR_TIMEOUT) != 0;
+    const bool bad = (*ctx_flags & (ERR_BADINPUT | ERR_FP16_RANGE)) != 0;
+    if (timeout || bad)
+        for (int i = threadIdx.x; i < k; i += blockDim.x) {
+            out[i].snr = __longlong_as_double(0x7ff8000000000000ll);
+            out[i].index = ~0ull;
+        }
+    if (status && threadIdx.x == 0) *status = timeout ? STK_ETIMEOUT : bad ? STK_EINVAL : STK_OK;
 }
 
 }  // namespace
@@ -825,25 +837,31 @@ extern "C" int stk_score_noalloc(const stk_map *m, uint64_t n_tracks, uint64_t s
     int rc = noalloc_setup(dev, &d);
     if (rc == STK_OK) {
         cudaStream_t st = (cudaStream_t)cuda_stream;
+        stk_ctx *c = m->ctx;
         unsigned char *base = (unsigned char *)d.base;
         float *snr = (float *)base;
         int *flags = (int *)(base + kNoAllocSnrBytes);
         void *sel = base + kNoAllocSnrBytes + kNoAllocFlagBytes;
         TrackSet ts{n_tracks, seed, counter_offset, tau_max_s};
-        Tuning tu{};
+        Tuning tu = c->tune;  // launch shape and wait limits; no coherent order (it needs scratch)
         ScorePlan plan{};
         int nl = 0;
-        // The array keeps the previous call's contents: the flag word must start at zero;
-        // the selection kernels reset their own state; every SNR is overwritten.
-        if ((e = cudaMemsetAsync(flags, 0, sizeof(int), st)) != cudaSuccess ||
+        // The map's last load or update may still be packing on the context's
+        // stream: this stream waits for it.  The array keeps the previous call's
+        // contents: the flag word must start at zero; the selection kernels reset
+        // their own state; the scoring kernel writes every SNR unless a bounded wait
+        // gives up, and then the finishing kernel marks the hits invalid.
+        if ((e = cudaEventRecord(c->stream_mark, c->stream)) != cudaSuccess ||
+            (e = cudaStreamWaitEvent(st, c->stream_mark, 0)) != cudaSuccess ||
+            (e = cudaMemsetAsync(flags, 0, sizeof(int), st)) != cudaSuccess ||
             (e = launch_score_generated(m->dev, ts, snr, flags, tu, d.num_sms, d.smem_optin, st, &plan)) !=
                 cudaSuccess ||
             (e = launch_select_topk(snr, n_tracks, k, ts, m->dev, sel, out_topk_dev, st, &nl)) != cudaSuccess)
             rc = set_err(nullptr, STK_ECUDA, "no-allocation scoring: %s", cudaGetErrorString(e));
-        else if (status_dev) {
-            noalloc_status_kernel<<<1, 1, 0, st>>>(flags, status_dev);
+        else {
+            noalloc_finish_kernel<<<1, 256, 0, st>>>(flags, c->d_err, k, out_topk_dev, status_dev);
             if ((e = cudaGetLastError()) != cudaSuccess)
-                rc = set_err(nullptr, STK_ECUDA, "status kernel: %s", cudaGetErrorString(e));
+                rc = set_err(nullptr, STK_ECUDA, "finishing kernel: %s", cudaGetErrorString(e));
         }
     }
     cudaSetDevice(prev);

@@ -70,47 +70,45 @@ struct BatchArgs {
 };
 
 // One slab of one tile: rows time columns for the R templates of this thread.
+// rb, wb: shared addresses of the slab's first record row and weight row, swt_a
+// of the per-frequency weight table.  Columns go in pairs (three rasteriser
+// additions per two columns, exact mod 2^32), each template's sums in column order.
 template <int R, int WMODE, int PREC, bool FAST>
-__device__ __forceinline__ void batch_slab(const typename Pix<PREC>::Rec *row, const float *wrow, const float *swt,
-                                           int rows, int ldr, int ldw, uint32_t magic, int shift, uint32_t d32,
+__device__ __forceinline__ void batch_slab(uint32_t rb, uint32_t wb, uint32_t swt_a, int rows, uint32_t row_bytes,
+                                           uint32_t wrow_bytes, uint32_t magic, int shift, uint32_t d32,
                                            uint32_t (&N)[R], uint32_t (&D)[R], const uint32_t (&D2)[R],
                                            const uint32_t (&pa)[R], const uint32_t (&pc)[R], float (&acc)[R],
                                            float (&W)[R])
 {
     using Rec = typename Pix<PREC>::Rec;
-#pragma unroll 2
-    for (int jj = 0; jj < rows; ++jj) {
+    auto col = [&](int r, uint32_t Nv, uint32_t rb_, uint32_t wb_) {
+        const uint32_t b = FAST ? __umulhi(Nv, magic) >> shift : div_corrected(Nv, magic, shift, d32);
+        const Rec v = Pix<PREC>::load_shared(rb_ + (b << Pix<PREC>::kLog2Bytes));
+        float wv = 0.f;
+        if (WMODE == WMODE_FREQ) wv = lds_f32(swt_a + (b << 2));
+        if (WMODE == WMODE_PIXEL) wv = lds_f32(wb_ + (b << 2));
+        pixel_add<PREC, WMODE>(v, template_turn_narrow(b, pa[r], pc[r]), wv, acc[r], W[r]);
+    };
+    int jj = 0;
+    for (; jj + 1 < rows; jj += 2) {
 #pragma unroll
-        for (int r = 0; r + 1 < R; r += 2) {  // templates in pairs: packed FP32 arithmetic
-            const uint32_t b0 = FAST ? __umulhi(N[r], magic) >> shift : div_corrected(N[r], magic, shift, d32);
-            const uint32_t b1 =
-                FAST ? __umulhi(N[r + 1], magic) >> shift : div_corrected(N[r + 1], magic, shift, d32);
-            const Rec v0 = row[b0], v1 = row[b1];
-            float w0 = 0.f, w1 = 0.f;
-            if (WMODE == WMODE_FREQ) { w0 = swt[b0]; w1 = swt[b1]; }
-            if (WMODE == WMODE_PIXEL) { w0 = wrow[b0]; w1 = wrow[b1]; }
-            accumulate_turn2<PREC, WMODE>(v0, v1, pixel_turn_narrow(b0, pa[r], pc[r], Pix<PREC>::arg(v0)),
-                                          pixel_turn_narrow(b1, pa[r + 1], pc[r + 1], Pix<PREC>::arg(v1)), w0, w1,
-                                          acc[r], acc[r + 1], W[r], W[r + 1]);
-            N[r] += D[r];
-            D[r] += D2[r];
-            N[r + 1] += D[r + 1];
-            D[r + 1] += D2[r + 1];
+        for (int r = 0; r < R; ++r) {
+            const uint32_t Na = N[r], Nb = Na + D[r];
+            col(r, Na, rb, wb);
+            col(r, Nb, rb + row_bytes, wb + wrow_bytes);
+            N[r] = Nb + D[r] + D2[r];
+            D[r] = D[r] + D2[r] + D2[r];
         }
-        if (R & 1) {
-            constexpr int r = R - 1;
-            const uint32_t bin = FAST ? __umulhi(N[r], magic) >> shift : div_corrected(N[r], magic, shift, d32);
-            const Rec v = row[bin];
-            float wv = 0.f;
-            if (WMODE == WMODE_FREQ) wv = swt[bin];
-            if (WMODE == WMODE_PIXEL) wv = wrow[bin];
-            accumulate_turn<PREC, WMODE>(v, pixel_turn_narrow(bin, pa[r], pc[r], Pix<PREC>::arg(v)), wv, acc[r],
-                                         W[r]);
+        rb += 2 * row_bytes;
+        wb += 2 * wrow_bytes;
+    }
+    if (jj < rows) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            col(r, N[r], rb, wb);
             N[r] += D[r];
             D[r] += D2[r];
         }
-        row += ldr;
-        if (WMODE == WMODE_PIXEL) wrow += ldw;
     }
 }
 
@@ -130,6 +128,7 @@ __global__ void __launch_bounds__(batch_max_threads(R), 1) score_batch_kernel(Ba
     int *abort_flag = reinterpret_cast<int *>(done + kBatchStages);
     unsigned char *slabs = smem + kBatchBookkeeping;
     float *swt = reinterpret_cast<float *>(slabs + (size_t)a.nstage * a.slot_bytes);
+    const uint32_t slabs_a = smem_u32(slabs), swt_a = smem_u32(swt);
     unsigned long long *ck = reinterpret_cast<unsigned long long *>(swt + a.wtab_floats);
     unsigned int *ci = reinterpret_cast<unsigned int *>(ck + kMaxWarps * a.K);
     __shared__ unsigned int sh_tile;
@@ -236,15 +235,15 @@ __global__ void __launch_bounds__(batch_max_threads(R), 1) score_batch_kernel(Ba
             }
             const int rows = min(S, n_t - s * S);
             const uint32_t row_bytes = (uint32_t)ldr * (uint32_t)sizeof(Rec);
-            const Rec *row = reinterpret_cast<const Rec *>(slabs + (size_t)slot * a.slot_bytes);
-            const float *wrow = reinterpret_cast<const float *>(slabs + (size_t)slot * a.slot_bytes +
-                                                                (size_t)S * row_bytes);
+            const uint32_t wrow_bytes = WMODE == WMODE_PIXEL ? (uint32_t)ldw * 4u : 0u;
+            const uint32_t rb = slabs_a + (uint32_t)slot * a.slot_bytes;
+            const uint32_t wb = rb + (uint32_t)S * row_bytes;
             if (fast)
-                batch_slab<R, WMODE, PREC, true>(row, wrow, swt, rows, ldr, ldw, magic, shift, d32, N, D, D2, pa, pc,
-                                                 acc, W);
+                batch_slab<R, WMODE, PREC, true>(rb, wb, swt_a, rows, row_bytes, wrow_bytes, magic, shift, d32, N, D,
+                                                 D2, pa, pc, acc, W);
             else
-                batch_slab<R, WMODE, PREC, false>(row, wrow, swt, rows, ldr, ldw, magic, shift, d32, N, D, D2, pa,
-                                                  pc, acc, W);
+                batch_slab<R, WMODE, PREC, false>(rb, wb, swt_a, rows, row_bytes, wrow_bytes, magic, shift, d32, N,
+                                                  D, D2, pa, pc, acc, W);
             // This warp is done with the buffer; the last warp to finish refills it.
             __syncwarp();
             if (lane == 0) {

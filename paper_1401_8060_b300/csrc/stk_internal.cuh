@@ -16,13 +16,13 @@ namespace stk {
 
 // ---------------------------------------------------------------- packed map
 // Each pixel is stored once, in polar form.  FP32 storage: an 8-byte record
-//   .x = bits of |z| (float), .y = arg(z) in turns as unsigned Q0.32,
+//   .x = bits of |z| (FP32), .y = bits of arg z in radians (FP32, [-pi, pi]),
 // where z = y sigma^-2 (weighted statistic) or z = y / sigma (STK_NORM_PAPER);
 // the weight array holds w = sigma^-2.  FP16 storage: a 4-byte record, low
-// half the FP16 value of |y| / sigma (the per-frequency or per-pixel scaling),
-// high half arg(y) in Q0.16 turns; the weight array then holds r = 1/sigma, so
-// |z| = (|y|/sigma) r in the weighted form and the weight is r^2.
-// Re[e^{i theta} z] = |z| cos(theta + 2 pi arg z): one cosine per pixel.
+// half arg(y) in Q0.16 turns, high half the FP16 value of |y| / sigma (the
+// per-frequency or per-pixel scaling); the weight array then holds r = 1/sigma,
+// so |z| = (|y|/sigma) r in the weighted form and the weight is r^2.
+// Re[e^{i theta} z] = |z| cos(theta + arg z): one cosine per pixel.
 enum Prec : int {
     PREC_FP32 = 0,
     PREC_FP16 = 1,
@@ -382,25 +382,21 @@ __host__ __device__ __forceinline__ Phase phase_consts(double f_min, double df, 
     return p;
 }
 
-// Angle (turns, Q0.32 read as signed, i.e. in [-1/2, 1/2)) -> cos(2 pi turn).
-// The integer-to-float conversion rounds to 24 significant bits (error at most
-// 2^-25 turn); __cosf is accurate to about 2^-21 absolute on [-pi, pi].
+// The template's phase at a bin, T = frac((f_min + bin df) tau) as Q0.32 turns
+// (read as signed: [-1/2, 1/2)).  A pixel's angle is then 2 pi T + arg z, with
+// the integer-to-float conversion of T rounding to 24 significant bits (at most
+// 2^-26 turn) and 2 pi / 2^32 rounded to FP32 (2^-24 relative).
 constexpr float kTurnToRad = 1.46291807926715968e-9f;  // 2 pi / 2^32
 
-__device__ __forceinline__ float cos_turn(uint32_t t)
+__device__ __forceinline__ uint32_t template_turn(uint32_t bin, const Phase &p)
 {
-    return __cosf((float)(int32_t)t * kTurnToRad);
-}
-
-__device__ __forceinline__ uint32_t pixel_turn(uint32_t bin, const Phase &p, uint32_t arg)
-{
-    return bin * p.a + __umulhi(bin, p.a_lo) + p.c + arg;
+    return bin * p.a + __umulhi(bin, p.a_lo) + p.c;
 }
 
 // The narrow form (a_lo = 0): slab and batched kernels, n_f <= kPhaseNarrowNf.
-__device__ __forceinline__ uint32_t pixel_turn_narrow(uint32_t bin, uint32_t a, uint32_t c, uint32_t arg)
+__device__ __forceinline__ uint32_t template_turn_narrow(uint32_t bin, uint32_t a, uint32_t c)
 {
-    return bin * a + c + arg;
+    return bin * a + c;
 }
 
 // ---------------------------------------------------------------- rasteriser state
@@ -435,6 +431,28 @@ __device__ __forceinline__ uint32_t raster_bin_wide(uint32_t f0, uint32_t f1, ui
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
 {
     return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// Loads from shared memory at a 32-bit shared-window address.
+__device__ __forceinline__ uint2 lds_u64(uint32_t a)
+{
+    uint2 v;
+    asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "r"(a));
+    return v;
+}
+
+__device__ __forceinline__ uint32_t lds_u32(uint32_t a)
+{
+    uint32_t v;
+    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(a));
+    return v;
+}
+
+__device__ __forceinline__ float lds_f32(uint32_t a)
+{
+    float v;
+    asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(a));
+    return v;
 }
 
 __device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
@@ -551,6 +569,7 @@ struct OrderMap {
     uint32_t n_f;
     uint32_t n_t;
     int shift;         // control bins >> shift form the key
+    int bbits;         // bits of each key coordinate (pinned templates)
     int tshift;        // general templates: control times >> tshift (tbits bits each)
     int tbits;
     int fbits;         // key bits below the coarse bucket

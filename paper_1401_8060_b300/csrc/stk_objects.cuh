@@ -42,6 +42,7 @@ struct stk_ctx {
     ScorePlan plan{};
     bool profiling = false;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};  // start, scoring done, selection done, order done
+    cudaEvent_t stream_mark = nullptr;  // stk_score_noalloc: marks the context stream's work for other streams
     bool timed = false;
     int last_launches = 0;
     std::string err;

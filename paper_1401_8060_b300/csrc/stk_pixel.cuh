@@ -14,90 +14,62 @@ template <int PREC>
 struct Pix;
 
 template <>
-struct Pix<PREC_FP32> {  // {float |z|, Q0.32 arg z}; the weight array holds w = sigma^-2
+struct Pix<PREC_FP32> {  // {FP32 |z|, FP32 arg z in radians}; the weight array holds w = sigma^-2
     using Rec = uint2;
     __device__ static __forceinline__ float mag(Rec v) { return __uint_as_float(v.x); }
-    __device__ static __forceinline__ uint32_t arg(Rec v) { return v.y; }
+    __device__ static __forceinline__ float arg_rad(Rec v) { return __uint_as_float(v.y); }
     __device__ static __forceinline__ Rec load_global(const void *p, size_t i) { return __ldg((const uint2 *)p + i); }
+    __device__ static __forceinline__ Rec load_shared(uint32_t a) { return lds_u64(a); }
+    static constexpr int kLog2Bytes = 3;
 };
 
 template <>
-struct Pix<PREC_FP16> {  // low half: FP16 |y|/sigma; high half: arg in Q0.16 turns; weights hold r = 1/sigma
+struct Pix<PREC_FP16> {  // low half: arg in Q0.16 turns; high half: FP16 |y|/sigma; weights hold r = 1/sigma
     using Rec = uint32_t;
     __device__ static __forceinline__ float mag(Rec v)
     {
-        return __half2float(__ushort_as_half((unsigned short)(v & 0xffffu)));
+        __half2 h;
+        memcpy(&h, &v, sizeof h);
+        return __high2float(h);
     }
-    __device__ static __forceinline__ uint32_t arg(Rec v) { return v & 0xffff0000u; }
+    __device__ static __forceinline__ float arg_rad(Rec v) { return (float)(int32_t)(v << 16) * kTurnToRad; }
     __device__ static __forceinline__ Rec load_global(const void *p, size_t i)
     {
         return __ldg((const unsigned int *)p + i);
     }
+    __device__ static __forceinline__ Rec load_shared(uint32_t a) { return lds_u32(a); }
+    static constexpr int kLog2Bytes = 2;
 };
 
-// One pixel of Eq. 7: acc += |z| cos(theta + 2 pi arg z), W += weight.
-// FP32 records carry |z| and wv = sigma^-2; FP16 records carry |y|/sigma and
-// wv = 1/sigma, so |z| = mag wv and the weight is wv^2.
+// One pixel of Eq. 7 given the template's phase turn T at the pixel's bin:
+// acc += |z| cos(2 pi T + arg z), W += weight.  FP32 records: the angle is one
+// fused multiply-add of the converted turn and the stored FP32 angle (|angle| <
+// 2 pi), |z| and w = sigma^-2 as stored.  FP16 records: the Q0.16 angle joins
+// the turn in integer arithmetic (exact mod 1 turn); the record holds |y|/sigma
+// and wv = 1/sigma, so |z| = mag wv and the weight is wv^2.
 template <int PREC, int WMODE>
-__device__ __forceinline__ void accumulate_turn(typename Pix<PREC>::Rec v, uint32_t turn, float wv, float &acc,
-                                                float &W)
+__device__ __forceinline__ void pixel_add(typename Pix<PREC>::Rec v, uint32_t T, float wv, float &acc, float &W)
 {
-    const float c = cos_turn(turn);
-    float mg = Pix<PREC>::mag(v);
-    if (PREC == PREC_FP16 && WMODE != WMODE_CONST) mg *= wv;
-    acc = fmaf(mg, c, acc);
-    if (WMODE != WMODE_CONST) W = (PREC == PREC_FP16) ? fmaf(wv, wv, W) : W + wv;
-}
-
-// Packed pairs of FP32 operations (Blackwell .f32x2): each lane rounds to
-// nearest exactly as the scalar operation does, two results per instruction.
-__device__ __forceinline__ void fma2(float &d0, float &d1, float a0, float a1, float b0, float b1)
-{
-    asm("{ .reg .b64 ra, rb, rc; mov.b64 ra, {%2, %3}; mov.b64 rb, {%4, %5}; mov.b64 rc, {%0, %1};"
-        " fma.rn.f32x2 rc, ra, rb, rc; mov.b64 {%0, %1}, rc; }"
-        : "+f"(d0), "+f"(d1)
-        : "f"(a0), "f"(a1), "f"(b0), "f"(b1));
-}
-
-__device__ __forceinline__ void add2(float &d0, float &d1, float a0, float a1)
-{
-    asm("{ .reg .b64 ra, rc; mov.b64 ra, {%2, %3}; mov.b64 rc, {%0, %1};"
-        " add.rn.f32x2 rc, rc, ra; mov.b64 {%0, %1}, rc; }"
-        : "+f"(d0), "+f"(d1)
-        : "f"(a0), "f"(a1));
-}
-
-__device__ __forceinline__ void mul2(float &d0, float &d1, float a0, float a1)
-{
-    asm("{ .reg .b64 ra, rc; mov.b64 ra, {%2, %3}; mov.b64 rc, {%0, %1};"
-        " mul.rn.f32x2 rc, rc, ra; mov.b64 {%0, %1}, rc; }"
-        : "+f"(d0), "+f"(d1)
-        : "f"(a0), "f"(a1));
-}
-
-// accumulate_turn for two templates' pixels at once, bit for bit the same.
-template <int PREC, int WMODE>
-__device__ __forceinline__ void accumulate_turn2(typename Pix<PREC>::Rec v0, typename Pix<PREC>::Rec v1,
-                                                 uint32_t t0, uint32_t t1, float w0, float w1, float &acc0,
-                                                 float &acc1, float &W0, float &W1)
-{
-    float x0 = (float)(int32_t)t0, x1 = (float)(int32_t)t1;
-    mul2(x0, x1, kTurnToRad, kTurnToRad);
-    const float c0 = __cosf(x0), c1 = __cosf(x1);
-    float m0 = Pix<PREC>::mag(v0), m1 = Pix<PREC>::mag(v1);
-    if (PREC == PREC_FP16 && WMODE != WMODE_CONST) mul2(m0, m1, w0, w1);
-    fma2(acc0, acc1, m0, m1, c0, c1);
-    if (WMODE != WMODE_CONST) {
-        if (PREC == PREC_FP16) fma2(W0, W1, w0, w1, w0, w1);
-        else add2(W0, W1, w0, w1);
+    if constexpr (PREC == PREC_FP32) {
+        const float x = fmaf((float)(int32_t)T, kTurnToRad, Pix<PREC_FP32>::arg_rad(v));
+        acc = fmaf(Pix<PREC_FP32>::mag(v), __cosf(x), acc);
+        if (WMODE != WMODE_CONST) W += wv;
+    } else {
+        const uint32_t t = T + ((uint32_t)v << 16);
+        const float c = __cosf((float)(int32_t)t * kTurnToRad);
+        float mg = Pix<PREC_FP16>::mag(v);
+        if (WMODE != WMODE_CONST) mg *= wv;
+        acc = fmaf(mg, c, acc);
+        if (WMODE != WMODE_CONST) W = fmaf(wv, wv, W);
     }
 }
 
+// The same pixel for a template phase given in full (64-bit increment for wide maps).
 template <int PREC, int WMODE>
 __device__ __forceinline__ void accumulate(typename Pix<PREC>::Rec v, uint32_t bin, const Phase &ph, float wv,
                                            float &acc, float &W)
 {
-    accumulate_turn<PREC, WMODE>(v, pixel_turn(bin, ph, Pix<PREC>::arg(v)), wv, acc, W);
+    pixel_add<PREC, WMODE>(v, template_turn(bin, ph), wv, acc, W);
 }
 
 // Normalisation (Eq. 7 with the weighting of the footnote to Eq. 5) in FP32.

@@ -44,7 +44,7 @@ __device__ __forceinline__ void pixel_at(const MapDev &m, int j, int k, float &z
         mag *= wv;
         wv *= wv;
     }
-    const float ang = (float)(int32_t)Pix<PREC>::arg(v) * 1.4629180792671596e-09f;  // 2 pi / 2^32
+    const float ang = Pix<PREC>::arg_rad(v);
     float s, c;
     __sincosf(ang, &s, &c);
     zr = mag * c;

@@ -317,6 +317,11 @@ __global__ void __launch_bounds__(staged_max_threads(R, WMODE), 1)
 
     const uint32_t magic = m.magic;
     const int shift = m.shift;
+    const uint32_t srec_a = smem_u32(srec), sw_a = smem_u32(sw), swt_a = smem_u32(swt);
+    const uint32_t row_bytes = (uint32_t)m.ldr * (uint32_t)sizeof(Rec);
+    const uint32_t wrow_bytes = WMODE == WMODE_PIXEL ? (uint32_t)m.ldw * 4u : 0u;
+    const uint32_t slab_bytes = a.slab_recs * (uint32_t)sizeof(Rec);
+    const uint32_t wslab_bytes = WMODE == WMODE_PIXEL ? a.slab_ws * 4u : 0u;
     uint64_t q = 0;      // slab sequence number
     int slot = 0;        // q % nstage
     uint32_t parity = 0; // (q / nstage) & 1
@@ -355,40 +360,39 @@ __global__ void __launch_bounds__(staged_max_threads(R, WMODE), 1)
                 break;
             }
             const int rows = min(a.S, m.n_t - s * a.S);
-            const Rec *row = srec + (size_t)slot * a.slab_recs;
-            const float *wrow = sw + (size_t)slot * a.slab_ws;
-#pragma unroll 2
-            for (int jj = 0; jj < rows; ++jj) {
+            uint32_t rb = srec_a + (uint32_t)slot * slab_bytes;  // shared address of the slab's current row
+            uint32_t wb = sw_a + (uint32_t)slot * wslab_bytes;   // its weight row (WMODE_PIXEL)
+            // One pixel of template r at rasteriser value Nv (row base rb_, weight row wb_).
+            auto col = [&](int r, uint32_t Nv, uint32_t rb_, uint32_t wb_) {
+                const uint32_t b = __umulhi(Nv, magic) >> shift;
+                const Rec v = Pix<PREC>::load_shared(rb_ + (b << Pix<PREC>::kLog2Bytes));
+                float wv = 0.f;
+                if (WMODE == WMODE_FREQ) wv = lds_f32(swt_a + (b << 2));
+                if (WMODE == WMODE_PIXEL) wv = lds_f32(wb_ + (b << 2));
+                pixel_add<PREC, WMODE>(v, template_turn_narrow(b, pa[r], pc[r]), wv, acc[r], W[r]);
+            };
+            // Columns in pairs: N_{j+1} = N_j + D_j and N_{j+2} = N_{j+1} + D_j + D2,
+            // D_{j+2} = D_j + 2 D2 (three additions per two columns, exact mod 2^32).
+            int jj = 0;
+            for (; jj + 1 < rows; jj += 2) {
 #pragma unroll
-                for (int r = 0; r + 1 < R; r += 2) {  // templates in pairs: packed FP32 arithmetic
-                    const uint32_t b0 = __umulhi(N[r], magic) >> shift;
-                    const uint32_t b1 = __umulhi(N[r + 1], magic) >> shift;
-                    const Rec v0 = row[b0], v1 = row[b1];
-                    float w0 = 0.f, w1 = 0.f;
-                    if (WMODE == WMODE_FREQ) { w0 = swt[b0]; w1 = swt[b1]; }
-                    if (WMODE == WMODE_PIXEL) { w0 = wrow[b0]; w1 = wrow[b1]; }
-                    accumulate_turn2<PREC, WMODE>(v0, v1, pixel_turn_narrow(b0, pa[r], pc[r], Pix<PREC>::arg(v0)),
-                                                  pixel_turn_narrow(b1, pa[r + 1], pc[r + 1], Pix<PREC>::arg(v1)),
-                                                  w0, w1, acc[r], acc[r + 1], W[r], W[r + 1]);
-                    N[r] += D[r];
-                    D[r] += D2[r];
-                    N[r + 1] += D[r + 1];
-                    D[r + 1] += D2[r + 1];
+                for (int r = 0; r < R; ++r) {
+                    const uint32_t Na = N[r], Nb = Na + D[r];
+                    col(r, Na, rb, wb);
+                    col(r, Nb, rb + row_bytes, wb + wrow_bytes);
+                    N[r] = Nb + D[r] + D2[r];
+                    D[r] = D[r] + D2[r] + D2[r];
                 }
-                if (R & 1) {
-                    constexpr int r = R - 1;
-                    const uint32_t bin = __umulhi(N[r], magic) >> shift;
-                    const Rec v = row[bin];
-                    float wv = 0.f;
-                    if (WMODE == WMODE_FREQ) wv = swt[bin];
-                    if (WMODE == WMODE_PIXEL) wv = wrow[bin];
-                    accumulate_turn<PREC, WMODE>(v, pixel_turn_narrow(bin, pa[r], pc[r], Pix<PREC>::arg(v)), wv,
-                                                 acc[r], W[r]);
+                rb += 2 * row_bytes;
+                wb += 2 * wrow_bytes;
+            }
+            if (jj < rows) {
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    col(r, N[r], rb, wb);
                     N[r] += D[r];
                     D[r] += D2[r];
                 }
-                row += m.ldr;
-                if (WMODE == WMODE_PIXEL) wrow += m.ldw;
             }
             // This warp is done with the buffer; the last warp to finish refills it.
             __syncwarp();

@@ -220,6 +220,38 @@ def test_phase_forms_at_the_narrow_limit(ctx, n_f):
     assert_snr_close(a[:300], o, ex, False, n_t, what=f"generated n_f={n_f}")
 
 
+@pytest.mark.parametrize("fp16", [False, True])
+def test_angles_beyond_pi(ctx, fp16):
+    """A pixel's angle is the template's phase 2 pi T (|T| < 1/2 turn) plus the
+    stored angle of z (|arg z| <= pi), summed in FP32 before the cosine, so the
+    cosine sees |angle| up to 2 pi, outside the [-pi, pi] range of its documented
+    error bound.  Constant-frequency templates whose phase and pixel angles both
+    sit in the outer quarter turns put every angle in (pi, 2 pi) or (-2 pi, -pi);
+    the SNRs stay within the parity bound of the FP64 oracle (libm cos), and the
+    FP32 records well inside it."""
+    n_t, n_f, f_min, df = 64, 64, 40.0, 0.5
+    rng = np.random.default_rng(31)
+    sig = synth.sigma_powerlaw(f_min + df * np.arange(n_f), 1.1)
+    side = np.where(np.arange(n_f) < n_f // 2, 1.0, -1.0)          # sign of the angles per bin
+    phi = side * rng.uniform(np.pi / 2, np.pi, (n_t, n_f))
+    y = (sig * rng.rayleigh(1.0, (n_t, n_f)) * np.exp(1j * phi)).astype(np.complex64)
+    m = ctx.load_map(torch.from_numpy(y).cuda(), torch.from_numpy(sig).cuda(), f_min, df, fp16=fp16)
+    om = oracle.OracleMap(y, sig, f_min, df, True)
+    n = 2000
+    b = rng.integers(0, n_f, n).astype(np.uint32)
+    f3 = np.repeat(b[:, None], 3, axis=1)
+    turns = side[b] * rng.uniform(0.25, 0.5, n)                     # the template's phase at its bin
+    tau = turns / (f_min + df * b.astype(np.float64))
+    got = ctx.score_explicit(m, torch.from_numpy(f3.astype(np.int32)), torch.from_numpy(tau)).cpu().numpy()
+    o, ex = om.score_explicit(f3, tau, extras=True)
+    rtol = 3.5e-4 if fp16 else RTOL
+    assert_snr_close(got, o, ex, False, n_t, rtol=rtol, what="angles beyond pi")
+    if not fp16:
+        err = np.max(np.abs(got - o) / (ex["absz"] / np.sqrt(ex["W"])))
+        assert err <= 3e-6, err
+    m.close()
+
+
 @pytest.mark.parametrize("threads,max_r,stages", [(64, 1, 2), (96, 3, 3), (1024, 4, 4), (512, 2, 2), (992, 5, 2),
                                                   (512, 11, 2), (448, 12, 3), (160, 7, 4), (480, 6, 2)])
 def test_launch_shapes_agree(ctx, threads, max_r, stages):
