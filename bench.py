@@ -214,10 +214,16 @@ def profiled_traffic():
     return int(kv["dram_bytes_per_launch"]), kv.get("kernel_source_hash")
 
 
-def cpu_baseline(fm, w, chunk, seconds=10.0):
+def cpu_baseline(fm, w, chunk, seconds=10.0, check=None):
     """The FP64 oracle, as it stands, on a bounded sample of the same workload:
     consecutive chunks of templates from index 0 until about `seconds` of
-    wall time have passed (or the workload is exhausted)."""
+    wall time have passed (or the workload is exhausted).
+
+    check: optional {"n": n, "hits": {name: hits}}; after the timed part (not in
+    the rate), the oracle also scores templates 0 .. n - 1 with each one's
+    comparison scale sum_j |z_j| / sqrt(W), and the templates of each hit list,
+    so the GPU's SNRs can be stated against it.  Returns (baseline, oracle SNRs
+    or None)."""
     import oracle
     om = oracle.OracleMap.from_ftmap(fm)
     cores = os.cpu_count() or 1
@@ -229,10 +235,36 @@ def cpu_baseline(fm, w, chunk, seconds=10.0):
         done += n
     dt = time.perf_counter() - t0
     px = done * fm.n_t
-    return {"value": px / dt, "unit": "track-pixels/s", "tracks_per_s": done / dt, "cores": cores,
+    base = {"value": px / dt, "unit": "track-pixels/s", "tracks_per_s": done / dt, "cores": cores,
             "kind": "oracle", "seconds": dt,
             "sample": f"templates 0..{done - 1} of the {w['n_tracks']}-template realistic workload "
                       f"({px:.3g} track-pixels; chunks of {chunk} until ~{seconds:g} s), FP64, all host threads"}
+    if not check:
+        return base, None
+    snr, sc = om.score_range_scale(w["seed"], 0, check["n"], w["tau_max"], nthreads=cores)
+    top = {name: om.score_explicit(np.array([list(v) for v in h["f"]], np.uint32), h["tau"])
+           for name, h in check["hits"].items()}
+    return base, {"snr": snr, "scale": sc, "top": top}
+
+
+def oracle_errors(gpu_sample, hits, orc, name):
+    """SNR error of the GPU against the FP64 oracle: over the sample, |dSNR| in units
+    of the template's scale sum_j |z_j| / sqrt(W) (the parity bound is 1e-5 of it);
+    over the k hits, plain relative error."""
+    d = np.abs(np.asarray(gpu_sample, np.float64) - orc["snr"]) / orc["scale"]
+    t = np.abs(hits["snr"] - orc["top"][name]) / np.abs(orc["top"][name])
+    return {"sample_templates": int(d.size), "sample_max_over_scale": float(d.max()),
+            "sample_rms_over_scale": float(np.sqrt(np.mean(d * d))),
+            "topk_max_rel": float(t.max()), "topk_rms_rel": float(np.sqrt(np.mean(t * t))),
+            "scale": "sum_j |z_j| / sqrt(W) per template; top-k: |SNR_gpu - SNR_oracle| / |SNR_oracle|"}
+
+
+def data_path_roofline(bytes_per_unit, units, ms, peak, kernel, note):
+    """Algorithmic bytes over the shared-memory / L1 data path (128 B/clk/SM)."""
+    achieved = bytes_per_unit * units / (ms / 1e3) / 1e9
+    return {"bound": "smem", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": None, "kernel": kernel, "kernel_ms": ms, "bytes_per_unit": bytes_per_unit, "units": units,
+            "note": note}
 
 
 WORKLOAD_TEXT = ("realistic 500x1600 map (0.5 Hz bins from 40 Hz), per-frequency power-law sigma, "
@@ -354,6 +386,14 @@ def main():
     hits = out.cpu().numpy().view(stk.HIT_DTYPE)
     plan = ctx.last_plan()
 
+    props = torch.cuda.get_device_properties(local)
+    n_sm = props.multi_processor_count
+    clocks = clk.summary()
+    sm_mhz = clocks["sm_mhz"] or 2032.0
+    peak = SMEM_BYTES_PER_CLK_PER_SM * n_sm * sm_mhz * 1e6 / 1e9
+    ACC_N = 100_000                          # templates whose SNRs are checked against the oracle
+    acc_gpu = {}
+
     # the same workload scored in template-index order (no coherent-order pre-pass)
     variants = {}
     if not args.no_variants:
@@ -377,7 +417,9 @@ def main():
         variants["index_order"] = {
             "ms_per_step": msi, "kernel_ms": sum(ki) / len(ki), "speedup_of_coherent_order": msi / ms,
             "topk_identical": bool(np.array_equal(hi["index"], hits["index"]) and
-                                   np.array_equal(hi["snr"], hits["snr"]))}
+                                   np.array_equal(hi["snr"], hits["snr"])),
+            "roofline": data_path_roofline(BYTES_PER_TRACK_PIXEL, T * fm.n_t, sum(ki) / len(ki), peak,
+                                           "score_staged_kernel", "8 B per track-pixel, template-index order")}
 
     # FP16 pixel storage on the same workload (4-byte records), same timing rules
     if not args.no_variants:
@@ -409,7 +451,17 @@ def main():
             "kernel_ms": sum(k16) / len(k16), "speedup_vs_fp32": ms / ms16,
             "topk_overlap_with_fp32": len(common) / K,
             "max_rel_snr_diff_vs_fp32_on_common_topk": max(rel) if rel else None,
-            "storage": "4 B/pixel: FP16 |y|/sigma (per-frequency scaling) + Q0.16 phase; FP32 sums"}
+            "storage": "4 B/pixel: FP16 |y|/sigma (per-frequency scaling) + Q0.16 phase; FP32 sums",
+            "roofline": data_path_roofline(4, T * fm.n_t, sum(k16) / len(k16), peak, "score_staged_kernel",
+                                           "4 B per track-pixel (the FP16 record)")}
+        # SNRs of templates 0 .. ACC_N - 1 in both precisions (checked against the oracle below)
+        ctx.set_profiling(False)
+        ctx.set_tracks(ACC_N, w["seed"], 0, w["tau_max"])
+        acc_gpu["fp32"] = ctx.score_all(m).cpu().numpy()
+        acc_gpu["fp16"] = ctx.score_all(m16).cpu().numpy()
+        acc_gpu["hits16"] = h16
+        ctx.set_tracks(T, w["seed"], offset, w["tau_max"])
+        ctx.set_profiling(True)
         m16.close()
 
     # general templates (random start / middle / end times, duration >= 25 columns = 100 s)
@@ -437,7 +489,10 @@ def main():
             "value": pxg / (msg / 1e3), "unit": "track-pixels/s (expected pixels)", "ms_per_step": msg,
             "kernel_ms": sum(kg) / len(kg), "templates": Tg, "t_min_columns": tmin_g,
             "rasteriser": "FP32 estimate of the curve's frequency, exact integer test within a proven error "
-                          "margin of a rounding boundary; one thread per template, L2 gathers"}
+                          "margin of a rounding boundary; one thread per template, L2 gathers",
+            "roofline": data_path_roofline(BYTES_PER_TRACK_PIXEL, pxg, sum(kg) / len(kg), peak,
+                                           "score_general_kernel", "8 B per expected track-pixel; the gathers "
+                                           "come from L2 through the L1 data path")}
         ctx.set_template_shape(False)
         ctx.set_tracks(T, w["seed"], offset, w["tau_max"])
 
@@ -461,7 +516,10 @@ def main():
             "discrete_snr_mean_before": float(np.mean(hits["snr"])),
             "discrete_snr_mean_after_rounding": float(np.mean(d_after)),
             "kernels": "stk_refine: per step one launch computes the interpolated SNR, its gradient and the Adam "
-                       "step (32-128 threads per template, chosen by count; position and phase in fixed point)"}
+                       "step (32-128 threads per template, chosen by count; position and phase in fixed point)",
+            "roofline": data_path_roofline(16, float(K) * fm.n_t * 50, r0.elapsed_time(r1), peak, "interp_kernel",
+                                           "16 B per template-column per step (the two FP32 records that "
+                                           "interpolation reads); gathers from L2 through the L1 data path")}
         ctx.set_profiling(True)
 
     # 256 ragged maps in one persistent launch vs 256 sequential single-map launches
@@ -515,7 +573,10 @@ def main():
             "loudest_snr_injected_maps_median": float(np.median(hb[inj, 0]["snr"])) if inj else None,
             "loudest_snr_noise_maps_median": float(np.median(np.delete(hb[:, 0]["snr"], inj))),
             "config": "n_t ~ U{100..1000}, n_f ~ U{200..2000}, 0.5 Hz from 40 Hz, sigma0 ~ U(0.5, 2), "
-                      "10% injected (SNR 10-30)"}
+                      "10% injected (SNR 10-30)",
+            "roofline": data_path_roofline(BYTES_PER_TRACK_PIXEL, pxb, msb, peak, "score_batch_kernel",
+                                           "8 B per track-pixel; time of the whole graph (order pass, "
+                                           "persistent scoring kernel, merge)")}
         batch.close()
         # the same maps with little work per map (2e4 templates): launch overheads and
         # per-map fill dominate the sequential calls; one batched launch avoids them
@@ -639,15 +700,10 @@ def main():
             hits = search.merge_hits([np.frombuffer(b, dtype=stk.HIT_DTYPE) for b in gathered], K)
 
     if rank == 0:
-        clocks = clk.summary()
         px = world * T * fm.n_t
         value = px / (ms / 1e3)
         score_avg = sum(score_ms) / len(score_ms)
         achieved = T * fm.n_t * BYTES_PER_TRACK_PIXEL / (score_avg / 1e3) / 1e9
-        props = torch.cuda.get_device_properties(local)
-        n_sm = props.multi_processor_count
-        sm_mhz = clocks["sm_mhz"] or 2032.0
-        peak = SMEM_BYTES_PER_CLK_PER_SM * n_sm * sm_mhz * 1e6 / 1e9
         traffic, src_hash = profiled_traffic()
         line = {
             "metric": METRIC, "value": value, "unit": "track-pixels/s",
@@ -680,7 +736,13 @@ def main():
         if variants:
             line["variants"] = variants
         if world == 1 and not args.no_cpu_baseline:
-            line["cpu_baseline"] = cpu_baseline(fm, w, args.cpu_sample)
+            check = None
+            if "fp32" in acc_gpu:
+                check = {"n": ACC_N, "hits": {"fp32": hits, "fp16": acc_gpu["hits16"]}}
+            line["cpu_baseline"], orc = cpu_baseline(fm, w, args.cpu_sample, check=check)
+            if orc is not None:
+                line["accuracy_vs_oracle"] = oracle_errors(acc_gpu["fp32"], hits, orc, "fp32")
+                variants["fp16"]["err_vs_oracle"] = oracle_errors(acc_gpu["fp16"], acc_gpu["hits16"], orc, "fp16")
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
