@@ -46,6 +46,8 @@ extern "C" {
 #define STK_ECUDA    -3  /* a CUDA runtime call failed (message names it) */
 #define STK_ETIMEOUT -4  /* a bounded in-kernel wait gave up; results of that call are invalid */
 #define STK_ESTATE   -5  /* call out of order, e.g. scoring before stk_set_tracks */
+#define STK_EBOUNDS  -7  /* debug build (libstk_debug.so) only: a pixel gather outside its template's
+                            bins or the map, or a damaged canary word after a buffer */
 
 /* ---- stk_load_map flags ---------------------------------------------- */
 #define STK_HOST_PTR       0x1u /* y and sigma are host pointers (pageable or pinned) */
@@ -74,6 +76,14 @@ typedef struct {
 
 /* Library version, 10000*major + 100*minor + patch. */
 STK_API int stk_version(void);
+
+/* Build flags of the loaded library: bit 0 set in the debug build (libstk_debug.so,
+ * compiled with STK_DEBUG_BOUNDS): every pixel gather checks its column and bin
+ * against the template's convex hull of control bins within the map and reports
+ * STK_EBOUNDS at the next deferred-error check instead of reading out of range;
+ * the packed map and the context's scratch carry trailing canary words, checked
+ * (synchronising) after every scoring, refinement and batch call.  0 otherwise. */
+STK_API int stk_build_flags(void);
 
 /* Create a context on CUDA device `device`, issuing work on `cuda_stream`
  * (a cudaStream_t; NULL = the legacy default stream).  *out receives the
@@ -254,6 +264,31 @@ STK_API int stk_interp_adjoint(stk_ctx *ctx, const stk_map *map, const float *f3
  * non-finite rates), STK_ENOMEM, STK_ECUDA. */
 STK_API int stk_refine(stk_ctx *ctx, const stk_map *map, float *f3_dev, float *tau_dev, uint64_t n, int steps,
                        float lr_bins, float lr_tau_frac, float tau_max, float *hist_dev);
+
+/* Discrete follow-up of the loudest templates (Sec. V): the refined templates
+ * are judged by the discrete statistic of Eq. 7, so this call climbs it directly.
+ * For each of n templates, one warp: the delay moves to the nearest maximum of
+ * SNR(tau) at the template's fixed pixels (the weight sum does not depend on
+ * tau and S(tau) is smooth: safeguarded Newton steps, each at most a tenth of
+ * the band's shortest period and kept only when the SNR rises), then each
+ * control bin moves by +-1 while a move, with its delay maximised again, raises
+ * the SNR, at most `moves` moves.  With alt_f3_dev / alt_tau_dev (continuous
+ * templates, e.g. stk_refine's output; rounded to the nearest bins and clamped)
+ * the alternative is climbed too.  The template kept is the start, the polished
+ * start or the polished alternative, whichever scores highest by the scorer's
+ * own arithmetic (the SNR stk_score_explicit returns; the start wins ties), so
+ * no template leaves with a lower SNR than it came with.
+ *   f3_dev     uint32 [n][3] control bins, tau_dev double [n] delays (s):
+ *              device memory, caller-owned, updated in place
+ *   tau_max    delays stay within [-tau_max, tau_max]
+ *   snr_dev    double [n] (optional): the kept template's SNR
+ *   which_dev  int [n] (optional): 0 start, 1 polished start, 2 polished alternative
+ * Asynchronous on the context's stream; no allocation.  Errors: STK_EINVAL (NULL
+ * pointer, tau_max <= 0, moves outside [0, 1024], only one of the alternatives),
+ * STK_ECUDA. */
+STK_API int stk_polish(stk_ctx *ctx, const stk_map *map, uint32_t *f3_dev, double *tau_dev, const float *alt_f3_dev,
+                       const float *alt_tau_dev, uint64_t n, double tau_max, int moves, double *snr_dev,
+                       int *which_dev);
 
 /* Wait for the context's stream and report the first deferred error raised
  * by a kernel since the last stk_sync (bounded-wait timeout, bad explicit

@@ -293,6 +293,34 @@ class Context:
                                      C.c_void_p(h.data_ptr() if h is not None else 0)))
         return f, t, h
 
+    def polish(self, m: Map, f3, tau, tau_max: float, alt_f3=None, alt_tau=None, moves: int = 8):
+        """stk_polish: discrete follow-up of templates f3 (int [n][3] bins) and tau
+        (float64 [n] s), with optional continuous alternatives alt_f3 (float32 [n][3])
+        and alt_tau (float32 [n]).  Returns (f3 uint32-valued int64 tensor, tau float64,
+        snr float64, which int32), all on the device."""
+        torch = self._torch
+        self._bind_stream()
+        f = torch.as_tensor(f3, device="cuda").to(torch.int32).contiguous().clone()   # same bits as uint32
+        t = torch.as_tensor(tau, device="cuda").to(torch.float64).contiguous().clone()
+        n = t.numel()
+        if f.shape != (n, 3):
+            raise ValueError("f3 must be [n][3]")
+        a_f = a_t = None
+        if (alt_f3 is None) != (alt_tau is None):
+            raise ValueError("alt_f3 and alt_tau go together")
+        if alt_f3 is not None:
+            a_f = torch.as_tensor(alt_f3, device="cuda").to(torch.float32).contiguous()
+            a_t = torch.as_tensor(alt_tau, device="cuda").to(torch.float32).contiguous()
+            if a_f.shape != (n, 3) or a_t.numel() != n:
+                raise ValueError("alternatives must match f3 and tau")
+        snr = torch.empty(n, dtype=torch.float64, device="cuda")
+        which = torch.empty(n, dtype=torch.int32, device="cuda")
+        self._check(lib().stk_polish(self._h, m.handle, C.c_void_p(f.data_ptr()), C.c_void_p(t.data_ptr()),
+                                     C.c_void_p(a_f.data_ptr() if a_f is not None else 0),
+                                     C.c_void_p(a_t.data_ptr() if a_t is not None else 0), n, float(tau_max),
+                                     int(moves), C.c_void_p(snr.data_ptr()), C.c_void_p(which.data_ptr())))
+        return f.to(torch.int64), t, snr, which
+
     def sync(self):
         """stk_sync: wait and raise the first deferred kernel error."""
         self._check(lib().stk_sync(self._h))

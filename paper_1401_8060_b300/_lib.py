@@ -11,9 +11,12 @@ import os
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libstk.so")
+# STK_LIBRARY selects another build of the same ABI (the bounds-checked
+# libstk_debug.so); by default the release library beside this file.
+LIB_PATH = os.environ.get("STK_LIBRARY") or os.path.join(HERE, "libstk.so")
 
 STK_OK, STK_EINVAL, STK_ENOMEM, STK_ECUDA, STK_ETIMEOUT, STK_ESTATE, STK_ECANCELED = 0, -1, -2, -3, -4, -5, -6
+STK_EBOUNDS = -7
 STK_BATCH_MAX_K = 32
 STK_HOST_PTR, STK_SIGMA_PER_FREQ, STK_NORM_PAPER, STK_FP16 = 0x1, 0x2, 0x4, 0x8
 STK_OUT_HOST = 0x1
@@ -27,6 +30,7 @@ STK_OPT_INTERP_THREADS = 10
 _vp = C.c_void_p
 SIGNATURES = [
     ("stk_version", C.c_int, []),
+    ("stk_build_flags", C.c_int, []),
     ("stk_create", C.c_int, [C.POINTER(_vp), C.c_int, _vp]),
     ("stk_destroy", None, [_vp]),
     ("stk_set_stream", C.c_int, [_vp, _vp]),
@@ -53,6 +57,7 @@ SIGNATURES = [
     ("stk_interp_forward", C.c_int, [_vp, _vp, _vp, _vp, C.c_uint64, _vp]),
     ("stk_interp_adjoint", C.c_int, [_vp, _vp, _vp, _vp, _vp, C.c_uint64, _vp, _vp]),
     ("stk_refine", C.c_int, [_vp, _vp, _vp, _vp, C.c_uint64, C.c_int, C.c_float, C.c_float, C.c_float, _vp]),
+    ("stk_polish", C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, C.c_uint64, C.c_double, C.c_int, _vp, _vp]),
     ("stk_batch_create", C.c_int, [_vp, _vp, C.c_int, _vp, _vp, _vp, C.c_double, C.POINTER(_vp)]),
     ("stk_batch_destroy", None, [_vp]),
     ("stk_batch_score", C.c_int, [_vp, C.c_int, _vp, C.c_uint]),

@@ -42,6 +42,8 @@ int read_err_flags(stk_ctx *c, int *flags)
 
 int flags_to_status(stk_ctx *c, int f)
 {
+    if (f & ERR_BOUNDS)
+        return set_err(c, STK_EBOUNDS, "debug build: a pixel gather outside its template's bins or the map");
     if (f & ERR_TIMEOUT) return set_err(c, STK_ETIMEOUT, "a bounded in-kernel wait for a map slab gave up");
     if (f & ERR_CANCELED) return set_err(c, STK_ECANCELED, "batch cancelled through stk_batch_cancel");
     if (f & ERR_BADTRACK) return set_err(c, STK_EINVAL, "explicit template with a control bin outside [0, n_f)");
@@ -145,6 +147,18 @@ bool find_magic(uint64_t d, uint64_t n_max, uint32_t &magic, int &shift)
     return false;
 }
 
+// Debug build: every buffer the library allocates ends in kCanaryBytes of
+// kCanaryByte, checked after each call (debug_verify); a write past a buffer's
+// end changes them.  Release build: no canaries.
+constexpr size_t kCanaryBytes = kDebugBounds ? 256 : 0;
+constexpr unsigned char kCanaryByte = 0xA5;
+
+cudaError_t canary_set(void *buf, size_t at, cudaStream_t st)
+{
+    return kCanaryBytes ? cudaMemsetAsync(static_cast<char *>(buf) + at, kCanaryByte, kCanaryBytes, st)
+                        : cudaSuccess;
+}
+
 int ensure(stk_ctx *c, void **buf, size_t *cap, size_t need)
 {
     if (*cap >= need && *buf) return STK_OK;
@@ -154,14 +168,18 @@ int ensure(stk_ctx *c, void **buf, size_t *cap, size_t need)
         *buf = nullptr;
         *cap = 0;
     }
-    cudaError_t e = cudaMalloc(buf, need);
+    cudaError_t e = cudaMalloc(buf, need + kCanaryBytes);
     if (e != cudaSuccess) {
         *buf = nullptr;
         return set_err(c, STK_ENOMEM, "cudaMalloc(%zu bytes): %s", need, cudaGetErrorString(e));
     }
     *cap = need;
+    if ((e = canary_set(*buf, need, c->stream)) != cudaSuccess)
+        return set_err(c, STK_ECUDA, "canary: %s", cudaGetErrorString(e));
     return STK_OK;
 }
+
+
 
 int check_general(stk_ctx *c, const stk_map *m)
 {
@@ -183,9 +201,53 @@ int check_ready(stk_ctx *c, const stk_map *m)
 
 }  // namespace
 
+// Debug build, after a call: wait, then check every canary of the context (and
+// of map m) and the out-of-range gather flag.  Release build: nothing.
+int debug_verify(stk_ctx *c, const stk_map *m)
+{
+#ifndef STK_DEBUG_BOUNDS
+    (void)c;
+    (void)m;
+    return STK_OK;
+#else
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    struct Canary {
+        const void *buf;
+        size_t at;
+        const char *what;
+    };
+    const Canary cs[] = {{m ? m->rec_buf : nullptr, m ? m->rec_bytes : 0, "map records"},
+                         {m ? m->w_buf : nullptr, m ? m->w_bytes : 0, "map weights"},
+                         {c->snr_buf, c->snr_cap, "SNR scratch"},
+                         {c->sel_buf, c->sel_cap, "selection scratch"},
+                         {c->order_buf, c->order_cap, "order scratch"},
+                         {c->small_dev, c->small_cap, "parameter scratch"},
+                         {c->refine_buf, c->refine_cap, "refinement scratch"},
+                         {c->hits_dev, sizeof(stk_hit) * STK_MAX_K, "hit records"}};
+    unsigned char h[kCanaryBytes];
+    for (const Canary &k : cs) {
+        if (!k.buf) continue;
+        CUDA_TRY(c, cudaMemcpy(h, static_cast<const char *>(k.buf) + k.at, kCanaryBytes, cudaMemcpyDeviceToHost));
+        for (size_t i = 0; i < kCanaryBytes; ++i)
+            if (h[i] != kCanaryByte)
+                return set_err(c, STK_EBOUNDS, "debug build: canary after the %s damaged at byte %zu", k.what, i);
+    }
+    int fl = 0;
+    CUDA_TRY(c, cudaMemcpy(&fl, c->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (fl & ERR_BOUNDS) {
+        const int rest = fl & ~ERR_BOUNDS;   // other deferred errors stay for the next stk_sync
+        CUDA_TRY(c, cudaMemcpy(c->d_err, &rest, sizeof(int), cudaMemcpyHostToDevice));
+        return flags_to_status(c, ERR_BOUNDS);
+    }
+    return STK_OK;
+#endif
+}
+
 extern "C" {
 
 int stk_version(void) { return 100; }
+
+int stk_build_flags(void) { return kDebugBounds ? 1 : 0; }
 
 const char *stk_last_error(const stk_ctx *ctx) { return ctx ? ctx->err.c_str() : g_create_err.c_str(); }
 
@@ -208,7 +270,8 @@ int stk_create(stk_ctx **out, int device, void *cuda_stream)
     cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
     c->smem_optin = (size_t)v;
     if (cudaMalloc(&c->d_err, sizeof(int)) != cudaSuccess ||
-        cudaMalloc(&c->hits_dev, sizeof(stk_hit) * STK_MAX_K) != cudaSuccess) {
+        cudaMalloc(&c->hits_dev, sizeof(stk_hit) * STK_MAX_K + kCanaryBytes) != cudaSuccess ||
+        canary_set(c->hits_dev, sizeof(stk_hit) * STK_MAX_K, c->stream) != cudaSuccess) {
         cudaFree(c->d_err);
         delete c;
         return set_err(nullptr, STK_ENOMEM, "context allocation failed");
@@ -418,10 +481,20 @@ int stk_load_map(stk_ctx *c, const void *y_c64, const float *sigma, int n_t, int
     cudaError_t e;
     const size_t recbytes = (size_t)n_t * d.ldr * (fp16 ? 4 : 8);
     const size_t wbytes = per_freq ? (size_t)d.ldw * 4 : (size_t)n_t * d.ldw * 4;
-    if ((e = cudaMalloc(&m->rec_buf, recbytes)) != cudaSuccess || (e = cudaMalloc(&m->w_buf, wbytes)) != cudaSuccess) {
+    if ((e = cudaMalloc(&m->rec_buf, recbytes + kCanaryBytes)) != cudaSuccess ||
+        (e = cudaMalloc(&m->w_buf, wbytes + kCanaryBytes)) != cudaSuccess) {
         cudaFree(m->rec_buf);
         delete m;
         return set_err(c, STK_ENOMEM, "map allocation (%zu bytes): %s", recbytes + wbytes, cudaGetErrorString(e));
+    }
+    m->rec_bytes = recbytes;
+    m->w_bytes = wbytes;
+    if ((e = canary_set(m->rec_buf, recbytes, c->stream)) != cudaSuccess ||
+        (e = canary_set(m->w_buf, wbytes, c->stream)) != cudaSuccess) {
+        cudaFree(m->rec_buf);
+        cudaFree(m->w_buf);
+        delete m;
+        return set_err(c, STK_ECUDA, "canary: %s", cudaGetErrorString(e));
     }
     int rc = pack_into(c, m, y_c64, sigma, flags);
     if (rc) {
@@ -518,7 +591,7 @@ int stk_score_all(stk_ctx *c, const stk_map *m, double *out_snr_dev)
     c->timed = c->profiling;
     c->last_launches = 2 + (c->plan.order ? c->plan.order_launches : 0);
     if (c->profiling) CUDA_TRY(c, cudaEventRecord(c->ev[2], c->stream));
-    return STK_OK;
+    return debug_verify(c, m);
 }
 
 int stk_score(stk_ctx *c, const stk_map *m, int k, stk_hit *out, unsigned flags)
@@ -546,12 +619,13 @@ int stk_score(stk_ctx *c, const stk_map *m, int k, stk_hit *out, unsigned flags)
     if (c->profiling) CUDA_TRY(c, cudaEventRecord(c->ev[2], c->stream));
     if (flags & STK_OUT_HOST) {
         CUDA_TRY(c, cudaMemcpyAsync(out, c->hits_dev, sizeof(stk_hit) * (size_t)k, cudaMemcpyDeviceToHost, c->stream));
+        if ((rc = debug_verify(c, m)) != STK_OK) return rc;
         int fl = 0;
         rc = read_err_flags(c, &fl);
         if (rc) return rc;
         return flags_to_status(c, fl);
     }
-    return STK_OK;
+    return debug_verify(c, m);
 }
 
 int stk_track_params(stk_ctx *c, const stk_map *m, uint64_t g, uint32_t f[3], double *tau, int32_t *bins_host)
@@ -591,7 +665,7 @@ int stk_score_explicit(stk_ctx *c, const stk_map *m, const uint32_t *f3, const d
     cudaError_t e = launch_score_explicit(m->dev, f3, tau, n, c->snr_buf, c->d_err, c->stream);
     if (e == cudaSuccess) e = launch_widen(c->snr_buf, out, n, c->stream);
     if (e != cudaSuccess) return set_err(c, STK_ECUDA, "explicit scoring launch: %s", cudaGetErrorString(e));
-    return STK_OK;
+    return debug_verify(c, m);
 }
 
 int stk_set_template_shape(stk_ctx *c, int general, int t_min)
@@ -653,7 +727,7 @@ int stk_score_explicit_general(stk_ctx *c, const stk_map *m, const uint32_t *t3,
     cudaError_t e = launch_score_explicit_general(m->dev, t3, f3, tau, n, c->snr_buf, c->d_err, c->stream);
     if (e == cudaSuccess) e = launch_widen(c->snr_buf, out, n, c->stream);
     if (e != cudaSuccess) return set_err(c, STK_ECUDA, "explicit general scoring launch: %s", cudaGetErrorString(e));
-    return STK_OK;
+    return debug_verify(c, m);
 }
 
 int stk_interp_forward(stk_ctx *c, const stk_map *m, const float *f3, const float *tau, uint64_t n, float *snr)
@@ -663,10 +737,10 @@ int stk_interp_forward(stk_ctx *c, const stk_map *m, const float *f3, const floa
     if (n == 0) return STK_OK;
     if (!f3 || !tau || !snr) return set_err(c, STK_EINVAL, "NULL pointer");
     CUDA_TRY(c, cudaSetDevice(c->device));
-    cudaError_t e = launch_interp_tuned(m->dev, f3, tau, nullptr, n, snr, nullptr, nullptr, false, c->interp_threads,
+    cudaError_t e = launch_interp_tuned(m->dev, f3, tau, nullptr, n, snr, nullptr, nullptr, false, c->interp_threads, c->d_err,
                                         c->stream);
     if (e != cudaSuccess) return set_err(c, STK_ECUDA, "interpolated forward launch: %s", cudaGetErrorString(e));
-    return STK_OK;
+    return debug_verify(c, m);
 }
 
 int stk_interp_adjoint(stk_ctx *c, const stk_map *m, const float *f3, const float *tau, const float *g, uint64_t n,
@@ -677,10 +751,10 @@ int stk_interp_adjoint(stk_ctx *c, const stk_map *m, const float *f3, const floa
     if (n == 0) return STK_OK;
     if (!f3 || !tau || !g || !grad_f3 || !grad_tau) return set_err(c, STK_EINVAL, "NULL pointer");
     CUDA_TRY(c, cudaSetDevice(c->device));
-    cudaError_t e = launch_interp_tuned(m->dev, f3, tau, g, n, nullptr, grad_f3, grad_tau, true, c->interp_threads,
+    cudaError_t e = launch_interp_tuned(m->dev, f3, tau, g, n, nullptr, grad_f3, grad_tau, true, c->interp_threads, c->d_err,
                                         c->stream);
     if (e != cudaSuccess) return set_err(c, STK_ECUDA, "interpolated adjoint launch: %s", cudaGetErrorString(e));
-    return STK_OK;
+    return debug_verify(c, m);
 }
 
 int stk_refine(stk_ctx *c, const stk_map *m, float *f3, float *tau, uint64_t n, int steps, float lr_bins,
@@ -698,9 +772,26 @@ int stk_refine(stk_ctx *c, const stk_map *m, float *f3, float *tau, uint64_t n, 
     int rc = ensure(c, &c->refine_buf, &c->refine_cap, refine_scratch_bytes(n));
     if (rc) return rc;
     cudaError_t e = launch_refine(m->dev, f3, tau, n, steps, lr_bins, lr_tau_frac, tau_max, hist, c->refine_buf,
-                                  c->interp_threads, c->stream);
+                                  c->interp_threads, c->d_err, c->stream);
     if (e != cudaSuccess) return set_err(c, STK_ECUDA, "refinement launch: %s", cudaGetErrorString(e));
-    return STK_OK;
+    return debug_verify(c, m);
+}
+
+int stk_polish(stk_ctx *c, const stk_map *m, uint32_t *f3, double *tau, const float *alt_f3, const float *alt_tau,
+               uint64_t n, double tau_max, int moves, double *snr, int *which)
+{
+    if (!c) return STK_EINVAL;
+    if (!m || m->ctx != c) return set_err(c, STK_EINVAL, "map is NULL or belongs to another context");
+    if (!(tau_max > 0.0) || !std::isfinite(tau_max)) return set_err(c, STK_EINVAL, "tau_max must be > 0 and finite");
+    if (moves < 0 || moves > 1024) return set_err(c, STK_EINVAL, "moves = %d outside [0, 1024]", moves);
+    if ((alt_f3 == nullptr) != (alt_tau == nullptr)) return set_err(c, STK_EINVAL, "alt_f3 and alt_tau go together");
+    if (n == 0) return STK_OK;
+    if (!f3 || !tau) return set_err(c, STK_EINVAL, "NULL pointer");
+    CUDA_TRY(c, cudaSetDevice(c->device));
+    cudaError_t e = launch_polish(m->dev, f3, tau, alt_f3, alt_tau, n, tau_max, moves, snr, which, c->d_err,
+                                  c->stream);
+    if (e != cudaSuccess) return set_err(c, STK_ECUDA, "polish launch: %s", cudaGetErrorString(e));
+    return debug_verify(c, m);
 }
 
 int stk_sync(stk_ctx *c)

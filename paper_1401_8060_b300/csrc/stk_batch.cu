@@ -73,16 +73,19 @@ struct BatchArgs {
 // rb, wb: shared addresses of the slab's first record row and weight row, swt_a
 // of the per-frequency weight table.  Columns go in pairs (three rasteriser
 // additions per two columns, exact mod 2^32), each template's sums in column order.
+// Debug build: hull[r] = the template's bins (lo | hi << 16), j0 the slab's first
+// column, n_t the map's columns, err the flag word.
 template <int R, int WMODE, int PREC, bool FAST>
 __device__ __forceinline__ void batch_slab(uint32_t rb, uint32_t wb, uint32_t swt_a, int rows, uint32_t row_bytes,
                                            uint32_t wrow_bytes, uint32_t magic, int shift, uint32_t d32,
                                            uint32_t (&N)[R], uint32_t (&D)[R], const uint32_t (&D2)[R],
                                            const uint32_t (&pa)[R], const uint32_t (&pc)[R], float (&acc)[R],
-                                           float (&W)[R])
+                                           float (&W)[R], const uint32_t *hull, int j0, int n_t, int *err)
 {
     using Rec = typename Pix<PREC>::Rec;
-    auto col = [&](int r, uint32_t Nv, uint32_t rb_, uint32_t wb_) {
-        const uint32_t b = FAST ? __umulhi(Nv, magic) >> shift : div_corrected(Nv, magic, shift, d32);
+    auto col = [&](int r, uint32_t Nv, uint32_t rb_, uint32_t wb_, int jcol) {
+        uint32_t b = FAST ? __umulhi(Nv, magic) >> shift : div_corrected(Nv, magic, shift, d32);
+        if (kDebugBounds) b = checked_bin(b, jcol, n_t, hull[r] & 0xffffu, hull[r] >> 16, err);
         const Rec v = Pix<PREC>::load_shared(rb_ + (b << Pix<PREC>::kLog2Bytes));
         float wv = 0.f;
         if (WMODE == WMODE_FREQ) wv = lds_f32(swt_a + (b << 2));
@@ -94,8 +97,8 @@ __device__ __forceinline__ void batch_slab(uint32_t rb, uint32_t wb, uint32_t sw
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             const uint32_t Na = N[r], Nb = Na + D[r];
-            col(r, Na, rb, wb);
-            col(r, Nb, rb + row_bytes, wb + wrow_bytes);
+            col(r, Na, rb, wb, j0 + jj);
+            col(r, Nb, rb + row_bytes, wb + wrow_bytes, j0 + jj + 1);
             N[r] = Nb + D[r] + D2[r];
             D[r] = D[r] + D2[r] + D2[r];
         }
@@ -105,7 +108,7 @@ __device__ __forceinline__ void batch_slab(uint32_t rb, uint32_t wb, uint32_t sw
     if (jj < rows) {
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            col(r, N[r], rb, wb);
+            col(r, N[r], rb, wb, j0 + jj);
             N[r] += D[r];
             D[r] += D2[r];
         }
@@ -209,6 +212,7 @@ __global__ void __launch_bounds__(batch_max_threads(R), 1) score_batch_kernel(Ba
         uint32_t N[R], D[R], D2[R];
         uint32_t pa[R], pc[R];  // narrow phase form (n_f <= kPhaseNarrowNf)
         float acc[R], W[R];
+        uint32_t hull[kDebugBounds ? R : 1];  // debug build: each template's bins, lo | hi << 16
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             uint64_t i = (uint64_t)tid + (uint64_t)r * nthr;
@@ -217,6 +221,7 @@ __global__ void __launch_bounds__(batch_max_threads(R), 1) score_batch_kernel(Ba
             uint32_t f[3];
             double tau;
             draw_track(bm->ts.seed, bm->ts.offset + rel, (uint32_t)bm->m.n_f, bm->ts.tau_max, f, tau);
+            if (kDebugBounds) hull[kDebugBounds ? r : 0] = hull_lo(f) | (hull_hi(f) << 16);
             const Raster32 rs = raster_init(f[0], f[1], f[2], (uint32_t)(n_t - 1));
             N[r] = rs.N; D[r] = rs.D; D2[r] = rs.D2;
             const Phase ph = phase_consts(bm->m.f_min, bm->m.df, tau, bm->m.n_f);
@@ -240,10 +245,10 @@ __global__ void __launch_bounds__(batch_max_threads(R), 1) score_batch_kernel(Ba
             const uint32_t wb = rb + (uint32_t)S * row_bytes;
             if (fast)
                 batch_slab<R, WMODE, PREC, true>(rb, wb, swt_a, rows, row_bytes, wrow_bytes, magic, shift, d32, N, D,
-                                                 D2, pa, pc, acc, W);
+                                                 D2, pa, pc, acc, W, hull, s * S, n_t, a.err);
             else
                 batch_slab<R, WMODE, PREC, false>(rb, wb, swt_a, rows, row_bytes, wrow_bytes, magic, shift, d32, N,
-                                                  D, D2, pa, pc, acc, W);
+                                                  D, D2, pa, pc, acc, W, hull, s * S, n_t, a.err);
             // This warp is done with the buffer; the last warp to finish refills it.
             __syncwarp();
             if (lane == 0) {
@@ -789,6 +794,9 @@ int stk_batch_score(stk_batch *b, int k, stk_hit *out, unsigned flags)
     if (rc) return rc;
     CUDA_TRY(c, cudaGraphLaunch(b->gexec, c->stream));
     const size_t bytes = sizeof(stk_hit) * (size_t)b->n_maps * k;
+    if (kDebugBounds)   // every map's canaries and the out-of-range flag (debug build)
+        for (int i = 0; i < b->n_maps; ++i)
+            if ((rc = debug_verify(c, b->maps[i])) != STK_OK) return rc;
     if (flags & STK_OUT_HOST) {
         CUDA_TRY(c, cudaMemcpyAsync(out, b->d_hits, bytes, cudaMemcpyDeviceToHost, c->stream));
         int fl = 0;

@@ -73,7 +73,40 @@ enum : int {
     FLAG_SIGMA_VARIES = 8,  // map packing saw more than one sigma value
     ERR_FP16_RANGE = 16,    // |y| / sigma beyond the FP16 range
     ERR_CANCELED = 32,      // a batch kernel saw its cancel flag
+    ERR_BOUNDS = 64,        // debug build: a gather outside its template's bins or the map
 };
+
+// ---------------------------------------------------------------- debug build checks
+// Built with STK_DEBUG_BOUNDS (libstk_debug.so), every pixel gather checks its
+// column against [0, n_t) and its bin against [lo, hi]: the convex hull of the
+// template's control bins (the Bezier curve lies inside it), within [0, n_f).
+// A bin outside is reported (ERR_BOUNDS, read by the next deferred-error check)
+// and replaced by lo, so the check can only report, never read out of range or
+// trap.  The release build compiles the checks away.
+#ifdef STK_DEBUG_BOUNDS
+constexpr bool kDebugBounds = true;
+#else
+constexpr bool kDebugBounds = false;
+#endif
+
+__device__ __forceinline__ uint32_t checked_bin(uint32_t b, int j, int n_t, uint32_t lo, uint32_t hi, int *err)
+{
+    if (kDebugBounds && (b < lo || b > hi || j < 0 || j >= n_t)) {
+        atomicOr(err, ERR_BOUNDS);
+        return lo;
+    }
+    return b;
+}
+
+__host__ __device__ __forceinline__ uint32_t hull_lo(const uint32_t f[3])
+{
+    return f[0] < f[1] ? (f[0] < f[2] ? f[0] : f[2]) : (f[1] < f[2] ? f[1] : f[2]);
+}
+
+__host__ __device__ __forceinline__ uint32_t hull_hi(const uint32_t f[3])
+{
+    return f[0] > f[1] ? (f[0] > f[2] ? f[0] : f[2]) : (f[1] > f[2] ? f[1] : f[2]);
+}
 
 // ---------------------------------------------------------------- Philox4x64-10
 // Counter-based generator of Salmon, Moraes, Dror and Shaw (SC'11): ten
@@ -599,7 +632,7 @@ cudaError_t launch_widen(const float *in, double *out, uint64_t n, cudaStream_t 
 
 // Interpolated statistic of continuous templates (forward: snr; adjoint: g * gradient).
 cudaError_t launch_interp(const MapDev &m, const float *f3, const float *tau, const float *g, uint64_t n, float *snr,
-                          float *gf3, float *gtau, bool adjoint, cudaStream_t st);
+                          float *gf3, float *gtau, bool adjoint, int *err, cudaStream_t st);
 
 // Top-k selection over the FP32 snr[0..n): hits get (snr widened to FP64, offset + i, params).  Scratch
 // is caller-provided: see select_scratch_bytes.  sample: keys sampled for the candidate

@@ -53,6 +53,8 @@ struct stk_map {
     MapDev dev{};
     void *rec_buf = nullptr;
     void *w_buf = nullptr;
+    size_t rec_bytes = 0;          // bytes of rec_buf and w_buf in use (a debug build's canary follows)
+    size_t w_bytes = 0;
     unsigned flags = 0;
 };
 
@@ -64,6 +66,8 @@ int set_err(stk_ctx *c, int code, const char *fmt, ...);
 int read_err_flags(stk_ctx *c, int *flags);
 // Map error bits to a status code (with message).
 int flags_to_status(stk_ctx *c, int flags);
+// Debug build: check canaries and out-of-range gathers after a call (release: STK_OK).
+int debug_verify(stk_ctx *c, const stk_map *m);
 
 #define CUDA_TRY(ctx, call)                                                                                         \
     do {                                                                                                           \

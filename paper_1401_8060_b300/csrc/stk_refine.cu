@@ -33,8 +33,9 @@ namespace {
 // FP32 records: z = |z| e^{2 pi i arg}, weight w.  FP16 records: |z| = h r with
 // r = 1/sigma (weight r^2), or h alone when the weight is constant.
 template <int WMODE, int PREC>
-__device__ __forceinline__ void pixel_at(const MapDev &m, int j, int k, float &zr, float &zi, float &w)
+__device__ __forceinline__ void pixel_at(const MapDev &m, int j, int k, float &zr, float &zi, float &w, int *err)
 {
+    if (kDebugBounds) k = (int)checked_bin((uint32_t)k, j, m.n_t, 0u, (uint32_t)m.n_f - 1u, err);
     const typename Pix<PREC>::Rec v = Pix<PREC>::load_global(m.rec, (size_t)j * m.ldr + k);
     float mag = Pix<PREC>::mag(v);
     float wv = 0.f;
@@ -59,6 +60,7 @@ constexpr int kInterpBlock = 128;
 struct InterpConst {
     double M, inv_M2, df, f_min;
     float inv_Mf, df_f, fmin_f;
+    int *err;  // deferred error flags (debug build: out-of-range gathers)
 };
 
 // Fused Adam step (refinement): the template's thread 0 takes the step from the
@@ -184,8 +186,8 @@ __global__ void __launch_bounds__(kInterpBlock) interp_kernel(MapDev m, InterpCo
         if (kb > n_f - 2) { a += (float)(kb - (n_f - 2)); kb = n_f - 2; }  // x = n_f - 1: the top knot
         if (n_f < 2) { kb = 0; a = 0.f; }
         float z0r, z0i, w0, z1r, z1i, w1;
-        pixel_at<WMODE, PREC>(m, j, kb, z0r, z0i, w0);
-        if (n_f > 1) pixel_at<WMODE, PREC>(m, j, kb + 1, z1r, z1i, w1);
+        pixel_at<WMODE, PREC>(m, j, kb, z0r, z0i, w0, k.err);
+        if (n_f > 1) pixel_at<WMODE, PREC>(m, j, kb + 1, z1r, z1i, w1, k.err);
         else { z1r = z0r; z1i = z0i; w1 = w0; }
         const float dzr = z1r - z0r, dzi = z1i - z0i, dw = w1 - w0;
         const float zr = fmaf(a, dzr, z0r), zi = fmaf(a, dzi, z0i), w = fmaf(a, dw, w0);
@@ -268,9 +270,10 @@ __global__ void __launch_bounds__(kInterpBlock) interp_kernel(MapDev m, InterpCo
     gtau[i] = gr[3];
 }
 
-InterpConst interp_const(const MapDev &m)
+InterpConst interp_const(const MapDev &m, int *err)
 {
     InterpConst k;
+    k.err = err;
     k.M = (double)(m.n_t - 1);
     k.inv_M2 = 1.0 / (k.M * k.M);
     k.df = m.df;
@@ -297,13 +300,13 @@ int interp_threads(uint64_t n, int P)
 
 template <int MODE, int P>
 cudaError_t launch_interp_P(const MapDev &m, const float *f3, const float *tau, const float *g, uint64_t n,
-                            float *snr, float *gf3, float *gtau, const AdamStep &ad, cudaStream_t st)
+                            float *snr, float *gf3, float *gtau, const AdamStep &ad, int *err, cudaStream_t st)
 {
     constexpr uint64_t TPB = kInterpBlock / P;
     const uint64_t blocks = (n + TPB - 1) / TPB;
     if (blocks > 0x7fffffffull) return cudaErrorInvalidValue;
     const unsigned b = (unsigned)blocks;
-    const InterpConst k = interp_const(m);
+    const InterpConst k = interp_const(m, err);
 #define STK_INTERP(W, PR) \
     interp_kernel<W, PR, MODE, P><<<b, kInterpBlock, 0, st>>>(m, k, f3, tau, g, n, snr, gf3, gtau, ad)
     if (m.prec == PREC_FP16) {
@@ -321,12 +324,12 @@ cudaError_t launch_interp_P(const MapDev &m, const float *f3, const float *tau, 
 
 template <int MODE>
 cudaError_t launch_interp_M(const MapDev &m, const float *f3, const float *tau, const float *g, uint64_t n,
-                            float *snr, float *gf3, float *gtau, const AdamStep &ad, int P, cudaStream_t st)
+                            float *snr, float *gf3, float *gtau, const AdamStep &ad, int P, int *err, cudaStream_t st)
 {
     switch (interp_threads(n, P)) {
-    case 128: return launch_interp_P<MODE, 128>(m, f3, tau, g, n, snr, gf3, gtau, ad, st);
-    case 64: return launch_interp_P<MODE, 64>(m, f3, tau, g, n, snr, gf3, gtau, ad, st);
-    default: return launch_interp_P<MODE, 32>(m, f3, tau, g, n, snr, gf3, gtau, ad, st);
+    case 128: return launch_interp_P<MODE, 128>(m, f3, tau, g, n, snr, gf3, gtau, ad, err, st);
+    case 64: return launch_interp_P<MODE, 64>(m, f3, tau, g, n, snr, gf3, gtau, ad, err, st);
+    default: return launch_interp_P<MODE, 32>(m, f3, tau, g, n, snr, gf3, gtau, ad, err, st);
     }
 }
 
@@ -340,6 +343,206 @@ __global__ void __launch_bounds__(256) refine_init_kernel(const float *__restric
     st[2 * i + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
+// ------------------------------------------------------------------ discrete follow-up
+// The refined continuous templates are judged by the discrete statistic (Eq. 7
+// on whole pixels).  The polish climbs that statistic directly, one warp per
+// template: the delay is set to the nearest maximum of SNR(tau) at the
+// template's fixed pixels (W does not depend on tau; S(tau) = sum_j |z_j|
+// cos(2 pi f_j tau + arg z_j) is smooth, so safeguarded Newton steps on S find
+// it), then each control bin moves by +-1 while a move, with its delay again
+// maximised, raises the SNR.  The climb compares warp sums (any summation
+// order); the choice among the start, the polished start and the polished
+// alternative uses the scorer's own sequential sum, so it never returns a
+// template that scores below the start.
+constexpr int kPolishBlock = 128;   // 4 warps, one template each
+constexpr int kPolishNewton = 4;    // Newton steps per delay search
+
+struct PolishSums {
+    float S, dS, d2S, W;
+};
+
+// S, dS/dtau, d2S/dtau2 and W of template f at delay tau, summed over the warp's
+// lanes (lane l takes columns l, l + 32, ...), the same value in every lane.
+template <int WMODE, int PREC>
+__device__ __forceinline__ PolishSums polish_eval(const MapDev &m, const uint32_t f[3], double tau, int lane, int *err)
+{
+    const Phase ph = phase_consts(m.f_min, m.df, tau, m.n_f);
+    const float two_pi = 6.28318530717958647692f, fmin_f = (float)m.f_min, df_f = (float)m.df;
+    float S = 0.f, dS = 0.f, d2S = 0.f, W = 0.f;
+    for (int j = lane; j < m.n_t; j += 32) {
+        uint32_t b = raster_bin_wide(f[0], f[1], f[2], m.M, (uint32_t)j, m.d);
+        if (kDebugBounds) b = checked_bin(b, j, m.n_t, hull_lo(f), hull_hi(f), err);
+        const typename Pix<PREC>::Rec v = Pix<PREC>::load_global(m.rec, (size_t)j * m.ldr + b);
+        float wv = 0.f;
+        if (WMODE == WMODE_FREQ) wv = __ldg(m.w + b);
+        if (WMODE == WMODE_PIXEL) wv = __ldg(m.w + (size_t)j * m.ldw + b);
+        const uint32_t T = template_turn(b, ph);
+        float x, mg = Pix<PREC>::mag(v);
+        if constexpr (PREC == PREC_FP32) {
+            x = fmaf((float)(int32_t)T, kTurnToRad, Pix<PREC>::arg_rad(v));
+        } else {
+            x = (float)(int32_t)(T + ((uint32_t)v << 16)) * kTurnToRad;
+            if (WMODE != WMODE_CONST) mg *= wv;
+        }
+        float sn, cs;
+        __sincosf(x, &sn, &cs);
+        const float om = two_pi * fmaf((float)b, df_f, fmin_f);   // d angle / d tau
+        S = fmaf(mg, cs, S);
+        dS = fmaf(-mg * sn, om, dS);
+        d2S = fmaf(-mg * cs, om * om, d2S);
+        W += PREC == PREC_FP32 ? wv : wv * wv;
+    }
+    float v4[4] = {S, dS, d2S, W};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        for (int o = 16; o > 0; o >>= 1) v4[q] += __shfl_xor_sync(0xffffffffu, v4[q], o);
+        v4[q] = __shfl_sync(0xffffffffu, v4[q], 0);   // lane 0's sum for every lane: uniform decisions
+    }
+    return {v4[0], v4[1], v4[2], v4[3]};
+}
+
+template <int WMODE>
+__device__ __forceinline__ float polish_snr(const PolishSums &s, const MapDev &m)
+{
+    if (WMODE == WMODE_CONST || m.paper) return s.S * m.norm_f;
+    return s.S * rsqrtf(s.W);
+}
+
+// The delay maximising SNR near tau, within [-tau_max, tau_max]: Newton steps on
+// S where it is concave, else a step towards increasing S, each at most a tenth
+// of the shortest period in the band and kept only when the SNR rises (else
+// halved, twice).  Returns the SNR at the returned delay.
+template <int WMODE, int PREC>
+__device__ __forceinline__ float polish_delay(const MapDev &m, const uint32_t f[3], double &tau, double tau_max, int lane,
+                                              int *err)
+{
+    PolishSums cur = polish_eval<WMODE, PREC>(m, f, tau, lane, err);
+    float snr = polish_snr<WMODE>(cur, m);
+    const double f_top = m.f_min + (m.n_f - 1) * m.df;
+    const double dmax = 0.1 / fabs(f_top);
+    for (int it = 0; it < kPolishNewton; ++it) {
+        double step;
+        if (cur.d2S < 0.f) step = -(double)cur.dS / (double)cur.d2S;
+        else step = cur.dS > 0.f ? dmax : (cur.dS < 0.f ? -dmax : 0.0);
+        step = fmin(fmax(step, -dmax), dmax);
+        if (!(step != 0.0)) break;
+        bool moved = false;
+        for (int h = 0; h < 3 && !moved; ++h, step *= 0.5) {
+            const double t = fmin(fmax(tau + step, -tau_max), tau_max);
+            if (t == tau) break;
+            const PolishSums nx = polish_eval<WMODE, PREC>(m, f, t, lane, err);
+            const float sn = polish_snr<WMODE>(nx, m);
+            if (sn > snr) {
+                tau = t;
+                cur = nx;
+                snr = sn;
+                moved = true;
+            }
+        }
+        if (!moved) break;
+    }
+    return snr;
+}
+
+// Hill climb from (f, tau): delay first, then +-1 moves of the control bins.
+template <int WMODE, int PREC>
+__device__ __forceinline__ void polish_climb(const MapDev &m, uint32_t f[3], double &tau, double tau_max, int moves, int lane,
+                                             int *err)
+{
+    float snr = polish_delay<WMODE, PREC>(m, f, tau, tau_max, lane, err);
+    for (int mv = 0; mv < moves; ++mv) {
+        uint32_t bf[3] = {f[0], f[1], f[2]};
+        double bt = tau;
+        float bs = snr;
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+#pragma unroll
+            for (int d = -1; d <= 1; d += 2) {
+                if ((d < 0 && f[k] == 0) || (d > 0 && f[k] + 1 >= (uint32_t)m.n_f)) continue;
+                uint32_t g[3] = {f[0], f[1], f[2]};
+                g[k] += (uint32_t)d;
+                double t = tau;
+                const float sn = polish_delay<WMODE, PREC>(m, g, t, tau_max, lane, err);
+                if (sn > bs) {
+                    bf[0] = g[0]; bf[1] = g[1]; bf[2] = g[2];
+                    bt = t;
+                    bs = sn;
+                }
+            }
+        if (!(bs > snr)) break;
+        f[0] = bf[0]; f[1] = bf[1]; f[2] = bf[2];
+        tau = bt;
+        snr = bs;
+    }
+}
+
+// The scorer's SNR of one template: columns in order, one thread, the same
+// per-pixel arithmetic and normalisation as stk_score_explicit (bit-identical).
+template <int WMODE, int PREC>
+__device__ __forceinline__ float polish_canonical(const MapDev &m, const uint32_t f[3], double tau, int *err)
+{
+    const Phase ph = phase_consts(m.f_min, m.df, tau, m.n_f);
+    float acc = 0.f, W = 0.f;
+    for (int j = 0; j < m.n_t; ++j) {
+        uint32_t b = raster_bin_wide(f[0], f[1], f[2], m.M, (uint32_t)j, m.d);
+        if (kDebugBounds) b = checked_bin(b, j, m.n_t, hull_lo(f), hull_hi(f), err);
+        const typename Pix<PREC>::Rec v = Pix<PREC>::load_global(m.rec, (size_t)j * m.ldr + b);
+        float wv = 0.f;
+        if (WMODE == WMODE_FREQ) wv = __ldg(m.w + b);
+        if (WMODE == WMODE_PIXEL) wv = __ldg(m.w + (size_t)j * m.ldw + b);
+        accumulate<PREC, WMODE>(v, b, ph, wv, acc, W);
+    }
+    return finalize_snr<WMODE>(acc, W, m);
+}
+
+template <int WMODE, int PREC>
+__global__ void __launch_bounds__(kPolishBlock) polish_kernel(MapDev m, uint32_t *__restrict__ f3,
+                                                              double *__restrict__ tau,
+                                                              const float *__restrict__ alt_f3,
+                                                              const float *__restrict__ alt_tau, uint64_t n,
+                                                              double tau_max, int moves, double *__restrict__ snr_out,
+                                                              int *__restrict__ which_out, int *err)
+{
+    const uint64_t i = (uint64_t)blockIdx.x * (kPolishBlock / 32) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (i >= n) return;   // whole warps leave together
+    const uint32_t fs[3] = {min(f3[3 * i], (uint32_t)m.n_f - 1), min(f3[3 * i + 1], (uint32_t)m.n_f - 1),
+                            min(f3[3 * i + 2], (uint32_t)m.n_f - 1)};
+    const double ts = tau[i];
+    uint32_t fa[3] = {fs[0], fs[1], fs[2]};
+    double ta = fmin(fmax(ts, -tau_max), tau_max);
+    polish_climb<WMODE, PREC>(m, fa, ta, tau_max, moves, lane, err);
+    uint32_t fb[3] = {fa[0], fa[1], fa[2]};
+    double tb = ta;
+    if (alt_f3) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const float x = alt_f3[3 * i + k];
+            const float r = rintf(fminf(fmaxf(x == x ? x : 0.f, 0.f), (float)(m.n_f - 1)));
+            fb[k] = (uint32_t)r;
+        }
+        const double t = (double)alt_tau[i];
+        tb = t == t ? fmin(fmax(t, -tau_max), tau_max) : ta;
+        polish_climb<WMODE, PREC>(m, fb, tb, tau_max, moves, lane, err);
+    }
+    if (lane != 0) return;
+    // the choice, by the scorer's own sums: the start unless a polished form beats it
+    const float s0 = polish_canonical<WMODE, PREC>(m, fs, ts, err);
+    const float s1 = polish_canonical<WMODE, PREC>(m, fa, ta, err);
+    const float s2 = alt_f3 ? polish_canonical<WMODE, PREC>(m, fb, tb, err) : s1;
+    int w = 0;
+    float best = s0;
+    if (s1 > best) { w = 1; best = s1; }
+    if (alt_f3 && s2 > best) { w = 2; best = s2; }
+    const uint32_t *fo = w == 0 ? fs : (w == 1 ? fa : fb);
+    f3[3 * i] = fo[0];
+    f3[3 * i + 1] = fo[1];
+    f3[3 * i + 2] = fo[2];
+    tau[i] = w == 0 ? ts : (w == 1 ? ta : tb);
+    if (snr_out) snr_out[i] = (double)best;
+    if (which_out) which_out[i] = w;
+}
+
 }  // namespace
 
 size_t refine_scratch_bytes(uint64_t n)
@@ -348,7 +551,7 @@ size_t refine_scratch_bytes(uint64_t n)
 }
 
 cudaError_t launch_refine(const MapDev &m, float *f3, float *tau, uint64_t n, int steps, float lr_f, float lr_u,
-                          float tau_max, float *hist, void *scratch, int P, cudaStream_t st)
+                          float tau_max, float *hist, void *scratch, int P, int *err, cudaStream_t st)
 {
     if (n == 0 || steps < 0) return cudaSuccess;
     AdamStep ad{};
@@ -365,26 +568,49 @@ cudaError_t launch_refine(const MapDev &m, float *f3, float *tau, uint64_t n, in
         ad.step_u = (float)(lr_u / bc1);
         ad.sbc2 = (float)std::sqrt(bc2);
         e = launch_interp_M<2>(m, f3, tau, nullptr, n, hist ? hist + (size_t)(t - 1) * n : nullptr, nullptr,
-                               nullptr, ad, P, st);
+                               nullptr, ad, P, err, st);
     }
     if (e == cudaSuccess && hist)
         e = launch_interp_M<0>(m, f3, tau, nullptr, n, hist + (size_t)steps * n, nullptr, nullptr, AdamStep{}, P,
-                               st);
+                               err, st);
     return e;
 }
 
 cudaError_t launch_interp_tuned(const MapDev &m, const float *f3, const float *tau, const float *g, uint64_t n,
-                                float *snr, float *gf3, float *gtau, bool adjoint, int P, cudaStream_t st)
+                                float *snr, float *gf3, float *gtau, bool adjoint, int P, int *err, cudaStream_t st)
 {
     if (n == 0) return cudaSuccess;
-    return adjoint ? launch_interp_M<1>(m, f3, tau, g, n, snr, gf3, gtau, AdamStep{}, P, st)
-                   : launch_interp_M<0>(m, f3, tau, g, n, snr, gf3, gtau, AdamStep{}, P, st);
+    return adjoint ? launch_interp_M<1>(m, f3, tau, g, n, snr, gf3, gtau, AdamStep{}, P, err, st)
+                   : launch_interp_M<0>(m, f3, tau, g, n, snr, gf3, gtau, AdamStep{}, P, err, st);
+}
+
+cudaError_t launch_polish(const MapDev &m, uint32_t *f3, double *tau, const float *alt_f3, const float *alt_tau,
+                          uint64_t n, double tau_max, int moves, double *snr, int *which, int *err, cudaStream_t st)
+{
+    if (n == 0) return cudaSuccess;
+    constexpr uint64_t TPB = kPolishBlock / 32;
+    const uint64_t blocks = (n + TPB - 1) / TPB;
+    if (blocks > 0x7fffffffull) return cudaErrorInvalidValue;
+    const unsigned b = (unsigned)blocks;
+#define STK_POLISH(W, PR) \
+    polish_kernel<W, PR><<<b, kPolishBlock, 0, st>>>(m, f3, tau, alt_f3, alt_tau, n, tau_max, moves, snr, which, err)
+    if (m.prec == PREC_FP16) {
+        if (m.wmode == WMODE_CONST) STK_POLISH(WMODE_CONST, PREC_FP16);
+        else if (m.wmode == WMODE_FREQ) STK_POLISH(WMODE_FREQ, PREC_FP16);
+        else STK_POLISH(WMODE_PIXEL, PREC_FP16);
+    } else {
+        if (m.wmode == WMODE_CONST) STK_POLISH(WMODE_CONST, PREC_FP32);
+        else if (m.wmode == WMODE_FREQ) STK_POLISH(WMODE_FREQ, PREC_FP32);
+        else STK_POLISH(WMODE_PIXEL, PREC_FP32);
+    }
+#undef STK_POLISH
+    return cudaGetLastError();
 }
 
 cudaError_t launch_interp(const MapDev &m, const float *f3, const float *tau, const float *g, uint64_t n, float *snr,
-                          float *gf3, float *gtau, bool adjoint, cudaStream_t st)
+                          float *gf3, float *gtau, bool adjoint, int *err, cudaStream_t st)
 {
-    return launch_interp_tuned(m, f3, tau, g, n, snr, gf3, gtau, adjoint, 0, st);
+    return launch_interp_tuned(m, f3, tau, g, n, snr, gf3, gtau, adjoint, 0, err, st);
 }
 
 }  // namespace stk

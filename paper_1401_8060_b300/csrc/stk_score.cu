@@ -69,6 +69,7 @@ __global__ void __launch_bounds__(256) score_simple_kernel(MapDev m, TrackSet ts
         } else {
             bin = raster_bin_wide(f[0], f[1], f[2], m.M, (uint32_t)j, m.d);
         }
+        if (kDebugBounds) bin = checked_bin(bin, j, m.n_t, hull_lo(f), hull_hi(f), err);
         const auto v = Pix<PREC>::load_global(m.rec, (size_t)j * m.ldr + bin);
         float wv = 0.f;
         if (WMODE == WMODE_FREQ) wv = __ldg(m.w + bin);
@@ -137,7 +138,9 @@ __global__ void __launch_bounds__(256, 4) score_general_kernel(MapDev m, TrackSe
     // rather than once per lane.  Each template's sums do not depend on its
     // neighbours in the warp: when a flush happens changes nothing.
     float acc = 0.f, W = 0.f, acc_x = 0.f, W_x = 0.f;
+    const uint32_t h_lo = hull_lo(f), h_hi = hull_hi(f);
     auto add = [&](int j, int32_t b, float &a_, float &w_) {
+        if (kDebugBounds) b = (int32_t)checked_bin((uint32_t)b, j, m.n_t, h_lo, h_hi, err);
         const auto v = Pix<PREC>::load_global(m.rec, (size_t)j * m.ldr + (uint32_t)b);
         float wv = 0.f;
         if (WMODE == WMODE_FREQ) wv = __ldg(m.w + b);
@@ -166,6 +169,7 @@ __global__ void __launch_bounds__(256, 4) score_general_kernel(MapDev m, TrackSe
     // harmless and unused), then the sums in column order.
     using Rec = typename Pix<PREC>::Rec;
     auto gather = [&](int j, int32_t b, Rec &v, float &wv) {
+        if (kDebugBounds) b = (int32_t)checked_bin((uint32_t)b, j, m.n_t, 0u, (uint32_t)m.n_f - 1u, err);
         v = Pix<PREC>::load_global(m.rec, (size_t)j * m.ldr + (uint32_t)b);
         wv = 0.f;
         if (WMODE == WMODE_FREQ) wv = __ldg(m.w + b);
@@ -334,6 +338,7 @@ __global__ void __launch_bounds__(staged_max_threads(R, WMODE), 1)
         uint32_t N[R], D[R], D2[R];
         uint32_t pa[R], pc[R];  // narrow phase form (n_f <= kPhaseNarrowNf)
         float acc[R], W[R];
+        uint32_t hlo[kDebugBounds ? R : 1], hhi[kDebugBounds ? R : 1];  // debug build: each template's bins
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             uint64_t i = (uint64_t)tid + (uint64_t)r * nthr;
@@ -349,6 +354,10 @@ __global__ void __launch_bounds__(staged_max_threads(R, WMODE), 1)
             pc[r] = ph.c;
             acc[r] = 0.f;
             W[r] = 0.f;
+            if (kDebugBounds) {
+                hlo[kDebugBounds ? r : 0] = hull_lo(f);
+                hhi[kDebugBounds ? r : 0] = hull_hi(f);
+            }
         }
 
         for (int s = 0; s < a.nslabs; ++s, ++q) {
@@ -363,8 +372,10 @@ __global__ void __launch_bounds__(staged_max_threads(R, WMODE), 1)
             uint32_t rb = srec_a + (uint32_t)slot * slab_bytes;  // shared address of the slab's current row
             uint32_t wb = sw_a + (uint32_t)slot * wslab_bytes;   // its weight row (WMODE_PIXEL)
             // One pixel of template r at rasteriser value Nv (row base rb_, weight row wb_).
-            auto col = [&](int r, uint32_t Nv, uint32_t rb_, uint32_t wb_) {
-                const uint32_t b = __umulhi(Nv, magic) >> shift;
+            auto col = [&](int r, uint32_t Nv, uint32_t rb_, uint32_t wb_, int jcol) {
+                uint32_t b = __umulhi(Nv, magic) >> shift;
+                if (kDebugBounds)
+                    b = checked_bin(b, jcol, m.n_t, hlo[kDebugBounds ? r : 0], hhi[kDebugBounds ? r : 0], err);
                 const Rec v = Pix<PREC>::load_shared(rb_ + (b << Pix<PREC>::kLog2Bytes));
                 float wv = 0.f;
                 if (WMODE == WMODE_FREQ) wv = lds_f32(swt_a + (b << 2));
@@ -378,8 +389,8 @@ __global__ void __launch_bounds__(staged_max_threads(R, WMODE), 1)
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
                     const uint32_t Na = N[r], Nb = Na + D[r];
-                    col(r, Na, rb, wb);
-                    col(r, Nb, rb + row_bytes, wb + wrow_bytes);
+                    col(r, Na, rb, wb, s * a.S + jj);
+                    col(r, Nb, rb + row_bytes, wb + wrow_bytes, s * a.S + jj + 1);
                     N[r] = Nb + D[r] + D2[r];
                     D[r] = D[r] + D2[r] + D2[r];
                 }
@@ -389,7 +400,7 @@ __global__ void __launch_bounds__(staged_max_threads(R, WMODE), 1)
             if (jj < rows) {
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
-                    col(r, N[r], rb, wb);
+                    col(r, N[r], rb, wb, s * a.S + jj);
                     N[r] += D[r];
                     D[r] += D2[r];
                 }

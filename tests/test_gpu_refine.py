@@ -319,3 +319,55 @@ def test_threads_option_range(ctx):
     for bad in (1, 16, 96, 256, -32):
         with pytest.raises(stk.StkError):
             ctx.set_option(_lib.STK_OPT_INTERP_THREADS, bad)
+
+
+@pytest.mark.parametrize("mode,fp16", [("freq", False), ("pixel", False), ("const", False), ("freq", True)])
+def test_polish_never_loses_and_matches_oracle(ctx, mode, fp16):
+    """The discrete follow-up (stk_polish) of the loudest templates: every kept
+    template's SNR is the scorer's own (bit-identical to stk_score_explicit), at
+    least the start's, and within the parity bound of the FP64 oracle, whose
+    rescoring also finds no template below its start beyond that bound.  With
+    the refined continuous templates as alternatives, most templates gain."""
+    n_t, n_f, T, k = 160, 400, 60_000, 192
+    y, sig = _map(mode, n_t, n_f, 90)
+    m = ctx.load_map(torch.from_numpy(y).cuda(), torch.from_numpy(sig).cuda(), 40.0, 0.5, fp16=fp16)
+    om = oracle.OracleMap(y, sig, 40.0, 0.5, sig.ndim == 1)
+    ctx.set_tracks(T, 5, 0, TAU_MAX)
+    hits = ctx.score(m, k)
+    f_start = np.array([list(v) for v in hits["f"]], dtype=np.int64)
+    t_start = hits["tau"].copy()
+    f_ref = torch.tensor(f_start, dtype=torch.float32, device="cuda")
+    t_ref = torch.tensor(t_start, dtype=torch.float32, device="cuda")
+    f_ref, t_ref, _ = ctx.refine(m, f_ref, t_ref, TAU_MAX, steps=30)
+    f_out, t_out, snr, which = ctx.polish(m, f_start, t_start, TAU_MAX, alt_f3=f_ref, alt_tau=t_ref, moves=6)
+    f_out, t_out, snr, which = (x.cpu().numpy() for x in (f_out, t_out, snr, which))
+    assert np.all((which >= 0) & (which <= 2))
+    assert np.all((f_out >= 0) & (f_out < n_f)) and np.all(np.abs(t_out) <= TAU_MAX)
+    assert np.all(snr >= hits["snr"]), np.min(snr - hits["snr"])            # never below the start
+    again = ctx.score_explicit(m, torch.from_numpy(f_out.astype(np.int32)), torch.from_numpy(t_out)).cpu().numpy()
+    np.testing.assert_array_equal(again.astype(np.float32), snr.astype(np.float32))   # the scorer's own SNR
+    o, ex = om.score_explicit(f_out.astype(np.uint32), t_out, extras=True)
+    sc = ex["absz"] / np.sqrt(ex["W"])
+    rt = 3.5e-4 if fp16 else 1e-5
+    assert np.all(np.abs(snr - o) <= rt * np.maximum(np.abs(o), sc)), np.max(np.abs(snr - o) / sc)
+    o0, ex0 = om.score_explicit(f_start.astype(np.uint32), t_start, extras=True)
+    sc0 = ex0["absz"] / np.sqrt(ex0["W"])
+    assert np.all(o >= o0 - 2 * rt * np.maximum(sc, sc0)), np.min(o - o0)   # the oracle agrees
+    gain = snr - hits["snr"]
+    assert np.mean(gain > 0) > 0.8 and np.mean(gain) > 0, (np.mean(gain > 0), np.mean(gain))
+    # delay only, no alternative: still never below the start
+    f1, t1, s1, w1 = ctx.polish(m, f_start, t_start, TAU_MAX, moves=0)
+    s1, f1 = s1.cpu().numpy(), f1.cpu().numpy()
+    assert np.all(s1 >= hits["snr"]) and np.array_equal(f1, f_start)
+    m.close()
+
+
+def test_polish_invalid_inputs(ctx):
+    y, sig = _map("freq", 40, 64, 3)
+    m = ctx.load_map(torch.from_numpy(y).cuda(), torch.from_numpy(sig).cuda(), 40.0, 0.5)
+    f = np.zeros((4, 3), np.int64)
+    t = np.zeros(4)
+    for kw in ({"tau_max": 0.0}, {"tau_max": TAU_MAX, "moves": -1}, {"tau_max": TAU_MAX, "moves": 2000}):
+        with pytest.raises(stk.StkError):
+            ctx.polish(m, f, t, **kw)
+    m.close()
