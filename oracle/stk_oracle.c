@@ -30,6 +30,11 @@
  *     sqrt(sum_j sigma_j^-2); paper mode: SNR = (1/N) sum_j Re[e^{i theta_j}
  *     y_j / sigma_j] (Eq. 7 with the complex SNR p = y / sigma).
  *   - Loudest = signed maximum; ties go to the smaller template index.
+ *   - Notched pixels (the black lines of Fig. 1's caption): sigma = +infinity
+ *     marks a pixel removed from the analysis; it contributes nothing to S or
+ *     W (z = 0, w = 0, whatever y holds there).  The paper form keeps N, the
+ *     template's pixel count.  A template whose pixels are all notched has no
+ *     data: its SNR is 0.
  *
  * Precision: every step is IEEE binary64 with libm cos/sin; integers are exact
  * 64-bit (128-bit for the Philox products and the bin draw).
@@ -130,7 +135,9 @@ orc_map *orc_map_create(const float *y_c64, const float *sigma, int sigma_per_fr
             size_t p = (size_t)t * n_f + k;
             double s = sigma_per_freq ? (double)sigma[k] : (double)sigma[p];
             double yr = (double)y_c64[2 * p], yi = (double)y_c64[2 * p + 1];
-            if (paper_mode) {
+            if (isinf(s) && s > 0) {                     /* notched: no data */
+                m->z[2 * p] = 0.0; m->z[2 * p + 1] = 0.0; m->w[p] = paper_mode ? 1.0 : 0.0;
+            } else if (paper_mode) {
                 m->z[2 * p] = yr / s; m->z[2 * p + 1] = yi / s; m->w[p] = 1.0;
             } else {
                 double w = 1.0 / (s * s);
@@ -170,7 +177,7 @@ double orc_score_track(const orc_map *m, const uint32_t f[3], double tau,
         Z += sqrt(zr * zr + zi * zi);
     }
     free(bins);
-    double snr = m->paper_mode ? S / (double)n_t : S / sqrt(W);
+    double snr = m->paper_mode ? S / (double)n_t : (W > 0.0 ? S / sqrt(W) : 0.0);
     if (S_out) *S_out = S;
     if (W_out) *W_out = W;
     if (absterm_out) *absterm_out = A;
@@ -204,7 +211,7 @@ static void *orc_range_worker(void *arg)
         double tau, W = 0.0, Z = 0.0;
         orc_track_params(jb->seed, jb->g0 + i, jb->m->n_f, jb->tau_max, f, &tau);
         jb->out[i] = orc_score_track(jb->m, f, tau, NULL, &W, NULL, &Z);
-        if (jb->scale) jb->scale[i] = Z / (jb->m->paper_mode ? (double)jb->m->n_t : sqrt(W));
+        if (jb->scale) jb->scale[i] = jb->m->paper_mode ? Z / (double)jb->m->n_t : (W > 0.0 ? Z / sqrt(W) : 0.0);
     }
     return NULL;
 }
@@ -334,7 +341,7 @@ double orc_interp_score(const orc_map *m, const double f[3], double tau, double 
         snr = S / n_t;
         if (grad) for (int q = 0; q < 4; ++q) grad[q] = dS[q] / n_t;
     } else {
-        const double rw = 1.0 / sqrt(W);
+        const double rw = W > 0.0 ? 1.0 / sqrt(W) : 0.0;   /* every pixel notched: no data */
         snr = S * rw;
         if (grad) {
             for (int q = 0; q < 3; ++q) grad[q] = dS[q] * rw - 0.5 * S * rw * rw * rw * dW[q];
@@ -458,6 +465,10 @@ static double orc_score_general_scale(const orc_map *m, const uint32_t t[3], con
     }
     free(bins);
     double norm = m->paper_mode ? (double)N : sqrt(W);
+    if (!(norm > 0.0)) {                                  /* every pixel notched: no data */
+        if (scale_out) *scale_out = 0.0;
+        return 0.0;
+    }
     if (scale_out) *scale_out = Z / norm;
     return S / norm;
 }
@@ -500,7 +511,7 @@ static void *orc_general_worker(void *arg)
         } else {
             double W = 0.0, Z = 0.0;
             jb->out[i] = orc_score_track(jb->m, f, tau, NULL, &W, NULL, &Z);
-            if (jb->scale) jb->scale[i] = Z / (jb->m->paper_mode ? (double)jb->m->n_t : sqrt(W));
+            if (jb->scale) jb->scale[i] = jb->m->paper_mode ? Z / (double)jb->m->n_t : (W > 0.0 ? Z / sqrt(W) : 0.0);
         }
     }
     return NULL;

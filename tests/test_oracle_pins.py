@@ -160,6 +160,66 @@ def test_brute_force_enumeration(orc, paper_mode):
         np.testing.assert_allclose(got, ref, rtol=1e-12, atol=1e-12)
 
 
+def brute_snr_notched(y, sigma_full, f_min, df, bins, tau, paper_mode=False):
+    """Eq. 7 over the template's pixels that are not notched (sigma = +inf):
+    those add nothing to S or W; the paper form keeps N = the pixel count; no
+    un-notched pixel at all (weighted form) gives 0."""
+    j = np.arange(len(bins))
+    s = sigma_full[j, bins].astype(np.float64)
+    keep = np.isfinite(s)
+    yv = y[j, bins].astype(np.complex128)[keep]
+    s, fr = s[keep], f_min + bins[keep] * df
+    rot = np.exp(2j * np.pi * fr * tau)
+    if paper_mode:
+        return float(np.sum((rot * (yv / s)).real) / len(bins))
+    W = np.sum(s ** -2.0)
+    return float(np.sum((rot * yv / s ** 2).real) / np.sqrt(W)) if W > 0 else 0.0
+
+
+@pytest.mark.parametrize("paper_mode", [False, True])
+def test_notched_pixels_brute_force(orc, paper_mode):
+    """Fig. 1's notched (black) lines: pixels with sigma = +inf, whatever y holds
+    there (NaN here), add nothing; every template of a 5 x 6 map at several
+    delays against the direct evaluation over the remaining pixels."""
+    n_t, n_f, f_min, df = 5, 6, 100.0, 1.0
+    y, sig = _tiny_map(8, n_t, n_f)
+    rng = np.random.default_rng(9)
+    notch = rng.random((n_t, n_f)) < 0.3
+    notch[:, 2] = True                              # a whole notched line
+    sig = sig.copy()
+    sig[notch] = np.inf
+    y = y.copy()
+    y[notch] = np.complex64(complex(np.nan, np.nan))
+    om = orc.OracleMap(y, sig, f_min, df, sigma_per_freq=False, paper_mode=paper_mode)
+    trip = np.array([(a, b, c) for a in range(n_f) for b in range(n_f) for c in range(n_f)], dtype=np.uint32)
+    for tau in [-0.0071, 0.0, 0.0043]:
+        got = om.score_explicit(trip, np.full(len(trip), tau))
+        ref = [brute_snr_notched(y, sig, f_min, df, bezier_bins_exact(t, n_t), tau, paper_mode) for t in trip]
+        np.testing.assert_allclose(got, ref, rtol=1e-12, atol=1e-12)
+    assert om.score_explicit(np.array([(2, 2, 2)]), np.array([0.001]))[0] == 0.0   # all its pixels notched
+
+
+def test_notched_injection_closed_form(orc):
+    """Zero-noise injection on a template that crosses a notched band: the SNR
+    at the injected delay is A sqrt(sum of sigma^-2 over its un-notched pixels)."""
+    n_t, n_f, f_min, df = 64, 200, 40.0, 0.5
+    sig = (1.0 + np.linspace(0, 3, n_f) ** 2).astype(np.float32)
+    sig[90:110] = np.inf                             # a notched band the template crosses
+    f = (17, 180, 60)
+    b = bezier_bins_exact(f, n_t)
+    assert np.any((b >= 90) & (b < 110)) and np.any((b < 90) | (b >= 110))
+    A, tau_s = 2.5, -0.0061
+    y = np.zeros((n_t, n_f), np.complex64)
+    y[np.arange(n_t), b] = (A * np.exp(-2j * np.pi * (f_min + b * df) * tau_s)).astype(np.complex64)
+    om = orc.OracleMap(y, sig, f_min, df, True)
+    s = sig.astype(np.float64)[b]
+    W = float(np.sum(s[np.isfinite(s)] ** -2.0))
+    got = om.score_explicit(np.array([f]), np.array([tau_s]))[0]
+    assert got == pytest.approx(A * math.sqrt(W), rel=1e-6)
+    everywhere = orc.OracleMap(y, np.full(n_f, np.inf, np.float32), f_min, df, True)
+    assert everywhere.score_explicit(np.array([f]), np.array([tau_s]))[0] == 0.0   # no data at all
+
+
 def test_eq5_special_case_real_map(orc):
     """tau = 0 on a real-valued map reduces Eq. 7 to Eq. 5: the plain mean of rho over the pixels."""
     n_t, n_f = 30, 40
