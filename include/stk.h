@@ -100,21 +100,24 @@ STK_API int stk_set_stream(stk_ctx *ctx, void *cuda_stream);
 /* Copy and pack an ft-map (Eq. 6: the complex SNR map p(t; f), here given as
  * a cross-power y with per-pixel standard deviation sigma, Appendix A).
  *   y_c64   complex64 [n_t][n_f], time-major (frequency fastest), interleaved re, im
- *   sigma   float32 [n_t][n_f], or [n_f] with STK_SIGMA_PER_FREQ; every value finite, > 0
+ *   sigma   float32 [n_t][n_f], or [n_f] with STK_SIGMA_PER_FREQ; every value > 0; +infinity
+ *           marks a notched pixel (the black lines of Fig. 1's caption): it adds nothing to
+ *           either sum (z = 0, w = 0, whatever y holds there); the paper form keeps n_t; a
+ *           template with no un-notched pixel scores 0
  *   n_t     time columns, >= 2 (a template has one pixel per column)
  *   n_f     frequency bins, >= 1; bin k has frequency f_min_hz + k * df_hz
  *   flags   STK_HOST_PTR | STK_SIGMA_PER_FREQ | STK_NORM_PAPER | STK_FP16
  * Statistic selected (Eq. 7 and the footnote to Eq. 5 allowing other weights):
  *   default         SNR = sum_j Re[e^{2 pi i f_j tau} y_j sigma_j^-2] / sqrt(sum_j sigma_j^-2)
  *   STK_NORM_PAPER  SNR = (1/n_t) sum_j Re[e^{2 pi i f_j tau} y_j / sigma_j]
- * Arithmetic: pixel magnitude and phase stored FP32 and Q0.32 turns (FP16 and
- * Q0.16 with STK_FP16), sums and normalisation FP32 (square root and
+ * Arithmetic: pixel magnitude and angle stored FP32 (FP16 and Q0.16 turns with
+ * STK_FP16), sums and normalisation FP32 (square root and
  * division rounded to nearest); the SNR is reported widened to FP64.  The delay phase
  * f tau mod 1 is exact in 64-bit fixed point per template; per pixel it is a
  * 32-bit turn, within 3e-6 rad for n_f <= 8192 (2^-32 turn beyond).
  * The library keeps its own packed copy; the caller may free y and sigma when
  * the call returns (it synchronises the stream).  Errors: STK_EINVAL (sizes,
- * NULL pointers, a non-finite y, sigma <= 0 or non-finite, f_min/df
+ * NULL pointers, a non-finite y at a pixel that is not notched, sigma <= 0 or NaN, f_min/df
  * non-finite or df <= 0, |y|/sigma above 65504 with STK_FP16), STK_ENOMEM, STK_ECUDA. */
 STK_API int stk_load_map(stk_ctx *ctx, const void *y_c64, const float *sigma, int n_t, int n_f,
                  double f_min_hz, double df_hz, unsigned flags, stk_map **out);

@@ -48,7 +48,8 @@ int flags_to_status(stk_ctx *c, int f)
     if (f & ERR_CANCELED) return set_err(c, STK_ECANCELED, "batch cancelled through stk_batch_cancel");
     if (f & ERR_BADTRACK) return set_err(c, STK_EINVAL, "explicit template with a control bin outside [0, n_f)");
     if (f & ERR_BADINPUT)
-        return set_err(c, STK_EINVAL, "stk_update_map data: y non-finite or sigma <= 0 or non-finite");
+        return set_err(c, STK_EINVAL, "stk_update_map data: y non-finite at a pixel that is not notched, or sigma "
+                                      "<= 0 or NaN");
     if (f & ERR_FP16_RANGE) return set_err(c, STK_EINVAL, "stk_update_map data: |y| / sigma exceeds 65504 (FP16)");
     return STK_OK;
 }
@@ -77,8 +78,17 @@ __global__ void pack_kernel(const float2 *__restrict__ y, const float *__restric
         const size_t q = (size_t)t * n_f + k;
         const float2 v = y[q];
         const float s = per_freq ? sigma[k] : sigma[q];
-        if (!isfinite(v.x) || !isfinite(v.y) || !(s > 0.f) || !isfinite(s)) flags |= ERR_BADINPUT;
         if (s != s0) flags |= FLAG_SIGMA_VARIES;
+        if (isinf(s) && s > 0.f) {  // notched pixel (sigma = +inf): no data, whatever y holds
+            rec[p] = make_uint2(0u, 0u);
+            if (wout) {
+                const float w = paper ? 1.f : 0.f;
+                if (!per_freq) wout[(size_t)t * ldw + k] = w;
+                else if (t == 0) wout[k] = w;
+            }
+            continue;
+        }
+        if (!isfinite(v.x) || !isfinite(v.y) || !(s > 0.f) || !isfinite(s)) flags |= ERR_BADINPUT;
         const float w = paper ? 1.f : 1.f / (s * s);
         const float h = hypotf(v.x, v.y);
         const float mag = paper ? h / s : h * w;
@@ -111,8 +121,16 @@ __global__ void pack_fp16_kernel(const float2 *__restrict__ y, const float *__re
         const size_t q = (size_t)t * n_f + k;
         const float2 v = y[q];
         const float s = per_freq ? sigma[k] : sigma[q];
-        if (!isfinite(v.x) || !isfinite(v.y) || !(s > 0.f) || !isfinite(s)) flags |= ERR_BADINPUT;
         if (s != s0) flags |= FLAG_SIGMA_VARIES;
+        if (isinf(s) && s > 0.f) {  // notched pixel (sigma = +inf): no data, whatever y holds
+            rec[p] = 0u;
+            if (rout) {
+                if (!per_freq) rout[(size_t)t * ldw + k] = 0.f;
+                else if (t == 0) rout[k] = 0.f;
+            }
+            continue;
+        }
+        if (!isfinite(v.x) || !isfinite(v.y) || !(s > 0.f) || !isfinite(s)) flags |= ERR_BADINPUT;
         const float h = hypotf(v.x, v.y) / s;
         if (!(h <= 65504.f)) flags |= ERR_FP16_RANGE;
         const float turns = atan2f(v.y, v.x) * 0.159154943091895336f;  // [-1/2, 1/2]
@@ -413,7 +431,8 @@ static int pack_into(stk_ctx *c, stk_map *m, const void *y_c64, const float *sig
     int fl = 0;
     int rc = read_err_flags(c, &fl);
     if (rc) return rc;
-    if (fl & ERR_BADINPUT) return set_err(c, STK_EINVAL, "y has a non-finite value or sigma is <= 0 or non-finite");
+    if (fl & ERR_BADINPUT)
+        return set_err(c, STK_EINVAL, "y has a non-finite value at a pixel that is not notched, or sigma is <= 0 or NaN");
     if (fl & ERR_FP16_RANGE) return set_err(c, STK_EINVAL, "FP16 storage: |y| / sigma exceeds 65504");
     if (paper) {
         d.wmode = WMODE_CONST;
@@ -430,7 +449,8 @@ static int pack_into(stk_ctx *c, stk_map *m, const void *y_c64, const float *sig
     // |y| / sigma0 (SNR = S r0 / sqrt(n_t r0^2) = S / sqrt(n_t)); paper form: S / n_t
     if (paper) d.norm = 1.0 / (double)n_t;
     else if (d.wmode == WMODE_CONST) d.norm = fp16 ? 1.0 / std::sqrt((double)n_t)
-                                                   : 1.0 / std::sqrt((double)n_t * (double)d.w_const);
+                                       : (d.w_const > 0.f ? 1.0 / std::sqrt((double)n_t * (double)d.w_const)
+                                                           : 0.0);   // every pixel notched: SNR 0
     else d.norm = 0.0;
     d.norm_f = (float)d.norm;
     d.rec = m->rec_buf;

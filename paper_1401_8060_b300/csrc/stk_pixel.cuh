@@ -79,11 +79,12 @@ __device__ __forceinline__ void accumulate(typename Pix<PREC>::Rec v, uint32_t b
 // form: S times the constant rounded to FP32 (within 2^-23 relative).  No FP64
 // arithmetic: this GPU issues FP64 operations at a small fraction of the FP32
 // rate, and a per-template FP64 normalisation cost 4.5 % of the scoring kernel.
+// A template whose pixels are all notched (sigma = +inf: W = 0) has no data and scores 0.
 template <int WMODE>
 __device__ __forceinline__ float finalize_snr(float acc, float W, const MapDev &m)
 {
     if (WMODE == WMODE_CONST || m.paper) return acc * m.norm_f;
-    return __fdiv_rn(acc, __fsqrt_rn(W));
+    return W > 0.f ? __fdiv_rn(acc, __fsqrt_rn(W)) : 0.f;
 }
 
 // ------------------------------------------------------------------ selection order

@@ -243,7 +243,7 @@ __global__ void __launch_bounds__(kInterpBlock) interp_kernel(MapDev m, InterpCo
     S = v[0];
     W = v[1];
     const bool varying = WMODE != WMODE_CONST && !m.paper;
-    const float scale = varying ? rsqrtf(W) : (float)m.norm;
+    const float scale = varying ? (W > 0.f ? rsqrtf(W) : 0.f) : (float)m.norm;   // W = 0: all notched
     if (MODE == 0 || snr_out) snr_out[i] = S * scale;
     if (!ADJOINT) return;
     const float gi = MODE == 2 ? 1.f : (g ? g[i] : 1.f);
@@ -405,7 +405,7 @@ template <int WMODE>
 __device__ __forceinline__ float polish_snr(const PolishSums &s, const MapDev &m)
 {
     if (WMODE == WMODE_CONST || m.paper) return s.S * m.norm_f;
-    return s.S * rsqrtf(s.W);
+    return s.W > 0.f ? s.S * rsqrtf(s.W) : 0.f;
 }
 
 // The delay maximising SNR near tau, within [-tau_max, tau_max]: Newton steps on

@@ -88,9 +88,11 @@ template <int WMODE, int PREC>
 __device__ __forceinline__ float finalize_general(float acc, float W, const MapDev &m, int N)
 {
     if (m.paper) return __fdiv_rn(acc, (float)N);
-    if (WMODE == WMODE_CONST)
-        return __fdiv_rn(acc, __fsqrt_rn(PREC == PREC_FP16 ? (float)N : __fmul_rn((float)N, m.w_const)));
-    return __fdiv_rn(acc, __fsqrt_rn(W));
+    if (WMODE == WMODE_CONST) {
+        const float Wc = PREC == PREC_FP16 ? (float)N : __fmul_rn((float)N, m.w_const);
+        return Wc > 0.f ? __fdiv_rn(acc, __fsqrt_rn(Wc)) : 0.f;   // every pixel notched: no data
+    }
+    return W > 0.f ? __fdiv_rn(acc, __fsqrt_rn(W)) : 0.f;
 }
 
 // One thread per template, in coherent order when perm is given (a warp's

@@ -557,6 +557,64 @@ def test_update_map_invalid_data_reported(ctx):
     mc.close()
 
 
+def _notched_map(seed, n_t, n_f, mode):
+    """A map with notched pixels (sigma = +inf, NaN data there): whole notched
+    lines with per-frequency sigma, lines and scattered pixels with per-pixel sigma."""
+    y, sig = rand_map(seed, n_t, n_f, mode)
+    rng = np.random.default_rng(seed + 1)
+    y, sig = y.copy(), sig.copy()
+    lines = rng.choice(n_f, max(1, n_f // 12), replace=False)
+    if sig.ndim == 1:
+        sig[lines] = np.inf
+        y[:, lines] = np.complex64(complex(np.nan, np.nan))
+    else:
+        notch = rng.random((n_t, n_f)) < 0.05
+        notch[:, lines] = True
+        sig[notch] = np.inf
+        y[notch] = np.complex64(complex(np.nan, np.nan))
+    return y, sig
+
+
+@pytest.mark.parametrize("mode,paper,fp16", [("freq", False, False), ("pixel", False, False), ("pixel", True, False),
+                                             ("freq", False, True)])
+def test_notched_pixels(ctx, mode, paper, fp16):
+    """Notched pixels (sigma = +inf) add nothing: both kernels, generated and
+    general templates, against the oracle; a fully notched map scores 0."""
+    n_t, n_f, T = 48, 240, 30000
+    y, sig = _notched_map(70, n_t, n_f, mode)
+    m = ctx.load_map(torch.from_numpy(y).cuda(), torch.from_numpy(sig).cuda(), 40.0, 0.5, paper_mode=paper,
+                     fp16=fp16)
+    om = oracle.OracleMap(y, sig, 40.0, 0.5, sig.ndim == 1, paper_mode=paper)
+    rtol = 3.5e-4 if fp16 else RTOL
+    ctx.set_tracks(T, 12, 3, 0.01)
+    o, sc = om.score_range_scale(12, 3, T, 0.01)
+    got = {}
+    for kernel in (1, 2):
+        ctx.set_option(_lib.STK_OPT_KERNEL, kernel)
+        try:
+            got[kernel] = ctx.score_all(m).cpu().numpy()
+        finally:
+            ctx.set_option(_lib.STK_OPT_KERNEL, 0)
+        bad = np.abs(got[kernel] - o) > rtol * np.maximum(np.abs(o), sc)
+        assert not bad.any(), (kernel, np.count_nonzero(bad))
+    np.testing.assert_array_equal(got[1], got[2])
+    ctx.set_template_shape(True, 6)
+    try:
+        ctx.set_tracks(5000, 13, 0, 0.01)
+        g = ctx.score_all(m).cpu().numpy()
+        og, sg = om.score_range_ext(13, 0, 5000, 0.01, general=True, t_min=6, with_scale=True)
+        assert np.all(np.abs(g - og) <= rtol * np.maximum(np.abs(og), sg))
+    finally:
+        ctx.set_template_shape(False)
+    m.close()
+    allnotch = np.full_like(sig, np.inf)
+    ma = ctx.load_map(torch.from_numpy(y).cuda(), torch.from_numpy(allnotch).cuda(), 40.0, 0.5, paper_mode=paper,
+                      fp16=fp16)
+    ctx.set_tracks(2000, 12, 0, 0.01)
+    assert np.all(ctx.score_all(ma).cpu().numpy() == 0.0)
+    ma.close()
+
+
 @pytest.mark.parametrize("kernel", [0, 1, 2])
 def test_single_template(ctx, kernel):
     """One template (the smallest range): both kernels, with and without the
@@ -581,7 +639,8 @@ def test_invalid_inputs_rejected(ctx):
     L = _lib
     y = np.ones((10, 8), np.complex64)
     s = np.ones(8, np.float32)
-    for bad_y, bad_s in [(y.copy(), np.zeros(8, np.float32)), (y.copy(), -s), (y.copy(), s * np.inf)]:
+    for bad_y, bad_s in [(y.copy(), np.zeros(8, np.float32)), (y.copy(), -s), (y.copy(), -s * np.inf),
+                         (y.copy(), s * np.nan)]:
         with pytest.raises(stk.StkError) as e:
             ctx.load_map(bad_y, bad_s, 40.0, 0.5)
         assert e.value.code == L.STK_EINVAL
