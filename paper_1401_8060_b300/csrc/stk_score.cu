@@ -141,13 +141,16 @@ __global__ void __launch_bounds__(256, 4) score_general_kernel(MapDev m, TrackSe
     // neighbours in the warp: when a flush happens changes nothing.
     float acc = 0.f, W = 0.f, acc_x = 0.f, W_x = 0.f;
     const uint32_t h_lo = hull_lo(f), h_hi = hull_hi(f);
+    // General-template maps have n_t <= 4096 and n_f <= 8192: 32-bit pixel indices
+    // and the narrow phase form (its 64-bit increment term is zero) always apply.
+    const uint32_t ldr = (uint32_t)m.ldr, ldw = (uint32_t)m.ldw;
     auto add = [&](int j, int32_t b, float &a_, float &w_) {
         if (kDebugBounds) b = (int32_t)checked_bin((uint32_t)b, j, m.n_t, h_lo, h_hi, err);
-        const auto v = Pix<PREC>::load_global(m.rec, (size_t)j * m.ldr + (uint32_t)b);
+        const auto v = Pix<PREC>::load_global(m.rec, (uint32_t)j * ldr + (uint32_t)b);
         float wv = 0.f;
         if (WMODE == WMODE_FREQ) wv = __ldg(m.w + b);
-        if (WMODE == WMODE_PIXEL) wv = __ldg(m.w + (size_t)j * m.ldw + b);
-        accumulate<PREC, WMODE>(v, (uint32_t)b, ph, wv, a_, w_);
+        if (WMODE == WMODE_PIXEL) wv = __ldg(m.w + ((uint32_t)j * ldw + (uint32_t)b));
+        pixel_add<PREC, WMODE>(v, template_turn_narrow((uint32_t)b, ph.a, ph.c), wv, a_, w_);
     };
     int np = 0, pj0 = 0, pj1 = 0, pj2 = 0, pj3 = 0;
     int32_t pb0 = 0, pb1 = 0, pb2 = 0, pb3 = 0;
@@ -172,10 +175,10 @@ __global__ void __launch_bounds__(256, 4) score_general_kernel(MapDev m, TrackSe
     using Rec = typename Pix<PREC>::Rec;
     auto gather = [&](int j, int32_t b, Rec &v, float &wv) {
         if (kDebugBounds) b = (int32_t)checked_bin((uint32_t)b, j, m.n_t, 0u, (uint32_t)m.n_f - 1u, err);
-        v = Pix<PREC>::load_global(m.rec, (size_t)j * m.ldr + (uint32_t)b);
+        v = Pix<PREC>::load_global(m.rec, (uint32_t)j * ldr + (uint32_t)b);
         wv = 0.f;
         if (WMODE == WMODE_FREQ) wv = __ldg(m.w + b);
-        if (WMODE == WMODE_PIXEL) wv = __ldg(m.w + (size_t)j * m.ldw + b);
+        if (WMODE == WMODE_PIXEL) wv = __ldg(m.w + ((uint32_t)j * ldw + (uint32_t)b));
     };
     add((int)t[0], (int32_t)f[0], acc, W);
     const int jend = (int)t[2];
@@ -189,10 +192,10 @@ __global__ void __launch_bounds__(256, 4) score_general_kernel(MapDev m, TrackSe
         float w0, w1;
         gather(j, b0, v0, w0);
         gather(j1, b1, v1, w1);
-        if (ok0) accumulate<PREC, WMODE>(v0, (uint32_t)b0, ph, w0, acc, W);
+        if (ok0) pixel_add<PREC, WMODE>(v0, template_turn_narrow((uint32_t)b0, ph.a, ph.c), w0, acc, W);
         else push(j, b0);
         if (has1) {
-            if (ok1) accumulate<PREC, WMODE>(v1, (uint32_t)b1, ph, w1, acc, W);
+            if (ok1) pixel_add<PREC, WMODE>(v1, template_turn_narrow((uint32_t)b1, ph.a, ph.c), w1, acc, W);
             else push(j1, b1);
         }
         if (__any_sync(__activemask(), np >= 3)) flush();  // room for the next step's two
