@@ -734,6 +734,11 @@ def main():
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32", "data": "synthetic",
+            "dtype_notes": "FP32 pixel records (|z| and the angle of z), FP32 sums; the normalisation S / sqrt(W) "
+                           "in FP32 with the square root and the division rounded to nearest (within 2^-23 of the "
+                           "quotient of the FP32 sums); SNRs widened to FP64 in the hits; FP64 only in each "
+                           "template's delay and its exact fixed-point phase constants",
+            "notes": "synthetic maps shaped like the paper's searches stand in for its LIGO data",
             "config": workload_config(fm, T, K, world, args.tracks),
             "roofline": {"bound": "smem", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
