@@ -528,9 +528,9 @@ def main():
             "frac_improved": float((hist[-1] > hist[0]).float().mean()),
             "discrete_snr_mean_before": float(np.mean(hits["snr"])),
             "discrete_snr_mean_after_rounding": float(np.mean(d_after)),
-            "kernels": "stk_refine: per step one launch computes the interpolated SNR, its gradient and the Adam "
-                       "step (32-128 threads per template, chosen by count; position and phase in fixed point)",
-            "roofline": data_path_roofline(16, float(K) * fm.n_t * 50, r0.elapsed_time(r1), peak, "interp_kernel",
+            "kernels": "stk_refine: one launch runs all 50 steps, each the interpolated SNR, its gradient and the "
+                       "Adam step (32-128 threads per template, chosen by count; position and phase in fixed point)",
+            "roofline": data_path_roofline(16, float(K) * fm.n_t * 50, r0.elapsed_time(r1), peak, "refine_kernel",
                                            "16 B per template-column per step (the two FP32 records that "
                                            "interpolation reads); gathers from L2 through the L1 data path"),
             "polish": {

@@ -239,7 +239,7 @@ STK_API int stk_score_explicit_general(stk_ctx *ctx, const stk_map *map, const u
  * f3_dev: float [n][3]; tau_dev: float [n] seconds; device memory, caller-owned.
  * Arithmetic is FP32 except the curve position and phase (fixed point, Q32.32
  * bins and Q0.64 turns).  A template with a control frequency of magnitude
- * 2^30 bins or more, or a non-finite one or delay, gets NaN. */
+ * 2^29 bins or more, or a non-finite one or delay, gets NaN. */
 
 /* snr_dev[i] = SNR of continuous template i (float [n]).  Errors: STK_EINVAL, STK_ECUDA. */
 STK_API int stk_interp_forward(stk_ctx *ctx, const stk_map *map, const float *f3_dev, const float *tau_dev,
@@ -262,8 +262,11 @@ STK_API int stk_interp_adjoint(stk_ctx *ctx, const stk_map *map, const float *f3
  * tau_dev float [n] (seconds) are device memory, caller-owned, updated in place.
  * hist_dev (optional, NULL to skip): float [steps + 1][n] device memory, row t
  * the SNRs before step t + 1 (row steps: after the last step).  Context scratch:
- * 36 bytes per template.  One launch per step (the statistic, its gradient and
- * the Adam step fused), plus 1, plus 1 when hist_dev is given.  Errors: STK_EINVAL (NULL pointer, steps < 0, tau_max <= 0, negative or
+ * 12 bytes per step.  One launch runs every step (each template's block loops
+ * over the steps: the statistic, its gradient and the Adam step fused, the
+ * parameters and moments in registers), after a host-to-device copy of the
+ * steps' bias-corrected step sizes (computed in FP64 on the host).
+ * Errors: STK_EINVAL (NULL pointer, steps < 0, tau_max <= 0, negative or
  * non-finite rates), STK_ENOMEM, STK_ECUDA. */
 STK_API int stk_refine(stk_ctx *ctx, const stk_map *map, float *f3_dev, float *tau_dev, uint64_t n, int steps,
                        float lr_bins, float lr_tau_frac, float tau_max, float *hist_dev);
@@ -427,8 +430,8 @@ STK_API int stk_score_noalloc(const stk_map *map, uint64_t n_tracks, uint64_t se
                                    (likelier with a small sample) makes the selection fall back to an
                                    exact radix select over every SNR, which is slower */
 #define STK_OPT_INTERP_THREADS 10 /* continuous templates (stk_interp_*, stk_refine): threads per
-                                     template, 0 (default: 128 up to 512 templates, 64 up to 1536,
-                                     else 32), 32, 64 or 128.  Results may differ in the last bits
+                                     template, 0 (default: 128 up to 1536 templates, else 32), 32,
+                                     64 or 128.  Results may differ in the last bits
                                      (the order of the column sums) */
 
 /* Set a tuning option for later scoring calls.  Errors: STK_EINVAL. */

@@ -789,7 +789,7 @@ int stk_refine(stk_ctx *c, const stk_map *m, float *f3, float *tau, uint64_t n, 
     if (n == 0) return STK_OK;
     if (!f3 || !tau) return set_err(c, STK_EINVAL, "NULL pointer");
     CUDA_TRY(c, cudaSetDevice(c->device));
-    int rc = ensure(c, &c->refine_buf, &c->refine_cap, refine_scratch_bytes(n));
+    int rc = ensure(c, &c->refine_buf, &c->refine_cap, refine_scratch_bytes(steps));
     if (rc) return rc;
     cudaError_t e = launch_refine(m->dev, f3, tau, n, steps, lr_bins, lr_tau_frac, tau_max, hist, c->refine_buf,
                                   c->interp_threads, c->d_err, c->stream);

@@ -10,18 +10,23 @@
 //   SNR = S / sqrt(W) (weighted) or S / N (paper form) -- Eq. 7 at integer bins.
 // The forward kernel returns SNR; the adjoint kernel returns g * dSNR/d(f0, f1,
 // f2, tau) for an upstream gradient g, differentiating each of those steps.
-// One block of 128 threads per template: thread l takes the columns j = l (mod
-// 128) in order; the lanes' partial sums meet in a fixed shuffle tree and the
-// four warps' sums are added in warp order (deterministic).  Sums and
-// the pixel arithmetic are FP32; the curve position x_j and the phase argument are
-// FP64, since FP32 resolves x_j ~ 10^3 only to 6e-5 bins.  FP64 is a slow pipe on
-// this GPU, so x_j advances by forward differences and only the position, its
-// split into bin and fraction, and the phase's turns use it.
+// P = 32, 64 or 128 threads per template: thread l takes the columns j = l (mod
+// P) in order; the lanes' partial sums meet in a fixed shuffle tree and the
+// template's warps' sums are added in warp order (deterministic).  Sums and the
+// pixel arithmetic are FP32.  The curve position x_j and the phase need more than
+// FP32 (which resolves x_j ~ 10^3 only to 6e-5 bins): a template's quadratic
+// coefficients are formed once per evaluation in FP64 (a slow pipe on this GPU,
+// so eight lanes share the work), and each thread's positions and phases follow
+// from them by exact fixed-point integer arithmetic.  The ascent runs all its
+// steps in one launch, each template's parameters and Adam moments held by its
+// thread 0.
 #include <cuda_fp16.h>
 
 #include <cmath>
 
 #include "stk_internal.cuh"
+#include <vector>
+
 #include "stk_pixel.cuh"
 #include "stk_refine.cuh"
 
@@ -63,116 +68,113 @@ struct InterpConst {
     int *err;  // deferred error flags (debug build: out-of-range gathers)
 };
 
-// Fused Adam step (refinement): the template's thread 0 takes the step from the
-// gradient it has just summed.  mom == nullptr: no step.
-struct AdamStep {
-    float *u;          // tau / tau_max, the ascent's delay coordinate
-    float4 *mom;       // first and second moments of (f0, f1, f2, u), two float4 a template
-    float step_f, step_u, sbc2, tau_max, f_hi;
+// One template's curve and phase coefficients for one evaluation, set up by
+// eight lanes of the block's first warp, one value a lane (FP64 is a slow pipe
+// on this GPU, so no other thread repeats it), and read by the template's threads
+// from shared memory:
+//   x(j) = C0 + C1 j + C2 j^2 bins, (C0, C1, C2) = (a0, a1, a2) / M^2, each a
+//     Q32.96 two's complement integer (lo, hi words), so that every thread's start
+//     position and forward differences follow in exact 128-bit integer arithmetic;
+//   phase(j) = tau0 + tau1 j + tau2 j^2 turns (mod 1), each Q0.64, with the phases
+//     at the band edges, where the clamped curve sits.
+struct TplSetup {
+    uint64_t ph[5];  // tau0, tau1, tau2, phase at bin 0, phase at bin n_f - 1
+    uint64_t c[6];   // C0, C1, C2 as (lo, hi)
+    float fa;        // turns per bin, df tau
+    int finite;      // control frequencies and delay within range
 };
 
-// One Adam step of the gradient ascent of a template's SNR (Adam with betas 0.9,
-// 0.999 and eps 1e-8 on the loss -SNR, in torch's arithmetic order), then the
-// projection onto f in [0, n_f - 1] and |u| <= 1.  step_f = lr_f / (1 - 0.9^t),
-// step_u likewise, sbc2 = sqrt(1 - 0.999^t), from the host.
-__device__ __forceinline__ void adam_update(const AdamStep &ad, uint64_t i, float *f3, float *tau, const float gs[4])
+// Lane q (0..7) of a template's setup: value q of TplSetup (0-4 the phase
+// coefficients, 5-7 C0..C2) from the template's control bins and delay (s).
+// |f| < 2^29 keeps C 2^32 within int64 and the positions within Q32.32 (|x| <=
+// max |f| by the convex hull); larger or non-finite control frequencies, or a
+// non-finite delay, mark the template, whose results are then NaN.
+__device__ __forceinline__ void setup_lane(const InterpConst &k, int n_f, float f0f, float f1f, float f2f,
+                                           float tauf, int q, TplSetup &su)
 {
-    const float w1 = 0.1f, b2 = 0.999f, w2 = 0.001f, eps = 1e-8f;
-    float4 m = ad.mom[2 * i], v = ad.mom[2 * i + 1];
-    float p[4] = {f3[3 * i], f3[3 * i + 1], f3[3 * i + 2], ad.u[i]};
-    float *mm = &m.x, *vv = &v.x;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const float g = -gs[q];                                   // d(-SNR)/d(f, u)
-        mm[q] = mm[q] + w1 * (g - mm[q]);
-        vv[q] = vv[q] * b2 + w2 * g * g;
-        const float denom = __fsqrt_rn(vv[q]) / ad.sbc2 + eps;
-        p[q] = p[q] - (q < 3 ? ad.step_f : ad.step_u) * (mm[q] / denom);
+    const float lim = 536870912.f;  // 2^29
+    const bool finite = fabsf(f0f) < lim && fabsf(f1f) < lim && fabsf(f2f) < lim && fabsf(tauf) < 1e30f;
+    const double f0 = f0f, f1 = f1f, f2 = f2f, tau = tauf;
+    const double M = k.M;
+    const double a2 = f0 - 2.0 * f1 + f2, a1 = 2.0 * M * (f1 - f0), a0 = M * M * f0;
+    const double fa = k.df * tau, fb = k.f_min * tau;  // turns per bin, turns at bin 0
+    const double base = (q == 0 || q == 5 ? a0 : (q == 1 || q == 6 ? a1 : a2)) * k.inv_M2;
+    if (q < 5) {
+        // tau0 = frac(fb + fa C0), tau1 = frac(fa C1), tau2 = frac(fa C2), then the
+        // phases at bins 0 and n_f - 1; signed [-1/2, 1/2] turn, as Q0.64
+        const double mul = q == 3 ? 0.0 : (q == 4 ? (double)(n_f - 1) : base);
+        const double add = q == 1 || q == 2 ? 0.0 : fb;
+        const double turns = add + fa * mul;
+        const double fr = turns - floor(turns);
+        su.ph[q] = finite ? (uint64_t)__double2ll_rn((fr - rint(fr)) * 9223372036854775808.0) << 1 : 0;
+    } else {
+        // C 2^96 = floor(C 2^32) 2^64 + frac(C 2^32) 2^64 (both parts exact)
+        const double sc = base * 4294967296.0;
+        const double h = floor(sc);
+        su.c[2 * (q - 5)] = finite ? __double2ull_rz((sc - h) * 18446744073709551616.0) : 0;
+        su.c[2 * (q - 5) + 1] = finite ? (uint64_t)__double2ll_rn(h) : 0;
     }
-    ad.mom[2 * i] = m;
-    ad.mom[2 * i + 1] = v;
-#pragma unroll
-    for (int q = 0; q < 3; ++q) f3[3 * i + q] = fminf(fmaxf(p[q], 0.f), ad.f_hi);
-    const float uu = fminf(fmaxf(p[3], -1.f), 1.f);
-    ad.u[i] = uu;
-    tau[i] = uu * ad.tau_max;
+    if (q == 0) {
+        su.fa = (float)fa;
+        su.finite = finite;
+    }
 }
 
-// P threads per template (32, 64 or 128), kInterpBlock / P templates a block.
-// MODE 0: forward (snr); 1: adjoint (g * gradient to gf3, gtau; snr too when
-// snr_out is given); 2: adjoint with g = 1 and the fused Adam step, parameters
-// updated in place (each template's parameters are read by its own threads
-// before the reduction and written by its thread 0 after it).
-template <int WMODE, int PREC, int MODE, int P>
-__global__ void __launch_bounds__(kInterpBlock) interp_kernel(MapDev m, InterpConst k, const float *f3,
-                                                              const float *tau_in, const float *__restrict__ g,
-                                                              uint64_t n, float *__restrict__ snr_out,
-                                                              float *__restrict__ gf3, float *__restrict__ gtau,
-                                                              AdamStep ad)
+// The template's setup by the first 8 TPB threads of the block, then a barrier.
+template <int TPB, typename Params>
+__device__ __forceinline__ void setup_block(const InterpConst &k, int n_f, TplSetup *su, Params params)
 {
-    constexpr bool ADJOINT = MODE != 0;
-    constexpr int TPB = kInterpBlock / P;  // templates a block
-    constexpr int WPT = P / 32;            // warps a template
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int t = tid % P;                  // thread within the template
-    const uint64_t i_raw = (uint64_t)blockIdx.x * TPB + tid / P;
-    const bool valid = i_raw < n;           // no early return: the block meets at a barrier below
-    const uint64_t i = valid ? i_raw : n - 1;
-    const double f0 = f3[3 * i], f1 = f3[3 * i + 1], f2 = f3[3 * i + 2];
-    const double tau = tau_in[i];
-    const int n_t = m.n_t, n_f = m.n_f;
-    const double M = k.M, inv_M2 = k.inv_M2;
-    const double a2 = f0 - 2.0 * f1 + f2, a1 = 2.0 * M * (f1 - f0), a0 = M * M * f0;
-    const double fa = k.df * tau, fb = k.f_min * tau;     // turns per bin, turns at bin 0
-    const float two_pi = 6.28318530717958647692f;
-    // Column j, j + P, ... of this thread by forward differences (x(j + P) - x(j) =
-    // (a2 (2 P j + P^2) + a1 P) / M^2, second difference 2 P^2 a2 / M^2), in fixed
-    // point so the column loop has no FP64 arithmetic (a slow pipe on this GPU):
-    // the position X = x 2^32 (Q32.32) and the phase T = frac(fb + fa x) 2^64
-    // (Q0.64, wrapping), each a quadratic in j, advance by exact integer additions.
-    // The position's differences are rounded once from FP64, so after s steps it is
-    // within about s^2 2^-33 bins (s <= n_t / P); the phase is exact given its
-    // coefficients, each within 2^-64 turn.  |x| <= max |f| by the convex hull, so |f| < 2^30 keeps X in range;
-    // larger or non-finite control frequencies give NaN.
-    const bool finite = fabs(f0) < 1073741824.0 && fabs(f1) < 1073741824.0 && fabs(f2) < 1073741824.0 &&
-                        fabs(tau) < 1e30;
-    const double jl = (double)t, Pd = (double)P;
-    const double x_t = finite ? ((a2 * jl + a1) * jl + a0) * inv_M2 : 0.0;
-    const double dx = finite ? (a2 * (2.0 * Pd * jl + Pd * Pd) + a1 * Pd) * inv_M2 : 0.0;
-    const double ddx = finite ? 2.0 * Pd * Pd * a2 * inv_M2 : 0.0;
-    const double two32 = 4294967296.0;
-    int64_t X = __double2ll_rn(x_t * two32), DX = __double2ll_rn(dx * two32);
-    const int64_t DDX = __double2ll_rn(ddx * two32);
-    // The phase is a quadratic in j modulo one turn: T(j) = tau0 + tau1 j + tau2 j^2
-    // with tau0 = frac(fb + fa C0), tau1 = frac(fa C1), tau2 = frac(fa C2) and
-    // x(j) = C0 + C1 j + C2 j^2.  The template's thread 0 converts them to Q0.64
-    // (FP64, once a template); every thread's start value and differences follow
-    // in wrapping 64-bit integer arithmetic, exact given the three coefficients.
-    __shared__ uint64_t tq[TPB][5];  // tau0, tau1, tau2, and the phases at the band edges
-    const int tl = tid / P;
-    if (t == 0) {
-        auto q64 = [](double turns) {                      // frac(turns) as Q0.64
-            const double fr = turns - floor(turns);        // [0, 1]
-            return (uint64_t)__double2ll_rn(ldexp(fr - rint(fr), 63)) << 1;  // signed [-1/2, 1/2] turn
-        };
-        tq[tl][0] = finite ? q64(fb + fa * (a0 * inv_M2)) : 0;
-        tq[tl][1] = finite ? q64(fa * (a1 * inv_M2)) : 0;
-        tq[tl][2] = finite ? q64(fa * (a2 * inv_M2)) : 0;
-        tq[tl][3] = finite ? q64(fb) : 0;
-        tq[tl][4] = finite ? q64(fb + fa * (double)(n_f - 1)) : 0;
+    const int tid = threadIdx.x;
+    if (tid < 8 * TPB) {
+        float f0, f1, f2, tau;
+        params(tid >> 3, f0, f1, f2, tau);
+        setup_lane(k, n_f, f0, f1, f2, tau, tid & 7, su[tid >> 3]);
     }
-    if (WPT > 1) __syncthreads();
-    else __syncwarp();  // one warp a template: its lane 0 wrote, its lanes read
-    const uint64_t tau1 = tq[tl][1], tau2 = tq[tl][2], T_lo = tq[tl][3], T_hi = tq[tl][4];
+    __syncthreads();
+}
+
+typedef unsigned __int128 u128;
+
+__device__ __forceinline__ u128 q96(const uint64_t *c) { return ((u128)c[1] << 64) | c[0]; }
+
+// Q32.96 to Q32.32, rounded (two's complement, wrapping).
+__device__ __forceinline__ uint64_t q96_to_q32(u128 v) { return (uint64_t)((v + ((u128)1 << 63)) >> 64); }
+
+// One evaluation of a template by its P threads (thread t takes the columns
+// j = t (mod P) in order; the lanes' partial sums meet in a fixed shuffle tree,
+// the template's warps' sums are added in warp order: deterministic).  Every
+// thread of the block calls it (it has a barrier when P > 32).  Returns true on
+// the template's thread 0, with snr and, when ADJOINT, gi * dSNR/d(f0, f1, f2, tau).
+template <int WMODE, int PREC, bool ADJOINT, int P>
+__device__ __forceinline__ bool interp_step(const MapDev &m, const InterpConst &k, const TplSetup &su, int t,
+                                            float gi, float &snr, float gr[4])
+{
+    constexpr int WPT = P / 32;  // warps a template
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int n_t = m.n_t, n_f = m.n_f;
+    const float two_pi = 6.28318530717958647692f;
+    // Columns j, j + P, ... of this thread by forward differences in fixed point,
+    // so the column loop has no FP64 arithmetic: the position X = x 2^32 (Q32.32)
+    // and the phase T = phase 2^64 (Q0.64, wrapping) advance by integer additions.
+    // The start x(t) and the differences x(t + P) - x(t) = C1 P + C2 (2 P t + P^2)
+    // and 2 P^2 C2 are exact in Q32.96 and rounded once to Q32.32, so after s steps
+    // the position is within about s^2 2^-33 bins (s <= n_t / P); the phase is exact
+    // given its coefficients, each within 2^-64 turn.
+    const u128 C0 = q96(su.c), C1 = q96(su.c + 2), C2 = q96(su.c + 4);
     const uint64_t tt = (uint64_t)t, PP = (uint64_t)P;
-    uint64_t T = tq[tl][0] + tau1 * tt + tau2 * (tt * tt);
+    uint64_t X = q96_to_q32(C0 + C1 * tt + C2 * (tt * tt));
+    uint64_t DX = q96_to_q32(C1 * PP + C2 * (2 * PP * tt + PP * PP));
+    const uint64_t DDX = q96_to_q32(C2 * (2 * PP * PP));
+    const uint64_t tau1 = su.ph[1], tau2 = su.ph[2], T_lo = su.ph[3], T_hi = su.ph[4];
+    uint64_t T = su.ph[0] + tau1 * tt + tau2 * (tt * tt);
     uint64_t DT = tau1 * PP + tau2 * (2 * PP * tt + PP * PP);
     const uint64_t DDT = tau2 * (2 * PP * PP);
+    const float fa = su.fa;
     const int64_t X_hi = (int64_t)(n_f - 1) << 32;
     float S = 0.f, W = 0.f;
     float dS0 = 0.f, dS1 = 0.f, dS2 = 0.f, dS3 = 0.f, dW0 = 0.f, dW1 = 0.f, dW2 = 0.f;
     for (int j = t; j < n_t; j += P) {
-        int64_t Xc = X;
+        int64_t Xc = (int64_t)X;
         uint64_t Tc = T;
         X += DX;
         DX += DDX;
@@ -198,7 +200,7 @@ __global__ void __launch_bounds__(kInterpBlock) interp_kernel(MapDev m, InterpCo
         W += w;
         if (ADJOINT) {
             // d re/dx = -im 2 pi df tau + Re[e^{i phi} dz/dx]; d re/dtau = -im 2 pi f
-            const float dre_dx = clamped ? 0.f : fmaf(-im, two_pi * (float)fa, cs * dzr - sn * dzi);
+            const float dre_dx = clamped ? 0.f : fmaf(-im, two_pi * fa, cs * dzr - sn * dzi);
             const float dw_dx = clamped ? 0.f : dw;
             const float u = (float)j * k.inv_Mf, c0 = (1.f - u) * (1.f - u), c1 = 2.f * (1.f - u) * u, c2 = u * u;
             dS0 = fmaf(dre_dx, c0, dS0);
@@ -236,38 +238,162 @@ __global__ void __launch_bounds__(kInterpBlock) interp_kernel(MapDev m, InterpCo
                 v[q] = a;
             }
     }
-    if (t != 0 || !valid) return;
-    if (!finite)
+    if (t != 0) return false;
+    if (!su.finite)
 #pragma unroll
         for (int q = 0; q < NV; ++q) v[q] = __int_as_float(0x7fc00000);  // NaN
     S = v[0];
     W = v[1];
     const bool varying = WMODE != WMODE_CONST && !m.paper;
     const float scale = varying ? (W > 0.f ? rsqrtf(W) : 0.f) : (float)m.norm;   // W = 0: all notched
-    if (MODE == 0 || snr_out) snr_out[i] = S * scale;
-    if (!ADJOINT) return;
-    const float gi = MODE == 2 ? 1.f : (g ? g[i] : 1.f);
-    float gr[4];
-    if (varying) {
-        const float h = 0.5f * S * scale * scale * scale;
-        gr[0] = gi * (v[2 % NV] * scale - h * v[6 % NV]);
-        gr[1] = gi * (v[3 % NV] * scale - h * v[7 % NV]);
-        gr[2] = gi * (v[4 % NV] * scale - h * v[8 % NV]);
-    } else {
-        gr[0] = gi * v[2 % NV] * scale;
-        gr[1] = gi * v[3 % NV] * scale;
-        gr[2] = gi * v[4 % NV] * scale;
+    snr = S * scale;
+    if (ADJOINT) {
+        if (varying) {
+            const float h = 0.5f * S * scale * scale * scale;
+            gr[0] = gi * (v[2 % NV] * scale - h * v[6 % NV]);
+            gr[1] = gi * (v[3 % NV] * scale - h * v[7 % NV]);
+            gr[2] = gi * (v[4 % NV] * scale - h * v[8 % NV]);
+        } else {
+            gr[0] = gi * v[2 % NV] * scale;
+            gr[1] = gi * v[3 % NV] * scale;
+            gr[2] = gi * v[4 % NV] * scale;
+        }
+        gr[3] = gi * v[5 % NV] * scale;
     }
-    gr[3] = gi * v[5 % NV] * scale;
-    if (MODE == 2) {
-        const float gs[4] = {gr[0], gr[1], gr[2], gr[3] * ad.tau_max};  // dSNR/d(f0, f1, f2, u)
-        adam_update(ad, i, const_cast<float *>(f3), const_cast<float *>(tau_in), gs);
-        return;
+    return true;
+}
+
+// P threads per template (32, 64 or 128), kInterpBlock / P templates a block.
+// MODE 0: forward (snr); 1: adjoint (g * gradient to gf3, gtau; snr too when
+// snr_out is given).
+template <int WMODE, int PREC, int MODE, int P>
+__global__ void __launch_bounds__(kInterpBlock) interp_kernel(MapDev m, InterpConst k, const float *__restrict__ f3,
+                                                              const float *__restrict__ tau,
+                                                              const float *__restrict__ g, uint64_t n,
+                                                              float *__restrict__ snr_out, float *__restrict__ gf3,
+                                                              float *__restrict__ gtau)
+{
+    constexpr int TPB = kInterpBlock / P;
+    constexpr bool ADJOINT = MODE != 0;
+    __shared__ TplSetup su[TPB];
+    const uint64_t first = (uint64_t)blockIdx.x * TPB;
+    setup_block<TPB>(k, m.n_f, su, [&](int tl, float &f0, float &f1, float &f2, float &tv) {
+        const uint64_t i = first + tl < n ? first + tl : n - 1;  // the last block's spare slots repeat one
+        f0 = f3[3 * i];
+        f1 = f3[3 * i + 1];
+        f2 = f3[3 * i + 2];
+        tv = tau[i];
+    });
+    const int tl = threadIdx.x / P, t = threadIdx.x % P;
+    const uint64_t i = first + tl;
+    const float gi = ADJOINT && g && t == 0 && i < n ? g[i] : 1.f;
+    float snr, gr[4];
+    if (!interp_step<WMODE, PREC, ADJOINT, P>(m, k, su[tl], t, gi, snr, gr) || i >= n) return;
+    if (!ADJOINT || snr_out) snr_out[i] = snr;
+    if (ADJOINT) {
+        gf3[3 * i] = gr[0];
+        gf3[3 * i + 1] = gr[1];
+        gf3[3 * i + 2] = gr[2];
+        gtau[i] = gr[3];
     }
-    gf3[3 * i] = gr[0];
-    gf3[3 * i + 1] = gr[1];
-    gf3[3 * i + 2] = gr[2];
-    gtau[i] = gr[3];
+}
+
+// Step sizes of one Adam step and the projection's bounds.
+struct AdamStep {
+    float step_f, step_u, sbc2, tau_max, f_hi;
+};
+
+// One Adam step of the gradient ascent of a template's SNR (Adam with betas 0.9,
+// 0.999 and eps 1e-8 on the loss -SNR, in torch's arithmetic order) on p = (f0,
+// f1, f2, u = tau / tau_max) with moments mo, ve, then the projection onto f in
+// [0, n_f - 1] and |u| <= 1.  step_f = lr_f / (1 - 0.9^t), step_u likewise, sbc2
+// = sqrt(1 - 0.999^t), from the host.
+__device__ __forceinline__ void adam_update(const AdamStep &ad, float p[4], float mo[4], float ve[4],
+                                            const float gs[4])
+{
+    const float w1 = 0.1f, b2 = 0.999f, w2 = 0.001f, eps = 1e-8f;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const float g = -gs[q];                                   // d(-SNR)/d(f, u)
+        mo[q] = mo[q] + w1 * (g - mo[q]);
+        ve[q] = ve[q] * b2 + w2 * g * g;
+        const float denom = __fsqrt_rn(ve[q]) / ad.sbc2 + eps;
+        p[q] = p[q] - (q < 3 ? ad.step_f : ad.step_u) * (mo[q] / denom);
+    }
+#pragma unroll
+    for (int q = 0; q < 3; ++q) p[q] = fminf(fmaxf(p[q], 0.f), ad.f_hi);
+    p[3] = fminf(fmaxf(p[3], -1.f), 1.f);
+}
+
+// The whole ascent in one launch.  Templates are independent, so each block runs
+// every step for its own: the template's thread 0 keeps the parameters and Adam's
+// moments in registers and publishes (f0, f1, f2, tau) in shared memory for the
+// next step's setup; a barrier ends each step.  step_consts[s] = (lr_f / (1 -
+// 0.9^(s+1)), lr_u / (1 - 0.9^(s+1)), sqrt(1 - 0.999^(s+1))), from the host.
+// hist (optional): [steps + 1][n] SNRs, row s before step s + 1, row steps after
+// the last.
+template <int WMODE, int PREC, int P>
+__global__ void __launch_bounds__(kInterpBlock) refine_kernel(MapDev m, InterpConst k, float *__restrict__ f3,
+                                                              float *__restrict__ tau, uint64_t n, int steps,
+                                                              const float3 *__restrict__ step_consts, AdamStep ad,
+                                                              float *__restrict__ hist)
+{
+    constexpr int TPB = kInterpBlock / P;
+    __shared__ TplSetup su[TPB];
+    __shared__ float par[TPB][4];  // f0, f1, f2, tau of each template's current step
+    const int tl = threadIdx.x / P, t = threadIdx.x % P;
+    const uint64_t i_raw = (uint64_t)blockIdx.x * TPB + tl;
+    const bool valid = i_raw < n;
+    const uint64_t i = valid ? i_raw : n - 1;  // the last block's spare slots repeat one, writing nothing
+    float p[4] = {0.f, 0.f, 0.f, 0.f}, mo[4] = {0.f, 0.f, 0.f, 0.f}, ve[4] = {0.f, 0.f, 0.f, 0.f};
+    if (t == 0) {
+        const float tv = tau[i];
+        p[0] = f3[3 * i];
+        p[1] = f3[3 * i + 1];
+        p[2] = f3[3 * i + 2];
+        p[3] = tv / ad.tau_max;
+        par[tl][0] = p[0];
+        par[tl][1] = p[1];
+        par[tl][2] = p[2];
+        par[tl][3] = tv;
+    }
+    __syncthreads();
+    auto params = [&](int sl, float &f0, float &f1, float &f2, float &tv) {
+        f0 = par[sl][0];
+        f1 = par[sl][1];
+        f2 = par[sl][2];
+        tv = par[sl][3];
+    };
+    float snr, gr[4];
+    for (int s = 0; s < steps; ++s) {
+        // the step's SNR (history row s), its gradient and the update
+        setup_block<TPB>(k, m.n_f, su, params);
+        if (interp_step<WMODE, PREC, true, P>(m, k, su[tl], t, 1.f, snr, gr)) {
+            if (hist && valid) hist[(size_t)s * n + i] = snr;
+            const float3 c = step_consts[s];
+            AdamStep st = ad;
+            st.step_f = c.x;
+            st.step_u = c.y;
+            st.sbc2 = c.z;
+            const float gs[4] = {gr[0], gr[1], gr[2], gr[3] * ad.tau_max};  // dSNR/d(f0, f1, f2, u)
+            adam_update(st, p, mo, ve, gs);
+            par[tl][0] = p[0];
+            par[tl][1] = p[1];
+            par[tl][2] = p[2];
+            par[tl][3] = p[3] * ad.tau_max;
+        }
+        __syncthreads();
+    }
+    if (t == 0 && valid && steps > 0) {
+        f3[3 * i] = par[tl][0];
+        f3[3 * i + 1] = par[tl][1];
+        f3[3 * i + 2] = par[tl][2];
+        tau[i] = par[tl][3];
+    }
+    if (!hist) return;
+    setup_block<TPB>(k, m.n_f, su, params);
+    if (interp_step<WMODE, PREC, false, P>(m, k, su[tl], t, 1.f, snr, gr) && valid)
+        hist[(size_t)steps * n + i] = snr;
 }
 
 InterpConst interp_const(const MapDev &m, int *err)
@@ -285,22 +411,20 @@ InterpConst interp_const(const MapDev &m, int *err)
 }
 
 // Threads per template: 0 picks by the template count.  More threads per template
-// fill the GPU when templates are few; each thread also repeats part of the
-// template's setup, so with many templates one warp each is fastest (50 ascent
-// steps on the 500 x 1600 map, ms, for 32 / 64 / 128 threads: 256 templates
-// 0.78 / 0.69 / 0.57, 1024: 0.98 / 0.98 / 0.98, 4096: 1.93 / 2.19 / 3.00,
-// 16384: 5.43 / 7.13 / 10.5).
+// fill the GPU when templates are few; with many, one warp each is fastest (50
+// ascent steps on the 500 x 1600 map with history, ms, for 32 / 64 / 128 threads:
+// 256 templates 0.47 / 0.30 / 0.23, 1024: 0.52 / 0.37 / 0.31, 2048: 0.56 / 0.66 /
+// 0.57, 3072: 0.66 / 0.74 / 0.84, 4096: 0.73 / 1.00 / 1.09, 16384: 2.64 / 3.31 /
+// 4.04).
 int interp_threads(uint64_t n, int P)
 {
     if (P == 32 || P == 64 || P == 128) return P;
-    if (n <= 512) return 128;
-    if (n <= 1536) return 64;
-    return 32;
+    return n <= 1536 ? 128 : 32;
 }
 
 template <int MODE, int P>
 cudaError_t launch_interp_P(const MapDev &m, const float *f3, const float *tau, const float *g, uint64_t n,
-                            float *snr, float *gf3, float *gtau, const AdamStep &ad, int *err, cudaStream_t st)
+                            float *snr, float *gf3, float *gtau, int *err, cudaStream_t st)
 {
     constexpr uint64_t TPB = kInterpBlock / P;
     const uint64_t blocks = (n + TPB - 1) / TPB;
@@ -308,7 +432,7 @@ cudaError_t launch_interp_P(const MapDev &m, const float *f3, const float *tau, 
     const unsigned b = (unsigned)blocks;
     const InterpConst k = interp_const(m, err);
 #define STK_INTERP(W, PR) \
-    interp_kernel<W, PR, MODE, P><<<b, kInterpBlock, 0, st>>>(m, k, f3, tau, g, n, snr, gf3, gtau, ad)
+    interp_kernel<W, PR, MODE, P><<<b, kInterpBlock, 0, st>>>(m, k, f3, tau, g, n, snr, gf3, gtau)
     if (m.prec == PREC_FP16) {
         if (m.wmode == WMODE_CONST) STK_INTERP(WMODE_CONST, PREC_FP16);
         else if (m.wmode == WMODE_FREQ) STK_INTERP(WMODE_FREQ, PREC_FP16);
@@ -324,23 +448,13 @@ cudaError_t launch_interp_P(const MapDev &m, const float *f3, const float *tau, 
 
 template <int MODE>
 cudaError_t launch_interp_M(const MapDev &m, const float *f3, const float *tau, const float *g, uint64_t n,
-                            float *snr, float *gf3, float *gtau, const AdamStep &ad, int P, int *err, cudaStream_t st)
+                            float *snr, float *gf3, float *gtau, int P, int *err, cudaStream_t st)
 {
     switch (interp_threads(n, P)) {
-    case 128: return launch_interp_P<MODE, 128>(m, f3, tau, g, n, snr, gf3, gtau, ad, err, st);
-    case 64: return launch_interp_P<MODE, 64>(m, f3, tau, g, n, snr, gf3, gtau, ad, err, st);
-    default: return launch_interp_P<MODE, 32>(m, f3, tau, g, n, snr, gf3, gtau, ad, err, st);
+    case 128: return launch_interp_P<MODE, 128>(m, f3, tau, g, n, snr, gf3, gtau, err, st);
+    case 64: return launch_interp_P<MODE, 64>(m, f3, tau, g, n, snr, gf3, gtau, err, st);
+    default: return launch_interp_P<MODE, 32>(m, f3, tau, g, n, snr, gf3, gtau, err, st);
     }
-}
-
-__global__ void __launch_bounds__(256) refine_init_kernel(const float *__restrict__ tau, float *__restrict__ u,
-                                                          float4 *__restrict__ st, uint64_t n, float tau_max)
-{
-    const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    u[i] = tau[i] / tau_max;
-    st[2 * i] = make_float4(0.f, 0.f, 0.f, 0.f);
-    st[2 * i + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
 // ------------------------------------------------------------------ discrete follow-up
@@ -545,43 +659,72 @@ __global__ void __launch_bounds__(kPolishBlock) polish_kernel(MapDev m, uint32_t
 
 }  // namespace
 
-size_t refine_scratch_bytes(uint64_t n)
+size_t refine_scratch_bytes(int steps)
 {
-    return (size_t)n * (sizeof(float4) * 2 + sizeof(float));  // moments, u
+    return (size_t)(steps > 0 ? steps : 1) * sizeof(float3);  // the steps' step sizes
 }
+
+namespace {
+
+template <int P>
+cudaError_t launch_refine_P(const MapDev &m, float *f3, float *tau, uint64_t n, int steps, const float3 *consts,
+                            const AdamStep &ad, float *hist, int *err, cudaStream_t st)
+{
+    constexpr uint64_t TPB = kInterpBlock / P;
+    const uint64_t blocks = (n + TPB - 1) / TPB;
+    if (blocks > 0x7fffffffull) return cudaErrorInvalidValue;
+    const unsigned b = (unsigned)blocks;
+    const InterpConst k = interp_const(m, err);
+#define STK_REFINE(W, PR) \
+    refine_kernel<W, PR, P><<<b, kInterpBlock, 0, st>>>(m, k, f3, tau, n, steps, consts, ad, hist)
+    if (m.prec == PREC_FP16) {
+        if (m.wmode == WMODE_CONST) STK_REFINE(WMODE_CONST, PREC_FP16);
+        else if (m.wmode == WMODE_FREQ) STK_REFINE(WMODE_FREQ, PREC_FP16);
+        else STK_REFINE(WMODE_PIXEL, PREC_FP16);
+    } else {
+        if (m.wmode == WMODE_CONST) STK_REFINE(WMODE_CONST, PREC_FP32);
+        else if (m.wmode == WMODE_FREQ) STK_REFINE(WMODE_FREQ, PREC_FP32);
+        else STK_REFINE(WMODE_PIXEL, PREC_FP32);
+    }
+#undef STK_REFINE
+    return cudaGetLastError();
+}
+
+}  // namespace
 
 cudaError_t launch_refine(const MapDev &m, float *f3, float *tau, uint64_t n, int steps, float lr_f, float lr_u,
                           float tau_max, float *hist, void *scratch, int P, int *err, cudaStream_t st)
 {
     if (n == 0 || steps < 0) return cudaSuccess;
     AdamStep ad{};
-    ad.mom = static_cast<float4 *>(scratch);
-    ad.u = reinterpret_cast<float *>(ad.mom + 2 * n);
     ad.tau_max = tau_max;
     ad.f_hi = (float)(m.n_f - 1);
-    refine_init_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(tau, ad.u, ad.mom, n, tau_max);
-    cudaError_t e = cudaGetLastError();
-    for (int t = 1; t <= steps && e == cudaSuccess; ++t) {
-        // the step's SNR (history row t - 1), its gradient and the update, in one launch
-        const double bc1 = 1.0 - std::pow(0.9, t), bc2 = 1.0 - std::pow(0.999, t);
-        ad.step_f = (float)(lr_f / bc1);
-        ad.step_u = (float)(lr_u / bc1);
-        ad.sbc2 = (float)std::sqrt(bc2);
-        e = launch_interp_M<2>(m, f3, tau, nullptr, n, hist ? hist + (size_t)(t - 1) * n : nullptr, nullptr,
-                               nullptr, ad, P, err, st);
+    float3 *consts = static_cast<float3 *>(scratch);
+    if (steps > 0) {
+        // bias-corrected step sizes of every step, in FP64 on the host (Adam, betas 0.9 and 0.999)
+        std::vector<float3> hc((size_t)steps);
+        for (int t = 1; t <= steps; ++t) {
+            const double bc1 = 1.0 - std::pow(0.9, t), bc2 = 1.0 - std::pow(0.999, t);
+            hc[t - 1] = make_float3((float)(lr_f / bc1), (float)(lr_u / bc1), (float)std::sqrt(bc2));
+        }
+        // pageable source: the call returns once the data are staged
+        const cudaError_t e = cudaMemcpyAsync(consts, hc.data(), sizeof(float3) * (size_t)steps,
+                                              cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) return e;
     }
-    if (e == cudaSuccess && hist)
-        e = launch_interp_M<0>(m, f3, tau, nullptr, n, hist + (size_t)steps * n, nullptr, nullptr, AdamStep{}, P,
-                               err, st);
-    return e;
+    switch (interp_threads(n, P)) {
+    case 128: return launch_refine_P<128>(m, f3, tau, n, steps, consts, ad, hist, err, st);
+    case 64: return launch_refine_P<64>(m, f3, tau, n, steps, consts, ad, hist, err, st);
+    default: return launch_refine_P<32>(m, f3, tau, n, steps, consts, ad, hist, err, st);
+    }
 }
 
 cudaError_t launch_interp_tuned(const MapDev &m, const float *f3, const float *tau, const float *g, uint64_t n,
                                 float *snr, float *gf3, float *gtau, bool adjoint, int P, int *err, cudaStream_t st)
 {
     if (n == 0) return cudaSuccess;
-    return adjoint ? launch_interp_M<1>(m, f3, tau, g, n, snr, gf3, gtau, AdamStep{}, P, err, st)
-                   : launch_interp_M<0>(m, f3, tau, g, n, snr, gf3, gtau, AdamStep{}, P, err, st);
+    return adjoint ? launch_interp_M<1>(m, f3, tau, g, n, snr, gf3, gtau, P, err, st)
+                   : launch_interp_M<0>(m, f3, tau, g, n, snr, gf3, gtau, P, err, st);
 }
 
 cudaError_t launch_polish(const MapDev &m, uint32_t *f3, double *tau, const float *alt_f3, const float *alt_tau,

@@ -9,9 +9,9 @@ namespace stk {
 // Gradient ascent of n continuous templates' interpolated SNR: `steps` Adam steps
 // (lr_f in bins, lr_u in units of tau_max) with f3 and tau updated in place and
 // projected onto f in [0, n_f - 1], |tau| <= tau_max; hist (optional) gets
-// [steps + 1][n] SNRs.  Scratch: refine_scratch_bytes(n), 16-byte aligned.
-// P: threads per template (32, 64, 128; 0 chooses by n).
-size_t refine_scratch_bytes(uint64_t n);
+// [steps + 1][n] SNRs.  Scratch: refine_scratch_bytes(steps), 16-byte aligned.
+// P: threads per template (32, 64, 128; 0 chooses by n).  One launch for all steps.
+size_t refine_scratch_bytes(int steps);
 cudaError_t launch_refine(const MapDev &m, float *f3, float *tau, uint64_t n, int steps, float lr_f, float lr_u,
                           float tau_max, float *hist, void *scratch, int P, int *err, cudaStream_t st);
 

@@ -268,7 +268,7 @@ def test_refine_edge_cases(ctx):
     # zero learning rates leave the parameters where they are
     fz, tz, _ = ctx.refine(m, f3, tau, TAU_MAX, steps=4, lr_bins=0.0, lr_tau_frac=0.0)
     assert torch.equal(fz, f3) and torch.allclose(tz, tau, rtol=1e-6, atol=0)
-    # control frequencies beyond 2^30 bins or non-finite, or a non-finite delay: NaN, the others unaffected
+    # control frequencies beyond 2^29 bins or non-finite, or a non-finite delay: NaN, the others unaffected
     fw, tw = f3[:4].clone(), tau[:4].clone()
     fw[0, 1], fw[1, 2], tw[2] = 2.0 ** 31, float("nan"), float("inf")
     sw = ctx.interp_forward(m, fw, tw)
