@@ -540,9 +540,10 @@ def main():
                 "frac_improved": float(np.mean(gain > 0)),
                 "kept": {"start": int(np.sum(which_p == 0)), "polished_start": int(np.sum(which_p == 1)),
                          "polished_refined": int(np.sum(which_p == 2))},
-                "kernel": "stk_polish: one warp per template climbs the discrete statistic (Newton on the delay "
-                          "at fixed pixels, +-1 bin moves); the scorer's own SNR picks among start, polished "
-                          "start and polished refined template"}}
+                "kernel": "stk_polish: one block per template, six warps climbing the discrete statistic from the "
+                          "start and six from the refined template (Newton on the delay at fixed pixels; the six "
+                          "+-1 bin moves of a round one per warp); the scorer's own SNR picks among start, "
+                          "polished start and polished refined template"}}
         ctx.set_profiling(True)
 
     # 256 ragged maps in one persistent launch vs 256 sequential single-map launches

@@ -273,14 +273,17 @@ STK_API int stk_refine(stk_ctx *ctx, const stk_map *map, float *f3_dev, float *t
 
 /* Discrete follow-up of the loudest templates (Sec. V): the refined templates
  * are judged by the discrete statistic of Eq. 7, so this call climbs it directly.
- * For each of n templates, one warp: the delay moves to the nearest maximum of
- * SNR(tau) at the template's fixed pixels (the weight sum does not depend on
- * tau and S(tau) is smooth: safeguarded Newton steps, each at most a tenth of
- * the band's shortest period and kept only when the SNR rises), then each
- * control bin moves by +-1 while a move, with its delay maximised again, raises
- * the SNR, at most `moves` moves.  With alt_f3_dev / alt_tau_dev (continuous
- * templates, e.g. stk_refine's output; rounded to the nearest bins and clamped)
- * the alternative is climbed too.  The template kept is the start, the polished
+ * For each of n templates: the delay moves to the nearest maximum of SNR(tau)
+ * at the template's fixed pixels (the weight sum does not depend on tau and
+ * S(tau) is smooth: safeguarded Newton steps, each at most a tenth of the band's
+ * shortest period and kept only when the SNR rises), then the control bins take
+ * +-1 moves, each round the best of the six moves (its delay maximised again)
+ * while it raises the SNR (the first in the order bin 0 -1, bin 0 +1, bin 1 -1,
+ * ... among equals), at most `moves` rounds.  With alt_f3_dev / alt_tau_dev
+ * (continuous templates, e.g. stk_refine's output; rounded to the nearest bins
+ * and clamped, a NaN bin as 0 and a NaN delay as the start's) the alternative is
+ * climbed too.  One block of twelve warps a template: six climb from the start
+ * and six from the alternative, one move a warp.  The template kept is the start, the polished
  * start or the polished alternative, whichever scores highest by the scorer's
  * own arithmetic (the SNR stk_score_explicit returns; the start wins ties), so
  * no template leaves with a lower SNR than it came with.

@@ -47,21 +47,35 @@ struct Pix<PREC_FP16> {  // low half: arg in Q0.16 turns; high half: FP16 |y|/si
 // 2 pi), |z| and w = sigma^-2 as stored.  FP16 records: the Q0.16 angle joins
 // the turn in integer arithmetic (exact mod 1 turn); the record holds |y|/sigma
 // and wv = 1/sigma, so |z| = mag wv and the weight is wv^2.
+// pixel_term forms the pixel's factors (|z|, cosine), pixel_sum adds them and the
+// weight; pixel_add is the two in a row.
+template <int PREC, int WMODE>
+__device__ __forceinline__ void pixel_term(typename Pix<PREC>::Rec v, uint32_t T, float wv, float &mg, float &c)
+{
+    if constexpr (PREC == PREC_FP32) {
+        c = __cosf(fmaf((float)(int32_t)T, kTurnToRad, Pix<PREC_FP32>::arg_rad(v)));
+        mg = Pix<PREC_FP32>::mag(v);
+    } else {
+        const uint32_t t = T + ((uint32_t)v << 16);
+        c = __cosf((float)(int32_t)t * kTurnToRad);
+        mg = Pix<PREC_FP16>::mag(v);
+        if (WMODE != WMODE_CONST) mg *= wv;
+    }
+}
+
+template <int PREC, int WMODE>
+__device__ __forceinline__ void pixel_sum(float mg, float c, float wv, float &acc, float &W)
+{
+    acc = fmaf(mg, c, acc);
+    if (WMODE != WMODE_CONST) W = PREC == PREC_FP32 ? W + wv : fmaf(wv, wv, W);
+}
+
 template <int PREC, int WMODE>
 __device__ __forceinline__ void pixel_add(typename Pix<PREC>::Rec v, uint32_t T, float wv, float &acc, float &W)
 {
-    if constexpr (PREC == PREC_FP32) {
-        const float x = fmaf((float)(int32_t)T, kTurnToRad, Pix<PREC_FP32>::arg_rad(v));
-        acc = fmaf(Pix<PREC_FP32>::mag(v), __cosf(x), acc);
-        if (WMODE != WMODE_CONST) W += wv;
-    } else {
-        const uint32_t t = T + ((uint32_t)v << 16);
-        const float c = __cosf((float)(int32_t)t * kTurnToRad);
-        float mg = Pix<PREC_FP16>::mag(v);
-        if (WMODE != WMODE_CONST) mg *= wv;
-        acc = fmaf(mg, c, acc);
-        if (WMODE != WMODE_CONST) W = fmaf(wv, wv, W);
-    }
+    float mg, c;
+    pixel_term<PREC, WMODE>(v, T, wv, mg, c);
+    pixel_sum<PREC, WMODE>(mg, c, wv, acc, W);
 }
 
 // The same pixel for a template phase given in full (64-bit increment for wide maps).

@@ -459,17 +459,20 @@ cudaError_t launch_interp_M(const MapDev &m, const float *f3, const float *tau, 
 
 // ------------------------------------------------------------------ discrete follow-up
 // The refined continuous templates are judged by the discrete statistic (Eq. 7
-// on whole pixels).  The polish climbs that statistic directly, one warp per
-// template: the delay is set to the nearest maximum of SNR(tau) at the
-// template's fixed pixels (W does not depend on tau; S(tau) = sum_j |z_j|
-// cos(2 pi f_j tau + arg z_j) is smooth, so safeguarded Newton steps on S find
-// it), then each control bin moves by +-1 while a move, with its delay again
-// maximised, raises the SNR.  The climb compares warp sums (any summation
-// order); the choice among the start, the polished start and the polished
-// alternative uses the scorer's own sequential sum, so it never returns a
-// template that scores below the start.
-constexpr int kPolishBlock = 128;   // 4 warps, one template each
-constexpr int kPolishNewton = 4;    // Newton steps per delay search
+// on whole pixels).  The polish climbs that statistic directly: the delay is set
+// to the nearest maximum of SNR(tau) at the template's fixed pixels (W does not
+// depend on tau; S(tau) = sum_j |z_j| cos(2 pi f_j tau + arg z_j) is smooth, so
+// safeguarded Newton steps on S find it), then each control bin moves by +-1
+// while a move, with its delay again maximised, raises the SNR.  One block a
+// template: two groups of six warps climb from the start and from the
+// alternative side by side, and within a group each warp tries one of the six
+// moves (3 control bins x +-1), so a move costs one delay search instead of six.
+// The climb compares warp sums (any summation order); the choice among the
+// start, the polished start and the polished alternative uses the scorer's own
+// sequential sum, so it never returns a template that scores below the start.
+constexpr int kPolishWarps = 6;                       // a climb's warps: one per move
+constexpr int kPolishBlock = 2 * kPolishWarps * 32;   // the two climbs
+constexpr int kPolishNewton = 4;                      // Newton steps per delay search
 
 struct PolishSums {
     float S, dS, d2S, W;
@@ -525,7 +528,7 @@ __device__ __forceinline__ float polish_snr(const PolishSums &s, const MapDev &m
 // The delay maximising SNR near tau, within [-tau_max, tau_max]: Newton steps on
 // S where it is concave, else a step towards increasing S, each at most a tenth
 // of the shortest period in the band and kept only when the SNR rises (else
-// halved, twice).  Returns the SNR at the returned delay.
+// halved, twice).  One warp; returns the SNR at the returned delay.
 template <int WMODE, int PREC>
 __device__ __forceinline__ float polish_delay(const MapDev &m, const uint32_t f[3], double &tau, double tau_max, int lane,
                                               int *err)
@@ -558,53 +561,94 @@ __device__ __forceinline__ float polish_delay(const MapDev &m, const uint32_t f[
     return snr;
 }
 
-// Hill climb from (f, tau): delay first, then +-1 moves of the control bins.
-template <int WMODE, int PREC>
-__device__ __forceinline__ void polish_climb(const MapDev &m, uint32_t f[3], double &tau, double tau_max, int moves, int lane,
-                                             int *err)
+struct PolishSlot {
+    double tau;
+    float snr;
+};
+
+// Barrier of one climb's six warps (named barrier 1 + group).
+__device__ __forceinline__ void group_sync(int group)
 {
-    float snr = polish_delay<WMODE, PREC>(m, f, tau, tau_max, lane, err);
+    asm volatile("bar.sync %0, %1;" ::"r"(1 + group), "r"(kPolishWarps * 32) : "memory");
+}
+
+// Hill climb from (f, tau) by one group (warp gw of six): the delay first (warp
+// 0), then rounds of the six +-1 moves, one a warp, each with its delay
+// maximised; the first strictly best of them in the order (bin 0, -1), (bin 0,
+// +1), (bin 1, -1), ... is taken while it beats the current SNR.  f and tau end
+// the same in every thread of the group.
+template <int WMODE, int PREC>
+__device__ __forceinline__ void polish_climb(const MapDev &m, uint32_t f[3], double &tau, double tau_max, int moves,
+                                             int group, int gw, int lane, PolishSlot *slot, int *err)
+{
+    if (gw == 0) {
+        double t = tau;
+        const float s = polish_delay<WMODE, PREC>(m, f, t, tau_max, lane, err);
+        if (lane == 0) {
+            slot[0].tau = t;
+            slot[0].snr = s;
+        }
+    }
+    group_sync(group);
+    float snr = slot[0].snr;
+    tau = slot[0].tau;
+    group_sync(group);  // read before the slots are reused
+    const int k = gw >> 1;
+    const uint32_t d = (gw & 1) ? 1u : ~0u;  // +1 or -1 (selects below keep f and g in registers)
     for (int mv = 0; mv < moves; ++mv) {
-        uint32_t bf[3] = {f[0], f[1], f[2]};
-        double bt = tau;
+        float sn = -INFINITY;
+        double t = tau;
+        const uint32_t fk = k == 0 ? f[0] : (k == 1 ? f[1] : f[2]);
+        if (!((gw & 1) == 0 && fk == 0) && !((gw & 1) && fk + 1 >= (uint32_t)m.n_f)) {
+            const uint32_t g[3] = {f[0] + (k == 0 ? d : 0u), f[1] + (k == 1 ? d : 0u), f[2] + (k == 2 ? d : 0u)};
+            sn = polish_delay<WMODE, PREC>(m, g, t, tau_max, lane, err);
+        }
+        if (lane == 0) {
+            slot[gw].tau = t;
+            slot[gw].snr = sn;
+        }
+        group_sync(group);
+        int best = -1;
         float bs = snr;
 #pragma unroll
-        for (int k = 0; k < 3; ++k)
-#pragma unroll
-            for (int d = -1; d <= 1; d += 2) {
-                if ((d < 0 && f[k] == 0) || (d > 0 && f[k] + 1 >= (uint32_t)m.n_f)) continue;
-                uint32_t g[3] = {f[0], f[1], f[2]};
-                g[k] += (uint32_t)d;
-                double t = tau;
-                const float sn = polish_delay<WMODE, PREC>(m, g, t, tau_max, lane, err);
-                if (sn > bs) {
-                    bf[0] = g[0]; bf[1] = g[1]; bf[2] = g[2];
-                    bt = t;
-                    bs = sn;
-                }
+        for (int q = 0; q < kPolishWarps; ++q)
+            if (slot[q].snr > bs) {
+                bs = slot[q].snr;
+                best = q;
             }
-        if (!(bs > snr)) break;
-        f[0] = bf[0]; f[1] = bf[1]; f[2] = bf[2];
+        const double bt = best >= 0 ? slot[best].tau : tau;
+        group_sync(group);
+        if (best < 0) break;
+#pragma unroll
+        for (int q = 0; q < 3; ++q) f[q] += (best >> 1) == q ? ((best & 1) ? 1u : ~0u) : 0u;
         tau = bt;
         snr = bs;
     }
 }
 
-// The scorer's SNR of one template: columns in order, one thread, the same
-// per-pixel arithmetic and normalisation as stk_score_explicit (bit-identical).
+// The scorer's SNR of one template, bit-identical to stk_score_explicit: the
+// warp's lanes form the pixels' factors 32 columns at a time and every lane adds
+// them in column order, as the scorer's single thread does.
 template <int WMODE, int PREC>
-__device__ __forceinline__ float polish_canonical(const MapDev &m, const uint32_t f[3], double tau, int *err)
+__device__ __forceinline__ float polish_canonical(const MapDev &m, const uint32_t f[3], double tau, int lane, int *err)
 {
     const Phase ph = phase_consts(m.f_min, m.df, tau, m.n_f);
     float acc = 0.f, W = 0.f;
-    for (int j = 0; j < m.n_t; ++j) {
-        uint32_t b = raster_bin_wide(f[0], f[1], f[2], m.M, (uint32_t)j, m.d);
-        if (kDebugBounds) b = checked_bin(b, j, m.n_t, hull_lo(f), hull_hi(f), err);
-        const typename Pix<PREC>::Rec v = Pix<PREC>::load_global(m.rec, (size_t)j * m.ldr + b);
-        float wv = 0.f;
-        if (WMODE == WMODE_FREQ) wv = __ldg(m.w + b);
-        if (WMODE == WMODE_PIXEL) wv = __ldg(m.w + (size_t)j * m.ldw + b);
-        accumulate<PREC, WMODE>(v, b, ph, wv, acc, W);
+    for (int j0 = 0; j0 < m.n_t; j0 += 32) {
+        const int j = j0 + lane;
+        float mg = 0.f, c = 0.f, wv = 0.f;
+        if (j < m.n_t) {
+            uint32_t b = raster_bin_wide(f[0], f[1], f[2], m.M, (uint32_t)j, m.d);
+            if (kDebugBounds) b = checked_bin(b, j, m.n_t, hull_lo(f), hull_hi(f), err);
+            const typename Pix<PREC>::Rec v = Pix<PREC>::load_global(m.rec, (size_t)j * m.ldr + b);
+            if (WMODE == WMODE_FREQ) wv = __ldg(m.w + b);
+            if (WMODE == WMODE_PIXEL) wv = __ldg(m.w + (size_t)j * m.ldw + b);
+            pixel_term<PREC, WMODE>(v, template_turn(b, ph), wv, mg, c);
+        }
+        const int cnt = min(32, m.n_t - j0);
+        for (int q = 0; q < cnt; ++q)
+            pixel_sum<PREC, WMODE>(__shfl_sync(0xffffffffu, mg, q), __shfl_sync(0xffffffffu, c, q),
+                                   __shfl_sync(0xffffffffu, wv, q), acc, W);
     }
     return finalize_snr<WMODE>(acc, W, m);
 }
@@ -617,42 +661,60 @@ __global__ void __launch_bounds__(kPolishBlock) polish_kernel(MapDev m, uint32_t
                                                               double tau_max, int moves, double *__restrict__ snr_out,
                                                               int *__restrict__ which_out, int *err)
 {
-    const uint64_t i = (uint64_t)blockIdx.x * (kPolishBlock / 32) + (threadIdx.x >> 5);
-    const int lane = threadIdx.x & 31;
-    if (i >= n) return;   // whole warps leave together
+    __shared__ PolishSlot slots[2][kPolishWarps];
+    __shared__ uint32_t cf[3][3];   // candidates: start, polished start, polished alternative
+    __shared__ double ct[3];
+    __shared__ float cs[3];
+    const uint64_t i = blockIdx.x;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int group = warp / kPolishWarps, gw = warp % kPolishWarps;
     const uint32_t fs[3] = {min(f3[3 * i], (uint32_t)m.n_f - 1), min(f3[3 * i + 1], (uint32_t)m.n_f - 1),
                             min(f3[3 * i + 2], (uint32_t)m.n_f - 1)};
     const double ts = tau[i];
-    uint32_t fa[3] = {fs[0], fs[1], fs[2]};
-    double ta = fmin(fmax(ts, -tau_max), tau_max);
-    polish_climb<WMODE, PREC>(m, fa, ta, tau_max, moves, lane, err);
-    uint32_t fb[3] = {fa[0], fa[1], fa[2]};
-    double tb = ta;
-    if (alt_f3) {
+    const double ts_c = fmin(fmax(ts, -tau_max), tau_max);
+    if (group == 0 || alt_f3) {
+        uint32_t f[3] = {fs[0], fs[1], fs[2]};
+        double t = ts_c;
+        if (group == 1) {
 #pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            const float x = alt_f3[3 * i + k];
-            const float r = rintf(fminf(fmaxf(x == x ? x : 0.f, 0.f), (float)(m.n_f - 1)));
-            fb[k] = (uint32_t)r;
+            for (int k = 0; k < 3; ++k) {
+                const float x = alt_f3[3 * i + k];
+                f[k] = (uint32_t)rintf(fminf(fmaxf(x == x ? x : 0.f, 0.f), (float)(m.n_f - 1)));
+            }
+            const double ta = (double)alt_tau[i];
+            if (ta == ta) t = fmin(fmax(ta, -tau_max), tau_max);   // NaN: the start's delay
         }
-        const double t = (double)alt_tau[i];
-        tb = t == t ? fmin(fmax(t, -tau_max), tau_max) : ta;
-        polish_climb<WMODE, PREC>(m, fb, tb, tau_max, moves, lane, err);
+        polish_climb<WMODE, PREC>(m, f, t, tau_max, moves, group, gw, lane, slots[group], err);
+        if (gw == 0 && lane == 0) {
+            cf[1 + group][0] = f[0];
+            cf[1 + group][1] = f[1];
+            cf[1 + group][2] = f[2];
+            ct[1 + group] = t;
+        }
     }
-    if (lane != 0) return;
+    if (threadIdx.x == 0) {
+        cf[0][0] = fs[0];
+        cf[0][1] = fs[1];
+        cf[0][2] = fs[2];
+        ct[0] = ts;
+    }
+    __syncthreads();
     // the choice, by the scorer's own sums: the start unless a polished form beats it
-    const float s0 = polish_canonical<WMODE, PREC>(m, fs, ts, err);
-    const float s1 = polish_canonical<WMODE, PREC>(m, fa, ta, err);
-    const float s2 = alt_f3 ? polish_canonical<WMODE, PREC>(m, fb, tb, err) : s1;
+    const int nc = alt_f3 ? 3 : 2;
+    if (warp < nc) {
+        const float s = polish_canonical<WMODE, PREC>(m, cf[warp], ct[warp], lane, err);
+        if (lane == 0) cs[warp] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
     int w = 0;
-    float best = s0;
-    if (s1 > best) { w = 1; best = s1; }
-    if (alt_f3 && s2 > best) { w = 2; best = s2; }
-    const uint32_t *fo = w == 0 ? fs : (w == 1 ? fa : fb);
-    f3[3 * i] = fo[0];
-    f3[3 * i + 1] = fo[1];
-    f3[3 * i + 2] = fo[2];
-    tau[i] = w == 0 ? ts : (w == 1 ? ta : tb);
+    float best = cs[0];
+    if (cs[1] > best) { w = 1; best = cs[1]; }
+    if (alt_f3 && cs[2] > best) { w = 2; best = cs[2]; }
+    f3[3 * i] = cf[w][0];
+    f3[3 * i + 1] = cf[w][1];
+    f3[3 * i + 2] = cf[w][2];
+    tau[i] = ct[w];
     if (snr_out) snr_out[i] = (double)best;
     if (which_out) which_out[i] = w;
 }
@@ -731,10 +793,8 @@ cudaError_t launch_polish(const MapDev &m, uint32_t *f3, double *tau, const floa
                           uint64_t n, double tau_max, int moves, double *snr, int *which, int *err, cudaStream_t st)
 {
     if (n == 0) return cudaSuccess;
-    constexpr uint64_t TPB = kPolishBlock / 32;
-    const uint64_t blocks = (n + TPB - 1) / TPB;
-    if (blocks > 0x7fffffffull) return cudaErrorInvalidValue;
-    const unsigned b = (unsigned)blocks;
+    if (n > 0x7fffffffull) return cudaErrorInvalidValue;
+    const unsigned b = (unsigned)n;  // one block a template
 #define STK_POLISH(W, PR) \
     polish_kernel<W, PR><<<b, kPolishBlock, 0, st>>>(m, f3, tau, alt_f3, alt_tau, n, tau_max, moves, snr, which, err)
     if (m.prec == PREC_FP16) {
