@@ -297,6 +297,14 @@ int stk_create(stk_ctx **out, int device, void *cuda_stream)
     cudaMemset(c->d_err, 0, sizeof(int));
     for (auto &ev : c->ev) cudaEventCreate(&ev);
     cudaEventCreateWithFlags(&c->stream_mark, cudaEventDisableTiming);
+    // the order's key table (module memory of this device; every context writes the
+    // same values, and the synchronisation below completes them before any use)
+    if (order_build_tables(c->stream) != cudaSuccess) {
+        cudaFree(c->d_err);
+        cudaFree(c->hits_dev);
+        delete c;
+        return set_err(nullptr, STK_ECUDA, "order table build failed");
+    }
     cudaDeviceSynchronize();
     *out = c;
     return STK_OK;

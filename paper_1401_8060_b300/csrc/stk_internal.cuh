@@ -614,6 +614,9 @@ void order_shape(int n_f, int max_bits, int &shift, int &bits);
 void order_plan_maps(OrderMap *maps, int n_maps, uint32_t &nc, uint32_t &max_fbits);
 size_t order_scratch_bytes_maps(uint64_t total_n, uint32_t nc, int num_sms);
 cudaError_t order_prepare(uint32_t nc, uint32_t max_fbits);
+// Fills the order's Hilbert key table on the current device (every context, before
+// its first order pass; the values never change).
+cudaError_t order_build_tables(cudaStream_t st);
 cudaError_t launch_order_batch(const OrderMap *d_maps, int n_maps, uint64_t total_n, uint32_t nc, uint32_t max_fbits,
                                void *scratch, int num_sms, cudaStream_t st, const uint32_t **perm_out,
                                int *launches);

@@ -125,6 +125,30 @@ __device__ __forceinline__ uint32_t hilbert3(uint32_t x0, uint32_t x1, uint32_t 
     return (spread3(X[0]) << 2) | (spread3(X[1]) << 1) | spread3(X[2]);
 }
 
+// Hilbert indices of every cell at 1..7 bits a coordinate, so the keys kernel
+// looks a key up (one 4-byte gather from a 9.6 MB table that stays in L2)
+// instead of running the transform: bits b start at hilbert_tab_offset(b), cell
+// (x0, x1, x2) at (x0 << 2b) | (x1 << b) | x2.  Filled once per device by
+// order_build_tables from hilbert3 itself, so the keys are those of the
+// transform.
+constexpr int kHilbertTabBits = 7;
+__host__ __device__ constexpr uint32_t hilbert_tab_offset(int b)
+{
+    return (uint32_t)(((1ull << (3 * b)) - 8ull) / 7ull);  // sum of 8^i for i = 1 .. b - 1
+}
+constexpr uint32_t kHilbertTabEntries = hilbert_tab_offset(kHilbertTabBits + 1);
+__device__ uint32_t g_hilbert_tab[kHilbertTabEntries];
+
+__global__ void __launch_bounds__(256) hilbert_table_kernel()
+{
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < kHilbertTabEntries; i += gridDim.x * blockDim.x) {
+        int b = 1;
+        while (i >= hilbert_tab_offset(b + 1)) ++b;
+        const uint32_t c = i - hilbert_tab_offset(b), mask = (1u << b) - 1u;
+        g_hilbert_tab[i] = hilbert3(c >> (2 * b), (c >> b) & mask, c & mask, b);
+    }
+}
+
 // Key of one template: Hilbert index of its control bins (general templates: the
 // start and end column above a Morton code of the bins), split into coarse bucket
 // and fine bits.
@@ -143,7 +167,9 @@ __device__ __forceinline__ uint32_t template_key(const TrackSet &ts, uint64_t g,
         key |= (((t[0] >> tshift) << tbits) | (t[2] >> tshift)) << (3 * kGenBinBits);
     } else {
         const uint32_t mid = (f[0] + 2 * f[1] + f[2]) >> 2;
-        key = hilbert3(f[0] >> shift, mid >> shift, f[2] >> shift, bbits);
+        key = bbits > 0 ? __ldg(g_hilbert_tab + hilbert_tab_offset(bbits) +
+                                (((f[0] >> shift) << (2 * bbits)) | ((mid >> shift) << bbits) | (f[2] >> shift)))
+                        : 0u;
     }
     const uint32_t c = coarse0 + (key >> fbits);
     return (c << kFineShift) | (key & ((1u << fbits) - 1u));
@@ -523,6 +549,12 @@ cudaError_t run_order(const OrderArgs &oa, uint32_t max_fbits, void *scratch, cu
 
 
 }  // namespace
+
+cudaError_t order_build_tables(cudaStream_t st)
+{
+    hilbert_table_kernel<<<(kHilbertTabEntries + 255) / 256, 256, 0, st>>>();
+    return cudaGetLastError();
+}
 
 // Shared-memory limits of the order kernels on the current device (not while a
 // stream is being captured: batches call this before capturing their graph).
