@@ -560,7 +560,11 @@ cudaError_t order_build_tables(cudaStream_t st)
 // stream is being captured: batches call this before capturing their graph).
 cudaError_t order_prepare(uint32_t nc, uint32_t max_fbits)
 {
-    const int smem_c = (int)nc * 4, smem_f = 4 << max_fbits;
+    // the largest any pass may ask for, whatever this one needs: a later pass (or
+    // a graph captured later) never finds a limit lowered by an earlier one
+    (void)nc;
+    (void)max_fbits;
+    const int smem_c = (int)kMaxCoarse * 4, smem_f = 4 << kFineShift;
     cudaError_t e;
     if ((e = cudaFuncSetAttribute(order_keys_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   smem_c)) != cudaSuccess ||
