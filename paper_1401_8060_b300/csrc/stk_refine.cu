@@ -220,9 +220,33 @@ __device__ __forceinline__ bool interp_step(const MapDev &m, const InterpConst &
         v[2 % NV] = dS0; v[3 % NV] = dS1; v[4 % NV] = dS2; v[5 % NV] = dS3;
         v[6 % NV] = dW0; v[7 % NV] = dW1; v[8 % NV] = dW2;
     }
+    if (!ADJOINT) {
 #pragma unroll
-    for (int q = 0; q < NV; ++q)
-        for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
+        for (int q = 0; q < NV; ++q)
+            for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
+    } else {
+        // The same butterfly (lane l adds lane l ^ o at o = 16, 8, 4, 2, 1, so every
+        // lane ends with the same sums), transposed: each level sends half of the
+        // values still held, and the lanes with bit o set keep the upper half.  Value
+        // q ends in lanes 2q and 2q + 1, from where lane 0 fetches it: 25 shuffles
+        // instead of 45.
+        float u[16];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) u[q] = q < NV ? v[q % NV] : 0.f;
+#pragma unroll
+        for (int o = 16, h = 8; o > 1; o >>= 1, h >>= 1) {
+            const bool up = (lane & o) != 0;
+#pragma unroll
+            for (int q = 0; q < h; ++q) {
+                const float send = up ? u[q] : u[q + h];
+                const float keep = up ? u[q + h] : u[q];
+                u[q] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+            }
+        }
+        u[0] += __shfl_xor_sync(0xffffffffu, u[0], 1);
+#pragma unroll
+        for (int q = 0; q < NV; ++q) v[q] = __shfl_sync(0xffffffffu, u[0], 2 * q);
+    }
     if (WPT > 1) {
         // the template's warps' sums, added in warp order by its thread 0
         __shared__ float red[kInterpBlock / 32][NV];
