@@ -362,6 +362,34 @@ def test_polish_never_loses_and_matches_oracle(ctx, mode, fp16):
     m.close()
 
 
+def test_polish_non_finite_alternatives(ctx):
+    """A NaN alternative bin counts as bin 0 and a NaN alternative delay as the
+    start's delay: the polish still returns templates inside the map and the delay
+    range, never below the start, and the same as with those bins given as 0."""
+    n_t, n_f, T, k = 120, 300, 20_000, 64
+    y, sig = _map("freq", n_t, n_f, 41)
+    m = ctx.load_map(torch.from_numpy(y).cuda(), torch.from_numpy(sig).cuda(), 40.0, 0.5)
+    ctx.set_tracks(T, 9, 0, TAU_MAX)
+    hits = ctx.score(m, k)
+    f_start = np.array([list(v) for v in hits["f"]], dtype=np.int64)
+    t_start = hits["tau"].copy()
+    alt_f = f_start.astype(np.float32) + 0.4
+    alt_t = t_start.astype(np.float32)
+    alt_f[::3, 1] = np.nan
+    alt_t[1::3] = np.nan
+    f1, t1, s1, w1 = (x.cpu().numpy() for x in ctx.polish(m, f_start, t_start, TAU_MAX, alt_f3=alt_f,
+                                                            alt_tau=alt_t, moves=4))
+    assert np.all((f1 >= 0) & (f1 < n_f)) and np.all(np.abs(t1) <= TAU_MAX)
+    assert np.all(s1 >= hits["snr"]), np.min(s1 - hits["snr"])
+    # the NaN bins replaced by 0 as documented
+    exp_f = np.where(np.isnan(alt_f), 0.0, alt_f).astype(np.float32)
+    f2, t2, s2, w2 = (x.cpu().numpy() for x in ctx.polish(m, f_start, t_start, TAU_MAX, alt_f3=exp_f,
+                                                            alt_tau=alt_t, moves=4))
+    for a, b in ((f1, f2), (t1, t2), (s1, s2), (w1, w2)):
+        np.testing.assert_array_equal(a, b)
+    m.close()
+
+
 def test_polish_invalid_inputs(ctx):
     y, sig = _map("freq", 40, 64, 3)
     m = ctx.load_map(torch.from_numpy(y).cuda(), torch.from_numpy(sig).cuda(), 40.0, 0.5)
