@@ -86,6 +86,39 @@ def test_forward_and_adjoint_vs_oracle(ctx, mode, paper, fp16):
         assert np.all(np.abs(got - ref) <= tol), (q, np.max(np.abs(got - ref) / np.max(np.abs(ref))))
 
 
+@pytest.mark.parametrize("threads", [32, 128])
+def test_long_and_wide_maps_vs_oracle(ctx, threads):
+    """Long maps (3000 columns: each thread's position and phase advance over up
+    to 94 steps from starts formed in 128-bit fixed point) and a wide band (8000
+    bins, steep curves) against the FP64 oracle, forward and adjoint."""
+    from paper_1401_8060_b300 import _lib
+    ctx.set_option(_lib.STK_OPT_INTERP_THREADS, threads)
+    try:
+        for n_t, n_f, n in ((3000, 60, 48), (40, 8000, 96)):
+            y, sig = _map("freq", n_t, n_f, 60 + n_t)
+            m = ctx.load_map(torch.from_numpy(y).cuda(), torch.from_numpy(sig).cuda(), 40.0, 0.5)
+            om = oracle.OracleMap(y, sig, 40.0, 0.5, True)
+            rng = np.random.default_rng(n_t)
+            f3 = rng.uniform(0, n_f - 1, (n, 3)).astype(np.float32)
+            tau = rng.uniform(-TAU_MAX, TAU_MAX, n).astype(np.float32)
+            f3t, taut = torch.from_numpy(f3).cuda(), torch.from_numpy(tau).cuda()
+            snr = ctx.interp_forward(m, f3t, taut).cpu().numpy()
+            gf, gt = ctx.interp_adjoint(m, f3t, taut, torch.ones(n, device="cuda"))
+            gf, gt = gf.cpu().numpy(), gt.cpu().numpy()
+            o, og = om.interp_score(f3.astype(np.float64), tau.astype(np.float64), grad=True)
+            _, ex = om.score_explicit(np.clip(np.round(f3), 0, n_f - 1).astype(np.uint32), tau.astype(np.float64),
+                                      extras=True)
+            sc = ex["absz"] / np.sqrt(ex["W"])
+            assert np.all(np.abs(snr - o) <= 2e-5 * sc + 1e-5 * np.abs(o)), (n_t, np.max(np.abs(snr - o) / sc))
+            for q in range(4):
+                got = gf[:, q] if q < 3 else gt
+                tol = 2e-4 * np.max(np.abs(og[:, q])) + 1e-4 * np.abs(og[:, q])
+                assert np.all(np.abs(got - og[:, q]) <= tol), (n_t, q)
+            m.close()
+    finally:
+        ctx.set_option(_lib.STK_OPT_INTERP_THREADS, 0)
+
+
 def test_finite_differences_at_step_1e3(ctx):
     n_t, n_f, n = 200, 400, 64
     y, sig = _map("freq", n_t, n_f, 82)
